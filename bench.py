@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""SG-WLS throughput on GB300: megapixels per second per SG-WLS iteration.
+
+Workload (default): one 1024 x 768 RGB synthetic scene (200 rectangles, 50
+disks, sinusoidal texture, noise), guidance = luminance, r = 1, T = 3
+iterations, range parameter 0.1, lambda alternating 0.5 / 2.0 between
+steps.  One step = one full SG-WLS filter (2T passes) of that image.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed steps, then K steps; before every timed step L2 is
+flushed by writing a 256 MiB buffer (outside the timed events); each pass
+is bracketed by CUDA events on the stream it runs on.  `value` = megapixels
+x iterations / summed device time.  `e2e` repeats the measurement through
+the one-call API with pinned host buffers, host->device and device->host
+copies inside the timed region.  With N > 1 (torchrun) every rank filters
+its own image (weak scaling, no collective on the data path); rank 0
+prints the max-over-ranks timing.
+
+`--impl reference` times the FP64 CPU oracle on this host's cores on a
+bounded sample of the same workload (a 1024 x 192 crop per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "megapixels/s per SG-WLS iteration (fwd) at max-abs err <= 2e-4 vs FP64"
+UNIT = "MP/s/iter"
+WL = dict(name="rgb1024x768_r1_T3", H=768, W=1024, C=3, r=1, iters=3, lams=(0.5, 2.0), sigma_r=0.1, seed=2)
+FALLBACK_HBM_GBS = 6800.0
+REF_CROP_ROWS = 192
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _inputs(seed):
+    import synth
+    F = synth.rgb_scene(WL["H"], WL["W"], seed=seed)
+    G = synth.luminance(F)
+    return F, G
+
+
+# ----------------------------------------------------------------- oracle arm
+
+def _oracle_sample(crop_rows: int | None, iters: int, lam: float, seed: int):
+    """Runs the oracle once; returns (seconds, megapixels x iterations, output)."""
+    import numpy as np
+
+    from oracle import Params, sgwls
+    F, G = _inputs(seed)
+    if crop_rows:
+        F, G = F[:, :crop_rows], G[:crop_rows]
+    prm = Params(r=WL["r"], iters=iters, sigma_s=float(WL["r"]), sigma_r=WL["sigma_r"])
+    t0 = time.perf_counter()
+    U = sgwls(F.astype(np.float64), G.astype(np.float64), lam, prm)
+    dt = time.perf_counter() - t0
+    return dt, F.shape[1] * F.shape[2] / 1e6 * iters, U
+
+
+def _single_thread_env():
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    return env
+
+
+def _cpu_baseline_subprocess(out_npy: str | None):
+    """The oracle, single-threaded, in a fresh process: the full workload
+    image, T iterations at lambda 2.0 (also the accuracy reference)."""
+    code = (
+        "import sys, json, numpy as np; sys.path.insert(0, %r); import bench; "
+        "dt, mp, U = bench._oracle_sample(None, %d, 2.0, %d); "
+        "np.save(%r, U) if %r else None; print(json.dumps({'dt': dt, 'mp': mp}))"
+    ) % (ROOT, WL["iters"], WL["seed"], out_npy or "", bool(out_npy))
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_single_thread_env())
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    return d["dt"], d["mp"]
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    for i in range(args.warmup):
+        _oracle_sample(REF_CROP_ROWS, 1, WL["lams"][i % 2], WL["seed"])
+    times, mp = [], 0.0
+    for i in range(args.steps):
+        dt, m, _ = _oracle_sample(REF_CROP_ROWS, 1, WL["lams"][i % 2], WL["seed"])
+        times.append(dt)
+        mp += m
+    total = sum(times)
+    value = mp / total
+    sample = f"{WL['W']}x{REF_CROP_ROWS} crop of the workload image, 1 iteration per step"
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config_dict(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config_dict():
+    return {"workload": WL["name"], "H": WL["H"], "W": WL["W"], "C": WL["C"], "r": WL["r"],
+            "iters": WL["iters"], "lambda": list(WL["lams"]), "sigma_r": WL["sigma_r"],
+            "sigma_s": float(WL["r"]), "weight": "exp", "guidance": "luminance",
+            "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        mx = float(parts[2])
+                    except ValueError:
+                        continue
+                    for nm, v in zip(names, parts[5:9]):
+                        if v.lower().startswith("active"):
+                            reasons.add(nm)
+        finally:
+            os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1705_01674_gb300 import _capi
+    if not os.path.exists(_capi.LIB_PATH):
+        from paper_1705_01674_gb300 import build
+        build.build()
+    import paper_1705_01674_gb300 as sg
+
+    H, W, C, T = WL["H"], WL["W"], WL["C"], WL["iters"]
+    F, G = _inputs(WL["seed"] + rank)
+    f = torch.from_numpy(F).to(dev)
+    g = torch.from_numpy(G).to(dev)
+    bufs = [torch.empty_like(f), torch.empty_like(f)]
+    kw = dict(r=WL["r"], iters=T, sigma_r=WL["sigma_r"])
+    ws = torch.empty(sg.workspace_bytes(C, H, W, **kw), dtype=torch.uint8, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    dirs = [0, 1] * T
+    npass = len(dirs)
+
+    def step(lam, evs=None):
+        src = f
+        for t, d in enumerate(dirs):
+            dst = bufs[t & 1]
+            if evs is not None:
+                evs[t][0].record(stream)
+            sg.sgwls_filter_pass(src, g, lam, d, out=dst, workspace=ws, stream=stream, **kw)
+            if evs is not None:
+                evs[t][1].record(stream)
+            src = dst
+        return src
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(WL["lams"][i % 2])
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(npass)]
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    n0 = sg.launch_count()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            step(WL["lams"][i % 2], evs[i])
+    torch.cuda.synchronize(dev)
+    n1 = sg.launch_count()
+    barrier()
+    clk = clocks.stop()
+
+    pass_ms = [[evs[i][t][0].elapsed_time(evs[i][t][1]) for t in range(npass)] for i in range(args.steps)]
+    step_ms = [sum(x) for x in pass_ms]
+    total_ms = sum(step_ms)
+    col_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 0)
+    row_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    mp_per_step = H * W / 1e6 * T
+    value = world * mp_per_step * args.steps / (total_ms / 1e3)
+
+    # accuracy of the last lambda-2.0 output against the oracle (rank 0)
+    # and the CPU baseline: the oracle, single-threaded, same image.
+    err = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        with torch.cuda.stream(stream):
+            u = step(2.0)
+        torch.cuda.synchronize(dev)
+        fd, npy = tempfile.mkstemp(suffix=".npy")
+        os.close(fd)
+        try:
+            dt, mp = _cpu_baseline_subprocess(npy)
+            U = np.load(npy)
+            err = float(np.abs(u.cpu().numpy().astype(np.float64) - U).max())
+        finally:
+            os.unlink(npy)
+        cpu = {"value": mp / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"full {W}x{H} RGB image, T={T} iterations at lambda 2.0, one run, "
+                         "single thread (numpy/scipy FP64)"}
+
+    # end to end through the one-call API: pinned host in/out, copies timed
+    Fh = torch.from_numpy(F).pin_memory()
+    Gh = torch.from_numpy(G).pin_memory()
+    Uh = torch.empty_like(Fh).pin_memory()
+    fin = torch.empty_like(f)
+    gin = torch.empty_like(g)
+    uo = torch.empty_like(f)
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup + args.steps):
+            lam = WL["lams"][i % 2]
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fin.copy_(Fh, non_blocking=True)
+            gin.copy_(Gh, non_blocking=True)
+            sg.sgwls_filter(fin, gin, lam, out=uo, workspace=ws, stream=stream, **kw)
+            Uh.copy_(uo, non_blocking=True)
+            e1.record(stream)
+            if i >= args.warmup:
+                e2e_ms.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    e2e_total = sum(a.elapsed_time(b) for a, b in e2e_ms)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    e2e_value = world * mp_per_step * args.steps / (e2e_total / 1e3)
+
+    peak, peak_kind = _peaks()
+    bytes_per_pass = H * W * (C * 4 + C * 4 + 4)   # read estimate, read guidance, write estimate
+    dom_ms = max(col_ms, row_ms)
+    achieved = bytes_per_pass / (dom_ms / 1e3) / 1e9
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": None,
+        "kernel": "row pass" if row_ms >= col_ms else "column pass",
+        "peak_source": f"{peak_kind} hbm_gbs",
+        "pass_ms": {"column": col_ms, "row": row_ms},
+        "algorithmic_bytes_per_launch": bytes_per_pass,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config_dict(),
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int((Fh.numel() + Gh.numel()) * 4),
+                "d2h_bytes_per_step": int(Uh.numel() * 4)},
+        "gpu_launches": int(n1 - n0),
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if err is not None:
+        line["max_abs_err_vs_oracle"] = err
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

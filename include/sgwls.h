@@ -1,0 +1,145 @@
+/*
+ * sgwls.h -- C ABI of the GB300 SG-WLS library (libsgwls.so).
+ *
+ * Semi-Global Weighted Least Squares (Liu, Chen, Shen, Liu, Yang, ICCV 2017)
+ * smooths an image F under a guidance image G by repeating, T times, a pass
+ * along the column direction and a pass along the row direction (Sec. 2.3).
+ * Each pass builds, for every centre line k, the (2r+1)-line strip around k
+ * in zig-zag order (Sec. 2.1), solves its 1D WLS subsystem A_s u = f exactly
+ * (Eq. 5; A_s formed like Eq. 4 with the Eq. 2 guidance weights over the
+ * 2r+1 neighbouring entries of the formed vector), writes the solution back
+ * into the strip and averages the values each pixel received.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout     planar C x H x W, row-major, contiguous per image; the guidance
+ *            is one H x W plane.  Pixel (y, x) of channel c lives at
+ *            c*H*W + y*W + x elements from the base pointer.
+ * Pointers   image, guidance, output, workspace and saved-estimate pointers
+ *            are DEVICE pointers (cudaMalloc / caching-allocator memory of the
+ *            current device); parameter structs and image tables are HOST
+ *            pointers.  The caller owns every buffer; the library allocates
+ *            nothing and keeps no state between calls.
+ * Stream     `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *            default stream).  Every call is asynchronous on that stream:
+ *            results are ready when the stream has reached the call.
+ * Aliasing   the output may not alias the input; the guidance may alias the
+ *            input (guidance = input, as in the grayscale workloads).
+ * Errors     arguments are validated on the host before anything is
+ *            launched; a failed validation returns an SGWLS_E_* code and
+ *            touches no memory.  A CUDA launch failure returns SGWLS_E_CUDA
+ *            (the CUDA error string is kept by sgwls_last_cuda_error()).
+ * Precision  all elimination arithmetic is FP32; no FP64 on the GPU.
+ *            `storage` selects FP32 or BF16 for the input/output/guidance
+ *            buffers, `inter_storage` for the estimates between passes.
+ */
+#ifndef SGWLS_H
+#define SGWLS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SGWLS_OK = 0,
+  SGWLS_E_INVALID = -1,     /* a parameter is out of range or a pointer is NULL */
+  SGWLS_E_SHAPE = -2,       /* H, W < 2r+1, C < 1, or sizes too large            */
+  SGWLS_E_DTYPE = -3,       /* unknown storage type                              */
+  SGWLS_E_WORKSPACE = -4,   /* workspace missing or smaller than required        */
+  SGWLS_E_CUDA = -5,        /* a CUDA call failed (see sgwls_last_cuda_error)    */
+  SGWLS_E_DEVICE_FLAG = -6, /* a kernel reported an internal error flag          */
+  SGWLS_E_UNSUPPORTED = -7  /* valid request this build does not implement       */
+} sgwls_status;
+
+typedef enum { SGWLS_F32 = 0, SGWLS_BF16 = 1 } sgwls_dtype;
+
+/* Eq. 2: the two guidance weights. */
+typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
+
+/* User constants of the method.  Fill with sgwls_params_default() first.
+ *   weight      Eq. 2 form: exp(-|i-j|^2/2 sigma_s^2) exp(-|Gi-Gj|^2/2 sigma_r^2)
+ *               or 1/(|i-j|^alpha_s + eps) * 1/(|Gi-Gj|^alpha_r + eps);
+ *               |i-j| is the Euclidean distance of the pixel coordinates.
+ *   r           neighbourhood radius, (2r+1)x(2r+1) system, 1 <= r <= SGWLS_R_MAX
+ *   iters       T, the number of (column pass, row pass) pairs, >= 0 (Sec. 2.3)
+ *   step        tau, the sliding step between subsystem centres (Sec. 2.3),
+ *               1 <= step <= 2r+1; the last centre is always included
+ *   axis_order  0: column direction first (Sec. 2.3), 1: row direction first
+ *   refine      reserved (0)
+ *   storage     sgwls_dtype of f, g and u
+ *   inter_storage  sgwls_dtype of the estimates between passes
+ *   chunk_lines 0: automatic; otherwise the number of lines per chunk of
+ *               the parallel subsystem solve (a tuning knob; the result is
+ *               the same up to FP32 rounding for every value)            */
+typedef struct {
+  int weight;
+  float sigma_s, sigma_r;
+  float alpha_s, alpha_r, eps;
+  int r;
+  int iters;
+  int step;
+  int axis_order;
+  int refine;
+  int storage;
+  int inter_storage;
+  int chunk_lines;
+} sgwls_params;
+
+#define SGWLS_R_MAX 8
+#define SGWLS_C_MAX 64
+
+/* Defaults: exp weights, sigma_s = 1, sigma_r = 0.1, alpha_s = alpha_r = 1.2,
+ * eps = 1e-4 (Sec. 1), r = 1, iters = 1, step = 1, axis_order = 0,
+ * refine = 0, FP32 storage, chunk_lines = 0.  `p` must not be NULL. */
+void sgwls_params_default(sgwls_params* p);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* sgwls_status_string(sgwls_status s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* sgwls_last_cuda_error(void);
+
+/* Workspace bytes sgwls_filter needs for an H x W x C image with `p`
+ * (0 if the arguments are invalid).  Host-only; launches nothing. */
+size_t sgwls_workspace_bytes(int H, int W, int C, const sgwls_params* p);
+
+/* SG-WLS filter of one image (Sec. 2.3; Eqs. 2, 4, 5).
+ *   f       device, C x H x W input (storage type p->storage)
+ *   g       device, H x W guidance (p->storage); may equal f when C == 1
+ *   u       device, C x H x W output (p->storage); must not alias f
+ *   lambda  smoothness weight of Eq. 1 / Eq. 4, >= 0
+ *   ws      device workspace of at least sgwls_workspace_bytes(H, W, C, p)
+ *           bytes, 256-byte aligned; contents on entry are ignored
+ *   saved   device, NULL or 2*iters*C*H*W elements of type p->inter_storage:
+ *           if given, the input estimate of pass t (t = 0 .. 2*iters-1) is
+ *           written to element offset t*C*H*W (pass 0's input is a copy of
+ *           f), the per-pass checkpoints sgwls_filter_backward reads.
+ *   stream  cudaStream_t as void*
+ * iters == 0 copies f to u. */
+sgwls_status sgwls_filter(const void* f, const void* g, void* u, int H, int W, int C,
+                          float lambda, const sgwls_params* p, void* ws, size_t ws_bytes,
+                          void* saved, void* stream);
+
+/* One pass of Sec. 2.3 along one direction: for every centre line k the
+ * neighbourhood construction (Sec. 2.1), the exact solve of its subsystem
+ * (Eq. 5), the inverse construction and the averaging; u = pass(f).
+ *   direction  0: column direction (centres are columns), 1: row direction
+ * f, g, u, lambda, p, ws, ws_bytes, stream as in sgwls_filter (p->iters is
+ * ignored except for workspace sizing; f and u use p->storage).  The
+ * workspace of sgwls_workspace_bytes(H, W, C, p) suffices. */
+sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int W, int C,
+                               float lambda, const sgwls_params* p, int direction, void* ws,
+                               size_t ws_bytes, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all devices).  Diagnostics: lets a caller count the kernels
+ * behind a sequence of calls.  Host-only. */
+unsigned long long sgwls_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGWLS_H */

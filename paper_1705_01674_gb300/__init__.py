@@ -1,0 +1,121 @@
+"""GB300-native Semi-Global Weighted Least Squares (SG-WLS) filtering.
+
+Python face of libsgwls.so (include/sgwls.h).  PyTorch supplies device
+memory and the current CUDA stream; every step of the filter runs in the
+library's CUDA kernels.  Tensors must be CUDA tensors: there is no CPU path.
+
+    u = sgwls_filter(f, g, lam, r=1, iters=3)        # f: (C,H,W), g: (H,W)
+
+Parameters follow Liu et al., ICCV 2017: ``r`` the neighbourhood radius of
+the (2r+1)x(2r+1) system, ``iters`` the number T of (column, row) pass pairs
+(Sec. 2.3), ``step`` the sliding step tau, Eq. 2 weights ``weight='exp'``
+(``sigma_s``, default r, and ``sigma_r``) or ``'frac'`` (``alpha_s``,
+``alpha_r``, ``eps``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _capi
+from ._capi import SgwlsError, make_params
+
+__all__ = ["sgwls_filter", "sgwls_filter_pass", "workspace_bytes", "launch_count", "make_params", "SgwlsError"]
+
+_DT = {torch.float32: _capi.F32, torch.bfloat16: _capi.BF16}
+
+
+def _check_tensor(x: torch.Tensor, name: str):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (the SG-WLS library has no CPU path)")
+    if x.dtype not in _DT:
+        raise TypeError(f"{name} must be float32 or bfloat16, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _chw(f: torch.Tensor):
+    if f.dim() == 2:
+        return 1, f.shape[0], f.shape[1]
+    if f.dim() == 3:
+        return f.shape[0], f.shape[1], f.shape[2]
+    raise ValueError("f must be (H, W) or (C, H, W)")
+
+
+def workspace_bytes(C: int, H: int, W: int, **kw) -> int:
+    p = make_params(**kw)
+    n = _capi.lib().sgwls_workspace_bytes(int(H), int(W), int(C), ctypes.byref(p))
+    if n == 0 and p.iters > 0:
+        raise SgwlsError(-1, "sgwls_workspace_bytes", "invalid arguments")
+    return int(n)
+
+
+def sgwls_filter(f: torch.Tensor, g: torch.Tensor, lam: float, *, out: torch.Tensor | None = None,
+                 saved: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                 stream: torch.cuda.Stream | None = None, **kw) -> torch.Tensor:
+    """SG-WLS filter of one image through ``sgwls_filter`` (C ABI).
+
+    f: (C,H,W) or (H,W); g: (H,W), same dtype as f (float32 or bfloat16).
+    ``saved`` (optional): a float tensor with 2*iters*C*H*W elements in the
+    intermediate storage type that receives each pass's input estimate.
+    Keyword parameters: see ``make_params``."""
+    _check_tensor(f, "f")
+    _check_tensor(g, "g")
+    C, H, W = _chw(f)
+    if tuple(g.shape) != (H, W):
+        raise ValueError("g must be (H, W)")
+    if g.dtype != f.dtype:
+        raise TypeError("g must have the dtype of f")
+    kw.setdefault("storage", "bf16" if f.dtype == torch.bfloat16 else "f32")
+    p = make_params(**kw)
+    lib = _capi.lib()
+    if out is None:
+        out = torch.empty_like(f)
+    else:
+        _check_tensor(out, "out")
+    nws = lib.sgwls_workspace_bytes(H, W, C, ctypes.byref(p))
+    if workspace is None or workspace.numel() < nws:
+        workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    status = lib.sgwls_filter(
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+        H, W, C, ctypes.c_float(float(lam)), ctypes.byref(p),
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+        ctypes.c_void_p(saved.data_ptr() if saved is not None else 0),
+        ctypes.c_void_p(st.cuda_stream))
+    _capi.check(status, "sgwls_filter")
+    return out
+
+
+def sgwls_filter_pass(f: torch.Tensor, g: torch.Tensor, lam: float, direction: int, *,
+                      out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                      stream: torch.cuda.Stream | None = None, **kw) -> torch.Tensor:
+    """One pass along ``direction`` (0: column direction, 1: row direction)
+    through ``sgwls_filter_pass`` (C ABI)."""
+    _check_tensor(f, "f")
+    _check_tensor(g, "g")
+    C, H, W = _chw(f)
+    if tuple(g.shape) != (H, W) or g.dtype != f.dtype:
+        raise ValueError("g must be (H, W) with the dtype of f")
+    kw.setdefault("storage", "bf16" if f.dtype == torch.bfloat16 else "f32")
+    p = make_params(**kw)
+    lib = _capi.lib()
+    if out is None:
+        out = torch.empty_like(f)
+    nws = lib.sgwls_workspace_bytes(H, W, C, ctypes.byref(p))
+    if workspace is None or workspace.numel() < nws:
+        workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    status = lib.sgwls_filter_pass(
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+        H, W, C, ctypes.c_float(float(lam)), ctypes.byref(p), int(direction),
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+        ctypes.c_void_p(st.cuda_stream))
+    _capi.check(status, "sgwls_filter_pass")
+    return out
+
+
+def launch_count() -> int:
+    """Kernels launched by libsgwls.so in this process so far."""
+    return int(_capi.lib().sgwls_launch_count())

@@ -1,0 +1,331 @@
+// sgwls_api.cu -- the C ABI declared in include/sgwls.h: argument checks,
+// workspace layout, the sequence of passes (Sec. 2.3) and kernel dispatch.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "../../include/sgwls.h"
+#include "sgwls_launch.cuh"
+
+namespace sgwls {
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+// Launch counter: every kernel the library launches adds one.
+unsigned long long g_launches = 0;
+
+sgwls_status cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return SGWLS_E_CUDA;
+}
+
+size_t dt_size(int dt) { return dt == DT_F32 ? 4 : 2; }
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Resident-warp target used to size the chunking: 152 SMs x 16 warps.
+constexpr int kTargetWarps = 152 * 16;
+constexpr size_t kSmemPerWarpCap = 96 * 1024;
+constexpr size_t kSmemPerBlockCap = 200 * 1024;
+constexpr int kPMax = 512;
+
+Plan make_plan(int L, int D, int r, int CC, int chunk_lines) {
+  const int n = 2 * r + 1;
+  const int NF = r + 1 + CC;
+  const size_t line_bytes = (size_t)n * NF * 32 * sizeof(float);
+  const int bands = (D + (32 - 2 * r) - 1) / (32 - 2 * r);
+  int P = std::max(1, std::min(L, (kTargetWarps + bands - 1) / bands));
+  P = std::min(P, kPMax);
+  int h = (L + P - 1) / P;
+  if (chunk_lines > 0) h = std::min(chunk_lines, L);
+  const int hmax = std::max<int>(1, (int)(kSmemPerWarpCap / line_bytes));
+  if (h > hmax) h = hmax;
+  P = (L + h - 1) / h;
+  Plan pl;
+  pl.h = h;
+  pl.P = P;
+  const size_t warp_bytes = (size_t)h * line_bytes;
+  pl.warps_rec = (int)std::max<size_t>(1, std::min<size_t>(4, kSmemPerBlockCap / warp_bytes));
+  pl.warps_rec = std::min(pl.warps_rec, P);
+  pl.smem_rec = warp_bytes * pl.warps_rec;
+  return pl;
+}
+
+int n_fields(int r, int CC) { return 3 * r * r + 2 * r * CC; }
+
+struct Layout {
+  size_t img_off, img_bytes;
+  size_t summ_off, summ_bytes;
+  size_t xsep_off, xsep_bytes;
+  size_t total;
+};
+
+// Largest per-pass scratch over both directions and all channel groups.
+Layout make_layout(int H, int W, int C, const sgwls_params* p) {
+  Layout lo;
+  const int r = p->r;
+  const int CC = std::min(C, kGroupMax);
+  size_t summ = 0, xsep = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int L = dir == 0 ? H : W;
+    const int D = dir == 0 ? W : H;
+    const int nsys = D - 2 * r;
+    const Plan pl = make_plan(L, D, r, CC, p->chunk_lines);
+    summ = std::max(summ, (size_t)pl.P * n_fields(r, CC) * nsys * sizeof(float));
+    xsep = std::max(xsep, (size_t)std::max(pl.P - 1, 1) * r * CC * nsys * sizeof(float));
+  }
+  const size_t img = (p->iters > 0) ? (size_t)C * H * W * dt_size(p->inter_storage) : 0;
+  lo.img_off = 0;
+  lo.img_bytes = align256(img);
+  lo.summ_off = lo.img_off + lo.img_bytes;
+  lo.summ_bytes = align256(summ);
+  lo.xsep_off = lo.summ_off + lo.summ_bytes;
+  lo.xsep_bytes = align256(xsep);
+  lo.total = lo.xsep_off + lo.xsep_bytes;
+  return lo;
+}
+
+sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
+  if (!p) return SGWLS_E_INVALID;
+  if (p->r < 1 || p->r > SGWLS_R_MAX) return SGWLS_E_INVALID;
+  if (p->iters < 0 || p->step < 1 || p->step > 2 * p->r + 1) return SGWLS_E_INVALID;
+  if (p->axis_order != 0 && p->axis_order != 1) return SGWLS_E_INVALID;
+  if (p->weight != SGWLS_W_EXP && p->weight != SGWLS_W_FRAC) return SGWLS_E_INVALID;
+  if (p->weight == SGWLS_W_EXP && !(p->sigma_s > 0.f && p->sigma_r > 0.f)) return SGWLS_E_INVALID;
+  if (p->weight == SGWLS_W_FRAC && !(p->eps > 0.f && p->alpha_s >= 0.f && p->alpha_r >= 0.f)) return SGWLS_E_INVALID;
+  if (!isfinite(p->sigma_s) || !isfinite(p->sigma_r) || !isfinite(p->alpha_s) || !isfinite(p->alpha_r) ||
+      !isfinite(p->eps))
+    return SGWLS_E_INVALID;
+  if (p->refine != 0) return SGWLS_E_UNSUPPORTED;
+  if (p->chunk_lines < 0) return SGWLS_E_INVALID;
+  if ((p->storage != SGWLS_F32 && p->storage != SGWLS_BF16) ||
+      (p->inter_storage != SGWLS_F32 && p->inter_storage != SGWLS_BF16))
+    return SGWLS_E_DTYPE;
+  if (C < 1 || C > SGWLS_C_MAX) return SGWLS_E_SHAPE;
+  if (H < 2 * p->r + 1 || W < 2 * p->r + 1) return SGWLS_E_SHAPE;
+  if (H > 65536 || W > 65536 || (long long)H * W > (1LL << 31) / 4) return SGWLS_E_SHAPE;
+  if (p->step != 1) return SGWLS_E_UNSUPPORTED;
+  return SGWLS_OK;
+}
+
+PassLauncher launcher_for(int r) {
+  switch (r) {
+    case 1: return launch_pass_r1;
+    case 2: return launch_pass_r2;
+    case 3: return launch_pass_r3;
+    case 4: return launch_pass_r4;
+    case 5: return launch_pass_r5;
+    case 6: return launch_pass_r6;
+    case 7: return launch_pass_r7;
+    case 8: return launch_pass_r8;
+    default: return nullptr;
+  }
+}
+
+// Fills the parts of the argument block that depend only on the parameters.
+void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
+  const int r = p->r;
+  const int n = 2 * r + 1;
+  a.lam = lambda;
+  a.weight = p->weight;
+  if (p->weight == SGWLS_W_EXP) {
+    a.range_k = (float)(-1.4426950408889634 / (2.0 * (double)p->sigma_r * (double)p->sigma_r));
+  } else {
+    a.range_k = p->alpha_r;
+  }
+  a.eps = p->eps;
+  // Spatial factor of the pair (p, p+t) with j = p % n: same line -> distance
+  // t; next line -> one line over and |4r + 1 - 2j - t| across (the snake
+  // turns), for both directions.
+  for (int j = 0; j < n; ++j) {
+    for (int t = 1; t <= r; ++t) {
+      double d2;
+      if (j + t < n) {
+        d2 = (double)t * t;
+      } else {
+        const double dx = (double)(4 * r + 1 - 2 * j - t);
+        d2 = 1.0 + dx * dx;
+      }
+      double sp;
+      if (p->weight == SGWLS_W_EXP) {
+        sp = exp(-d2 / (2.0 * (double)p->sigma_s * (double)p->sigma_s));
+      } else {
+        sp = 1.0 / (pow(sqrt(d2), (double)p->alpha_s) + (double)p->eps);
+      }
+      a.sp[j * r + t - 1] = (float)(lambda * sp);
+    }
+  }
+}
+
+__global__ void k_convert(const void* src, int sdt, void* dst, int ddt, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) st_px(dst, i, ddt, ld_px(src, i, sdt));
+}
+
+sgwls_status copy_image(const void* src, int sdt, void* dst, int ddt, long long count, cudaStream_t st) {
+  if (sdt == ddt) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)count * dt_size(sdt), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? SGWLS_OK : cuda_fail(e);
+  }
+  k_convert<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(src, sdt, dst, ddt, count);
+  __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SGWLS_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+// One pass along `dir` (Sec. 2.3, the four steps): out = pass(in).
+sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const void* g, int H, int W, int C,
+                      float lambda, const sgwls_params* p, int dir, float* summ, float* xsep, cudaStream_t st) {
+  const long long plane = (long long)H * W;
+  PassArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = g;
+  a.plane = plane;
+  a.H = H;
+  a.W = W;
+  a.g_dt = p->storage;
+  a.in_dt = in_dt;
+  a.out_dt = out_dt;
+  a.dir = dir;
+  a.L = dir == 0 ? H : W;
+  a.D = dir == 0 ? W : H;
+  a.nsys = a.D - 2 * p->r;
+  a.summ = summ;
+  a.xsep = xsep;
+  fill_weights(a, p, lambda);
+  const PassLauncher launch = launcher_for(p->r);
+  for (int c0 = 0; c0 < C; c0 += kGroupMax) {
+    const int CC = std::min(kGroupMax, C - c0);
+    const Plan pl = make_plan(a.L, a.D, p->r, CC, p->chunk_lines);
+    a.h = pl.h;
+    a.P = pl.P;
+    a.in = static_cast<const char*>(in) + (size_t)c0 * plane * dt_size(in_dt);
+    a.out = static_cast<char*>(out) + (size_t)c0 * plane * dt_size(out_dt);
+    cudaError_t e = launch(a, pl, CC, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 3 : 1), __ATOMIC_RELAXED);
+  }
+  return SGWLS_OK;
+}
+
+// Runs all passes of one image.  Shared by the public entry points.
+sgwls_status run_filter(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
+                        const sgwls_params* p, void* ws, void* saved, cudaStream_t st) {
+  const Layout lo = make_layout(H, W, C, p);
+  const long long count = (long long)H * W * C;
+  const int sdt = p->storage, idt = p->inter_storage;
+  if (p->iters == 0) return copy_image(f, sdt, u, sdt, count, st);
+
+  char* wsb = static_cast<char*>(ws);
+  void* img = wsb + lo.img_off;
+  float* summ = reinterpret_cast<float*>(wsb + lo.summ_off);
+  float* xsep = reinterpret_cast<float*>(wsb + lo.xsep_off);
+  const int npass = 2 * p->iters;
+  const size_t inter_bytes = (size_t)count * dt_size(idt);
+  if (saved) {
+    sgwls_status s = copy_image(f, sdt, saved, idt, count, st);
+    if (s != SGWLS_OK) return s;
+  }
+  const void* cur = f;
+  int cur_dt = sdt;
+  for (int t = 0; t < npass; ++t) {
+    const int dir = ((t & 1) == 0) ? p->axis_order : 1 - p->axis_order;
+    void* dst;
+    int dst_dt;
+    if (t == npass - 1) {
+      dst = u;
+      dst_dt = sdt;
+    } else if (saved) {
+      dst = static_cast<char*>(saved) + (size_t)(t + 1) * inter_bytes;
+      dst_dt = idt;
+    } else {
+      dst = ((npass - 1 - t) & 1) ? img : u;
+      dst_dt = ((npass - 1 - t) & 1) ? idt : sdt;
+    }
+    sgwls_status s = run_pass(cur, cur_dt, dst, dst_dt, g, H, W, C, lambda, p, dir, summ, xsep, st);
+    if (s != SGWLS_OK) return s;
+    cur = dst;
+    cur_dt = dst_dt;
+  }
+  return SGWLS_OK;
+}
+
+}  // namespace sgwls
+
+using namespace sgwls;
+
+extern "C" {
+
+void sgwls_params_default(sgwls_params* p) {
+  if (!p) return;
+  p->weight = SGWLS_W_EXP;
+  p->sigma_s = 1.0f;
+  p->sigma_r = 0.1f;
+  p->alpha_s = 1.2f;
+  p->alpha_r = 1.2f;
+  p->eps = 1e-4f;
+  p->r = 1;
+  p->iters = 1;
+  p->step = 1;
+  p->axis_order = 0;
+  p->refine = 0;
+  p->storage = SGWLS_F32;
+  p->inter_storage = SGWLS_F32;
+  p->chunk_lines = 0;
+}
+
+const char* sgwls_status_string(sgwls_status s) {
+  switch (s) {
+    case SGWLS_OK: return "SGWLS_OK";
+    case SGWLS_E_INVALID: return "SGWLS_E_INVALID: invalid argument";
+    case SGWLS_E_SHAPE: return "SGWLS_E_SHAPE: invalid image shape";
+    case SGWLS_E_DTYPE: return "SGWLS_E_DTYPE: unknown storage type";
+    case SGWLS_E_WORKSPACE: return "SGWLS_E_WORKSPACE: workspace missing or too small";
+    case SGWLS_E_CUDA: return "SGWLS_E_CUDA: CUDA error";
+    case SGWLS_E_DEVICE_FLAG: return "SGWLS_E_DEVICE_FLAG: kernel reported an error";
+    case SGWLS_E_UNSUPPORTED: return "SGWLS_E_UNSUPPORTED: not implemented in this build";
+  }
+  return "SGWLS_E_?: unknown status";
+}
+
+const char* sgwls_last_cuda_error(void) { return g_cuda_err; }
+
+size_t sgwls_workspace_bytes(int H, int W, int C, const sgwls_params* p) {
+  if (check_params(H, W, C, p) != SGWLS_OK) return 0;
+  return make_layout(H, W, C, p).total;
+}
+
+sgwls_status sgwls_filter(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
+                          const sgwls_params* p, void* ws, size_t ws_bytes, void* saved, void* stream) {
+  sgwls_status s = check_params(H, W, C, p);
+  if (s != SGWLS_OK) return s;
+  if (!f || !g || !u || f == u) return SGWLS_E_INVALID;
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
+  const size_t need = make_layout(H, W, C, p).total;
+  if (need > 0 && (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255))) return SGWLS_E_WORKSPACE;
+  return run_filter(f, g, u, H, W, C, lambda, p, ws, saved, static_cast<cudaStream_t>(stream));
+}
+
+sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
+                               const sgwls_params* p, int direction, void* ws, size_t ws_bytes, void* stream) {
+  sgwls_status s = check_params(H, W, C, p);
+  if (s != SGWLS_OK) return s;
+  if (!f || !g || !u || f == u) return SGWLS_E_INVALID;
+  if (direction != 0 && direction != 1) return SGWLS_E_INVALID;
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
+  const Layout lo = make_layout(H, W, C, p);
+  if (!ws || ws_bytes < lo.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
+  char* wsb = static_cast<char*>(ws);
+  return run_pass(f, p->storage, u, p->storage, g, H, W, C, lambda, p, direction,
+                  reinterpret_cast<float*>(wsb + lo.summ_off), reinterpret_cast<float*>(wsb + lo.xsep_off),
+                  static_cast<cudaStream_t>(stream));
+}
+
+unsigned long long sgwls_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+}  // extern "C"

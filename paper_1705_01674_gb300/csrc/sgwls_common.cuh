@@ -1,0 +1,80 @@
+// sgwls_common.cuh -- argument block and small device helpers shared by the
+// SG-WLS pass kernels.
+//
+// Geometry of one pass (Sec. 2.1).  A pass runs along one direction:
+//   dir 0 ("column direction"): centres are columns k, the formed vector runs
+//        down the image rows; lines = rows (L = H), across = columns (D = W).
+//   dir 1 ("row direction"): centres are rows k, the vector runs along the
+//        columns; lines = columns (L = W), across = rows (D = H).
+// Entry p of the vector of centre k sits on line p / n at across-offset
+//   k - r + j   (line even, 0-based; the paper's odd 1-based rows), or
+//   k + r - j   (line odd: reversed), with j = p % n and n = 2r + 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace sgwls {
+
+constexpr int kRMax = 8;
+constexpr int kGroupMax = 4;   // channels solved together against one factor
+
+enum : int { DT_F32 = 0, DT_BF16 = 1 };
+
+struct PassArgs {
+  const void* in;      // C planes, dtype in_dt
+  const void* g;       // guidance plane, dtype g_dt
+  void* out;           // C planes, dtype out_dt
+  long long plane;     // H * W (elements per plane)
+  int H, W;
+  int in_dt, g_dt, out_dt;
+  int dir;             // 0 column direction, 1 row direction
+  int D;               // extent across the lines (number of columns for dir 0)
+  int L;               // number of lines (rows for dir 0)
+  int nsys;            // number of centres: D - 2r (step 1)
+  int h;               // lines per chunk
+  int P;               // chunks per subsystem
+  float lam;           // lambda
+  int weight;          // 0 exp, 1 frac
+  float range_k;       // exp: -log2(e) / (2 sigma_r^2);  frac: alpha_r
+  float eps;           // frac epsilon
+  // lambda * spatial factor of the pair (p, p+t) for j = p % n, t = 1..r:
+  // sp[j * r + t - 1]
+  float sp[(2 * kRMax + 1) * kRMax];
+  float* summ;         // chunk summaries  [P][nfields][nsys]
+  float* xsep;         // separator values [P-1][r*CC][nsys]
+};
+
+__device__ __forceinline__ float ld_px(const void* base, long long idx, int dt) {
+  if (dt == DT_F32) return __ldg(reinterpret_cast<const float*>(base) + idx);
+  const unsigned short raw = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+  return __uint_as_float(static_cast<unsigned>(raw) << 16);
+}
+
+__device__ __forceinline__ void st_px(void* base, long long idx, int dt, float v) {
+  if (dt == DT_F32) {
+    reinterpret_cast<float*>(base)[idx] = v;
+  } else {
+    reinterpret_cast<__nv_bfloat16*>(base)[idx] = __float2bfloat16_rn(v);
+  }
+}
+
+// Pixel index of (line, across-offset) for the pass direction.
+__device__ __forceinline__ long long pix_index(const PassArgs& a, int line, int off) {
+  return a.dir == 0 ? (long long)line * a.W + off : (long long)off * a.W + line;
+}
+
+// Range factor of Eq. 2 for the guidance difference dg.
+__device__ __forceinline__ float range_factor(const PassArgs& a, float dg) {
+  if (a.weight == 0) return exp2f(dg * dg * a.range_k);
+  return 1.0f / (powf(fabsf(dg), a.range_k) + a.eps);
+}
+
+__device__ __forceinline__ float fast_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+}  // namespace sgwls

@@ -1,0 +1,8 @@
+// Kernels of one SG-WLS pass instantiated for neighbourhood radius r = 3.
+#include "sgwls_launch.cuh"
+
+namespace sgwls {
+cudaError_t launch_pass_r3(const PassArgs& a, const Plan& pl, int CC, cudaStream_t st) {
+  return launch_pass_r<3>(a, pl, CC, st);
+}
+}  // namespace sgwls

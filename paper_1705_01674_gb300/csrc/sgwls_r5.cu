@@ -1,0 +1,8 @@
+// Kernels of one SG-WLS pass instantiated for neighbourhood radius r = 5.
+#include "sgwls_launch.cuh"
+
+namespace sgwls {
+cudaError_t launch_pass_r5(const PassArgs& a, const Plan& pl, int CC, cudaStream_t st) {
+  return launch_pass_r<5>(a, pl, CC, st);
+}
+}  // namespace sgwls

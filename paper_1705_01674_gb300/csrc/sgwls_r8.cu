@@ -1,0 +1,8 @@
+// Kernels of one SG-WLS pass instantiated for neighbourhood radius r = 8.
+#include "sgwls_launch.cuh"
+
+namespace sgwls {
+cudaError_t launch_pass_r8(const PassArgs& a, const Plan& pl, int CC, cudaStream_t st) {
+  return launch_pass_r<8>(a, pl, CC, st);
+}
+}  // namespace sgwls

@@ -1,0 +1,98 @@
+"""The C ABI library loads, exports every symbol include/sgwls.h declares,
+and validates arguments on the host (no GPU needed for any of this)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(sgwls_\w+)\s*\(", text, flags=re.M):
+            if not m.group(0).lstrip().startswith(("typedef", "#")):
+                names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1705_01674_gb300 import build, _capi
+    build.build()
+    return _capi
+
+
+def test_header_declares_entry_points():
+    names = _declared_functions()
+    for need in ("sgwls_filter", "sgwls_workspace_bytes", "sgwls_params_default", "sgwls_status_string"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(capi):
+    lib = capi.lib()
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_defaults_and_status_strings(capi):
+    lib = capi.lib()
+    p = capi.SgwlsParams()
+    lib.sgwls_params_default(ctypes.byref(p))
+    assert (p.r, p.iters, p.step, p.axis_order, p.weight) == (1, 1, 1, 0, 0)
+    assert p.sigma_s == pytest.approx(1.0) and p.sigma_r == pytest.approx(0.1)
+    assert p.eps == pytest.approx(1e-4)
+    for code in range(-7, 1):
+        assert lib.sgwls_status_string(code).decode().startswith("SGWLS_")
+
+
+def test_workspace_bytes_host_only(capi):
+    lib = capi.lib()
+    p = capi.make_params(r=1, iters=3)
+    n1 = lib.sgwls_workspace_bytes(768, 1024, 3, ctypes.byref(p))
+    assert n1 >= 768 * 1024 * 3 * 4 and n1 % 256 == 0
+    p0 = capi.make_params(r=1, iters=0)
+    assert lib.sgwls_workspace_bytes(768, 1024, 3, ctypes.byref(p0)) < n1
+    bad = capi.make_params(r=1)
+    bad.r = 9
+    assert lib.sgwls_workspace_bytes(64, 64, 1, ctypes.byref(bad)) == 0
+    assert lib.sgwls_workspace_bytes(2, 64, 1, ctypes.byref(p)) == 0
+
+
+def _call(capi, H=64, W=64, C=1, lam=1.0, p=None, f=0x1000, g=0x2000, u=0x3000, ws=0x10000, nws=1 << 30):
+    lib = capi.lib()
+    p = p if p is not None else capi.make_params()
+    return lib.sgwls_filter(ctypes.c_void_p(f), ctypes.c_void_p(g), ctypes.c_void_p(u), H, W, C,
+                            ctypes.c_float(lam), ctypes.byref(p), ctypes.c_void_p(ws), nws,
+                            ctypes.c_void_p(0), ctypes.c_void_p(0))
+
+
+def test_validation_before_any_launch(capi):
+    """Invalid arguments are rejected on the host (the pointers here are
+    never dereferenced: every call fails validation first)."""
+    E_INVALID, E_SHAPE, E_DTYPE, E_WS, E_UNSUP = -1, -2, -3, -4, -7
+    assert _call(capi, f=0) == E_INVALID
+    assert _call(capi, u=0x1000) == E_INVALID            # u aliases f
+    assert _call(capi, lam=-1.0) == E_INVALID
+    assert _call(capi, lam=float("nan")) == E_INVALID
+    assert _call(capi, H=2, p=capi.make_params(r=1)) == E_SHAPE
+    assert _call(capi, W=4, p=capi.make_params(r=2)) == E_SHAPE
+    assert _call(capi, C=0) == E_SHAPE
+    for field, val in (("r", 0), ("r", 9), ("iters", -1), ("step", 0), ("axis_order", 2),
+                       ("weight", 5), ("sigma_r", 0.0), ("chunk_lines", -2)):
+        p = capi.make_params()
+        setattr(p, field, val)
+        assert _call(capi, p=p) == E_INVALID, field
+    p = capi.make_params()
+    p.storage = 7
+    assert _call(capi, p=p) == E_DTYPE
+    assert _call(capi, ws=0) == E_WS
+    assert _call(capi, nws=16) == E_WS
+    assert _call(capi, ws=0x10010) == E_WS                # misaligned
+    assert _call(capi, p=capi.make_params(r=1, refine=1)) == E_UNSUP

@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: max |GPU - oracle| <= 2e-4 on [0, 1]-valued FP32 images for
+r <= 3 and T <= 3 (the stated target).  The same bound is applied to r = 4, 5
+(all elimination is FP32 on strictly diagonally dominant systems, so the
+error does not grow with r beyond FP32 rounding).  BF16 storage bounds
+follow from each pass being a convex averaging of exact solves
+(non-expansive in the max norm): each BF16 store adds at most 2^-9 for
+values in [0, 1].
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import COLUMN, ROW, Params, sgwls, sgwls_pass
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_01674_gb300 import build
+    build.build()
+    import paper_1705_01674_gb300 as m
+    return m
+
+
+def _gpu(api, F, G, lam, **kw):
+    import torch
+    dev = torch.device("cuda:0")
+    f = torch.from_numpy(np.ascontiguousarray(F)).to(dev)
+    g = torch.from_numpy(np.ascontiguousarray(G)).to(dev)
+    u = api.sgwls_filter(f, g, lam, **kw)
+    torch.cuda.synchronize()
+    return u.float().cpu().numpy().astype(np.float64)
+
+
+def _oracle(F, G, lam, r=1, iters=1, axis_order=0, weight="exp", sigma_s=None, sigma_r=0.1,
+            alpha_s=1.2, alpha_r=1.2, eps=1e-4, **_):
+    prm = Params(r=r, iters=iters, axis_order=axis_order, weight=weight,
+                 sigma_s=float(r if sigma_s is None else sigma_s), sigma_r=sigma_r,
+                 alpha_s=alpha_s, alpha_r=alpha_r, eps=eps)
+    return sgwls(F.astype(np.float64), G.astype(np.float64), lam, prm)
+
+
+def _maxerr(a, b):
+    return float(np.abs(a.reshape(b.shape) - b).max())
+
+
+def test_config_gray64(api):
+    """64x64 grayscale, 8 rectangles + noise, guidance = input, r = 1, T = 1,
+    lambda = 1, range parameter 0.1."""
+    F = synth.rect_gray(64, 64, seed=0)
+    kw = dict(r=1, iters=1, sigma_r=0.1)
+    err = _maxerr(_gpu(api, F, F[0], 1.0, **kw), _oracle(F, F[0], 1.0, **kw))
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("C", [1, 3])
+@pytest.mark.parametrize("axis_order", [0, 1])
+@pytest.mark.parametrize("chunk_lines", [0, 1, 3, 1000])
+def test_parity_small_ragged(api, r, C, axis_order, chunk_lines):
+    """53 x 71 images: several warp bands with a ragged last band, several
+    chunks with a ragged last chunk (or one chunk), both pass orders."""
+    F = synth.rgb_scene(53, 71, seed=10 + r, n_rect=15, n_disk=4)[:C]
+    G = synth.luminance(synth.rgb_scene(53, 71, seed=10 + r, n_rect=15, n_disk=4))
+    kw = dict(r=r, iters=2, axis_order=axis_order, sigma_r=0.1)
+    got = _gpu(api, F, G, 2.0, chunk_lines=chunk_lines, **kw)
+    err = _maxerr(got, _oracle(F, G, 2.0, **kw))
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (3, 40), (40, 3), (5, 130), (130, 5), (33, 31)])
+def test_edge_shapes(api, shape):
+    """Minimum sizes (a single centre), very thin images, sizes one past a
+    warp band."""
+    H, W = shape
+    r = 1 if min(H, W) < 5 else 2
+    rng = np.random.default_rng(H * 1000 + W)
+    F = rng.uniform(0, 1, size=(2, H, W)).astype(np.float32)
+    G = rng.uniform(0, 1, size=(H, W)).astype(np.float32)
+    kw = dict(r=r, iters=2, sigma_r=0.3)
+    assert _maxerr(_gpu(api, F, G, 1.5, **kw), _oracle(F, G, 1.5, **kw)) <= TOL
+
+
+def test_many_channels_and_alias(api):
+    """C = 6 (channel groups of 4 + 2 against one guidance), and C = 1 with
+    the guidance tensor being the input tensor itself."""
+    import torch
+    F = np.concatenate([synth.rgb_scene(40, 45, seed=s, n_rect=8, n_disk=2) for s in (1, 2)])
+    G = synth.luminance(F[:3])
+    kw = dict(r=2, iters=1, sigma_r=0.1)
+    assert _maxerr(_gpu(api, F, G, 1.0, **kw), _oracle(F, G, 1.0, **kw)) <= TOL
+    f = torch.from_numpy(F[1]).cuda()
+    u = api.sgwls_filter(f, f, 1.0, **kw)
+    torch.cuda.synchronize()
+    assert _maxerr(u.cpu().numpy().astype(np.float64), _oracle(F[1:2], F[1], 1.0, **kw)) <= TOL
+
+
+def test_frac_weights(api):
+    """Eq. 2 fractional weights (alpha_s = alpha_r = 1.2, eps = 1e-4) with a
+    small lambda (the 1/eps range factor makes lambda * w large)."""
+    F = synth.rgb_scene(37, 52, seed=4, n_rect=10, n_disk=2)
+    G = synth.luminance(F)
+    for r in (1, 2):
+        kw = dict(r=r, iters=1, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+        err = _maxerr(_gpu(api, F, G, 0.002, **kw), _oracle(F, G, 0.002, **kw))
+        assert err <= TOL, (r, err)
+
+
+def test_single_pass_entry(api):
+    import torch
+    F = synth.rgb_scene(29, 47, seed=6, n_rect=6, n_disk=2)
+    G = synth.luminance(F)
+    f = torch.from_numpy(F).cuda()
+    g = torch.from_numpy(G).cuda()
+    for direction, d in ((0, COLUMN), (1, ROW)):
+        u = api.sgwls_filter_pass(f, g, 3.0, direction, r=2, sigma_r=0.2)
+        torch.cuda.synchronize()
+        ref = sgwls_pass(F.astype(np.float64), G.astype(np.float64), 3.0, Params(r=2, sigma_s=2.0, sigma_r=0.2), d)
+        assert _maxerr(u.cpu().numpy().astype(np.float64), ref) <= TOL
+
+
+def test_saved_checkpoints_and_iters0(api):
+    import torch
+    F = synth.rgb_scene(31, 36, seed=8, n_rect=6, n_disk=2)
+    G = synth.luminance(F)
+    f = torch.from_numpy(F).cuda()
+    g = torch.from_numpy(G).cuda()
+    T = 2
+    saved = torch.empty((2 * T,) + tuple(f.shape), device="cuda")
+    u = api.sgwls_filter(f, g, 1.0, r=1, iters=T, saved=saved)
+    torch.cuda.synchronize()
+    _, inputs = sgwls(F, G, 1.0, Params(r=1, iters=T), return_inputs=True)
+    for t in range(2 * T):
+        assert _maxerr(saved[t].cpu().numpy().astype(np.float64), inputs[t]) <= TOL
+    u0 = api.sgwls_filter(f, g, 1.0, r=1, iters=0)
+    torch.cuda.synchronize()
+    assert torch.equal(u0, f)
+
+
+@pytest.mark.parametrize("inter", ["f32", "bf16"])
+def test_bf16_storage(api, inter):
+    """BF16 input/guidance/output (FP32 elimination).  The oracle filters the
+    same BF16-rounded inputs; bound: one BF16 rounding of the output per
+    store (2^-9 on [0, 1]) per BF16 store, plus the FP32 tolerance."""
+    import torch
+    F = synth.rgb_scene(64, 80, seed=9, n_rect=12, n_disk=3)
+    G = synth.luminance(F)
+    fb = torch.from_numpy(F).to(torch.bfloat16)
+    gb = torch.from_numpy(G).to(torch.bfloat16)
+    T = 2
+    u = api.sgwls_filter(fb.cuda(), gb.cuda(), 1.0, r=2, iters=T, inter_storage=inter)
+    torch.cuda.synchronize()
+    ref = _oracle(fb.float().numpy(), gb.float().numpy(), 1.0, r=2, iters=T)
+    stores = 1 if inter == "f32" else 2 * T
+    bound = stores * 2.0 ** -9 + TOL
+    err = _maxerr(u.float().cpu().numpy().astype(np.float64), ref)
+    assert err <= bound, (err, bound)
+
+
+@pytest.mark.parametrize("lam", [0.5, 2.0])
+def test_config_rgb_1024x768_full(api, lam):
+    """Full size: 1024 x 768 RGB scene (200 rectangles, 50 disks, texture,
+    noise), guidance = luminance, r = 1, T = 3, range parameter 0.1; every
+    output pixel compared with the FP64 oracle."""
+    F = synth.rgb_scene(768, 1024, seed=2)
+    G = synth.luminance(F)
+    kw = dict(r=1, iters=3, sigma_r=0.1)
+    err = _maxerr(_gpu(api, F, G, lam, **kw), _oracle(F, G, lam, **kw))
+    assert err <= TOL, err
