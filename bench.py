@@ -119,6 +119,7 @@ def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return 0
+    os.environ.update({k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")})
     for i in range(args.warmup):
         _oracle_sample(REF_CROP_ROWS, 1, WL["lams"][i % 2], WL["seed"])
     times, mp = [], 0.0

@@ -4,6 +4,10 @@ Each translation unit under csrc/ is compiled in parallel, then linked into
 ``paper_1705_01674_gb300/libsgwls.so``.  Objects go to ``_build/`` next to
 this file.  A TU is rebuilt only when it or a header is newer than its
 object.  Usage: ``python -m paper_1705_01674_gb300.build [--force]``.
+
+Development shortcut: with ``SGWLS_RADII=1,2`` only those radii are
+compiled; the launchers of the other radii are built as stubs that return
+"unsupported".  The default (unset) builds every radius.
 """
 from __future__ import annotations
 
@@ -36,8 +40,21 @@ def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
+def _radius_of(src: str):
+    base = os.path.basename(src)
+    if base.startswith("sgwls_r") and base[7:-3].isdigit():
+        return int(base[7:-3])
+    return None
+
+
 def _compile(src: str, force: bool, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+    radii = os.environ.get("SGWLS_RADII")
+    r = _radius_of(src)
+    stub = bool(radii) and r is not None and str(r) not in radii.split(",")
+    tag = ".stub.o" if stub else ".o"
+    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", tag))
+    if stub:
+        extra = list(extra) + ["-DSGWLS_STUB_RADIUS"]
     if not force and os.path.exists(obj):
         newest = max(os.path.getmtime(p) for p in [src] + _headers())
         if os.path.getmtime(obj) >= newest:
@@ -55,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     workers = max(1, min(len(srcs), os.cpu_count() or 4))
     with cf.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(lambda s: _compile(s, force, list(extra)), srcs))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+    if True:  # linking is cheap; relink so stub/full object sets never mix up
         cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:

@@ -28,38 +28,41 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Resident-warp target used to size the chunking: 152 SMs x 16 warps.
 constexpr int kTargetWarps = 152 * 16;
-constexpr size_t kSmemPerWarpCap = 96 * 1024;
-constexpr size_t kSmemPerBlockCap = 200 * 1024;
-constexpr int kPMax = 512;
+constexpr size_t kSmemBlockTarget = 110 * 1024;   // two blocks per SM
+constexpr size_t kSmemBlockMax = 200 * 1024;
+constexpr int kGMax = 8;
 
 Plan make_plan(int L, int D, int r, int CC, int chunk_lines) {
-  const int n = 2 * r + 1;
-  const int NF = r + 1 + CC;
-  const size_t line_bytes = (size_t)n * NF * 32 * sizeof(float);
   const int bands = (D + (32 - 2 * r) - 1) / (32 - 2 * r);
-  int P = std::max(1, std::min(L, (kTargetWarps + bands - 1) / bands));
-  P = std::min(P, kPMax);
-  int h = (L + P - 1) / P;
+  // enough chunks for ~kTargetWarps warps in flight: h <= L * bands / target
+  int h = std::max(1, (int)(((long long)L * bands) / kTargetWarps));
+  // blocks of G = 8 chunk-warps, two blocks per SM: shrink h to fit
+  while (h > 1 && smem_recover(r, CC, h, kGMax) > kSmemBlockTarget) --h;
   if (chunk_lines > 0) h = std::min(chunk_lines, L);
-  const int hmax = std::max<int>(1, (int)(kSmemPerWarpCap / line_bytes));
-  if (h > hmax) h = hmax;
-  P = (L + h - 1) / h;
+  while (h > 1 && smem_recover(r, CC, h, 1) > kSmemBlockMax) --h;
+  h = std::min(h, L);
   Plan pl;
   pl.h = h;
-  pl.P = P;
-  const size_t warp_bytes = (size_t)h * line_bytes;
-  pl.warps_rec = (int)std::max<size_t>(1, std::min<size_t>(4, kSmemPerBlockCap / warp_bytes));
-  pl.warps_rec = std::min(pl.warps_rec, P);
-  pl.smem_rec = warp_bytes * pl.warps_rec;
+  pl.P = (L + h - 1) / h;
+  int G = 1;
+  while (G < kGMax && G < pl.P && smem_recover(r, CC, h, 2 * G) <= kSmemBlockMax &&
+         smem_summary(r, CC, h, 2 * G) <= kSmemBlockMax)
+    G *= 2;
+  pl.G = G;
+  pl.NG = (pl.P + G - 1) / G;
+  pl.smem_sum = smem_summary(r, CC, h, G);
+  pl.smem_rec = smem_recover(r, CC, h, G);
   return pl;
 }
 
 int n_fields(int r, int CC) { return 3 * r * r + 2 * r * CC; }
+int n_mfields(int r, int CC) { return 3 * r * r + r * CC; }
 
 struct Layout {
   size_t img_off, img_bytes;
   size_t summ_off, summ_bytes;
   size_t xsep_off, xsep_bytes;
+  size_t mdata_off, mdata_bytes;
   size_t total;
 };
 
@@ -67,24 +70,33 @@ struct Layout {
 Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   Layout lo;
   const int r = p->r;
-  const int CC = std::min(C, kGroupMax);
-  size_t summ = 0, xsep = 0;
+  size_t summ = 0, xsep = 0, mdata = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
     const int nsys = D - 2 * r;
-    const Plan pl = make_plan(L, D, r, CC, p->chunk_lines);
-    summ = std::max(summ, (size_t)pl.P * n_fields(r, CC) * nsys * sizeof(float));
-    xsep = std::max(xsep, (size_t)std::max(pl.P - 1, 1) * r * CC * nsys * sizeof(float));
+    for (int c0 = 0; c0 < C; c0 += kGroupMax) {
+      const int CC = std::min(kGroupMax, C - c0);
+      const Plan pl = make_plan(L, D, r, CC, p->chunk_lines);
+      summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
+      xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
+      mdata = std::max(mdata, (size_t)pl.NG * std::max(pl.G - 1, 1) * n_mfields(r, CC) * nsys * sizeof(float));
+    }
   }
-  const size_t img = (p->iters > 0) ? (size_t)C * H * W * dt_size(p->inter_storage) : 0;
+  // Intermediate estimates ping-pong between u and one workspace image when
+  // both have the same storage type; otherwise between two workspace images
+  // (u is then written by the last pass only).
+  const int n_img = (p->iters > 0) ? (p->inter_storage == p->storage ? 1 : 2) : 0;
+  const size_t img = (size_t)n_img * C * H * W * dt_size(p->inter_storage);
   lo.img_off = 0;
   lo.img_bytes = align256(img);
   lo.summ_off = lo.img_off + lo.img_bytes;
   lo.summ_bytes = align256(summ);
   lo.xsep_off = lo.summ_off + lo.summ_bytes;
   lo.xsep_bytes = align256(xsep);
-  lo.total = lo.xsep_off + lo.xsep_bytes;
+  lo.mdata_off = lo.xsep_off + lo.xsep_bytes;
+  lo.mdata_bytes = align256(mdata);
+  lo.total = lo.mdata_off + lo.mdata_bytes;
   return lo;
 }
 
@@ -180,7 +192,9 @@ sgwls_status copy_image(const void* src, int sdt, void* dst, int ddt, long long 
 
 // One pass along `dir` (Sec. 2.3, the four steps): out = pass(in).
 sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const void* g, int H, int W, int C,
-                      float lambda, const sgwls_params* p, int dir, float* summ, float* xsep, cudaStream_t st) {
+                      float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st) {
+  const Layout lo = make_layout(H, W, C, p);
+  char* wsb = static_cast<char*>(ws);
   const long long plane = (long long)H * W;
   PassArgs a;
   memset(&a, 0, sizeof(a));
@@ -195,8 +209,9 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
   a.L = dir == 0 ? H : W;
   a.D = dir == 0 ? W : H;
   a.nsys = a.D - 2 * p->r;
-  a.summ = summ;
-  a.xsep = xsep;
+  a.summ = reinterpret_cast<float*>(wsb + lo.summ_off);
+  a.xsep = reinterpret_cast<float*>(wsb + lo.xsep_off);
+  a.mdata = reinterpret_cast<float*>(wsb + lo.mdata_off);
   fill_weights(a, p, lambda);
   const PassLauncher launch = launcher_for(p->r);
   for (int c0 = 0; c0 < C; c0 += kGroupMax) {
@@ -204,11 +219,12 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     const Plan pl = make_plan(a.L, a.D, p->r, CC, p->chunk_lines);
     a.h = pl.h;
     a.P = pl.P;
+    a.ngroups = pl.NG;
     a.in = static_cast<const char*>(in) + (size_t)c0 * plane * dt_size(in_dt);
     a.out = static_cast<char*>(out) + (size_t)c0 * plane * dt_size(out_dt);
     cudaError_t e = launch(a, pl, CC, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 3 : 1), __ATOMIC_RELAXED);
+    __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? (pl.NG > 1 ? 3 : 2) : 1), __ATOMIC_RELAXED);
   }
   return SGWLS_OK;
 }
@@ -223,8 +239,6 @@ sgwls_status run_filter(const void* f, const void* g, void* u, int H, int W, int
 
   char* wsb = static_cast<char*>(ws);
   void* img = wsb + lo.img_off;
-  float* summ = reinterpret_cast<float*>(wsb + lo.summ_off);
-  float* xsep = reinterpret_cast<float*>(wsb + lo.xsep_off);
   const int npass = 2 * p->iters;
   const size_t inter_bytes = (size_t)count * dt_size(idt);
   if (saved) {
@@ -243,11 +257,14 @@ sgwls_status run_filter(const void* f, const void* g, void* u, int H, int W, int
     } else if (saved) {
       dst = static_cast<char*>(saved) + (size_t)(t + 1) * inter_bytes;
       dst_dt = idt;
-    } else {
+    } else if (idt == sdt) {
       dst = ((npass - 1 - t) & 1) ? img : u;
-      dst_dt = ((npass - 1 - t) & 1) ? idt : sdt;
+      dst_dt = sdt;
+    } else {
+      dst = static_cast<char*>(img) + (size_t)(t & 1) * inter_bytes;
+      dst_dt = idt;
     }
-    sgwls_status s = run_pass(cur, cur_dt, dst, dst_dt, g, H, W, C, lambda, p, dir, summ, xsep, st);
+    sgwls_status s = run_pass(cur, cur_dt, dst, dst_dt, g, H, W, C, lambda, p, dir, ws, st);
     if (s != SGWLS_OK) return s;
     cur = dst;
     cur_dt = dst_dt;
@@ -320,9 +337,7 @@ sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int
   if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
   const Layout lo = make_layout(H, W, C, p);
   if (!ws || ws_bytes < lo.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
-  char* wsb = static_cast<char*>(ws);
-  return run_pass(f, p->storage, u, p->storage, g, H, W, C, lambda, p, direction,
-                  reinterpret_cast<float*>(wsb + lo.summ_off), reinterpret_cast<float*>(wsb + lo.xsep_off),
+  return run_pass(f, p->storage, u, p->storage, g, H, W, C, lambda, p, direction, ws,
                   static_cast<cudaStream_t>(stream));
 }
 

@@ -15,6 +15,9 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace sgwls {
 
 constexpr int kRMax = 8;
@@ -35,6 +38,7 @@ struct PassArgs {
   int nsys;            // number of centres: D - 2r (step 1)
   int h;               // lines per chunk
   int P;               // chunks per subsystem
+  int ngroups;         // chunk groups (one block of G chunks each)
   float lam;           // lambda
   int weight;          // 0 exp, 1 frac
   float range_k;       // exp: -log2(e) / (2 sigma_r^2);  frac: alpha_r
@@ -42,8 +46,10 @@ struct PassArgs {
   // lambda * spatial factor of the pair (p, p+t) for j = p % n, t = 1..r:
   // sp[j * r + t - 1]
   float sp[(2 * kRMax + 1) * kRMax];
-  float* summ;         // chunk summaries  [P][nfields][nsys]
-  float* xsep;         // separator values [P-1][r*CC][nsys]
+  float* summ;         // group 2-ports     [NG][Fields::N][nsys]
+  float* xsep;         // group separators  [NG-1][r*CC][nsys]
+  float* mdata;        // merge factors     [NG][G-1][MFields::N][nsys]
+  int early_stage;     // k_recover may stage its tile before griddep_wait
 };
 
 __device__ __forceinline__ float ld_px(const void* base, long long idx, int dt) {
@@ -65,11 +71,26 @@ __device__ __forceinline__ long long pix_index(const PassArgs& a, int line, int 
   return a.dir == 0 ? (long long)line * a.W + off : (long long)off * a.W + line;
 }
 
-// Range factor of Eq. 2 for the guidance difference dg.
+__device__ __forceinline__ float fast_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Range factor of Eq. 2 for the guidance difference dg: exp weights use the
+// hardware base-2 exponential on dg^2 * (-log2(e) / (2 sigma_r^2)).
 __device__ __forceinline__ float range_factor(const PassArgs& a, float dg) {
-  if (a.weight == 0) return exp2f(dg * dg * a.range_k);
+  if (a.weight == 0) return fast_ex2(dg * dg * a.range_k);
   return 1.0f / (powf(fabsf(dg), a.range_k) + a.eps);
 }
+
+// Programmatic dependent launch: wait for the preceding kernel of the stream
+// to complete (its memory is then visible), and allow the next kernel to be
+// scheduled.  Every kernel here calls launch_dependents only after its own
+// wait, so a kernel that runs code before its wait may read anything written
+// two or more kernels earlier.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 __device__ __forceinline__ float fast_rcp(float x) {
   float y;

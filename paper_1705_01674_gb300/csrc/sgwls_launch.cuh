@@ -8,29 +8,76 @@ namespace sgwls {
 struct Plan {
   int h;          // lines per chunk
   int P;          // chunks per subsystem
-  int warps_rec;  // warps (chunks) per k_recover block
-  size_t smem_rec;
+  int G;          // chunks (warps) per block
+  int NG;         // chunk groups = ceil(P / G)
+  size_t smem_sum, smem_rec;
 };
+
+// Shared memory of the two tiled kernels for a plan (bytes).
+inline size_t tile_floats(int r, int CC, int h, int G) { return (size_t)(CC + 1) * (G * h + 2) * (33 + 2 * r); }
+inline size_t smem_summary(int r, int CC, int h, int G) {
+  return 4 * (tile_floats(r, CC, h, G) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
+}
+inline size_t smem_recover(int r, int CC, int h, int G) {
+  const int n = 2 * r + 1;
+  const size_t merge = (size_t)(G - 1) * (3 * r * r + r * CC) * 32 + 2 * (size_t)r * CC * 32;
+  return 4 * (tile_floats(r, CC, h, G) + (size_t)G * 2 * r * CC * 32 + merge + (size_t)G * h * n * (r + CC) * 32);
+}
+
+constexpr size_t kReducedSmemMax = 96 * 1024;
 
 // Launches the kernels of one pass for a group of CC <= 4 channels.
 using PassLauncher = cudaError_t (*)(const PassArgs&, const Plan&, int CC, cudaStream_t);
+
+// Launch with programmatic stream serialization (the kernels synchronise
+// with griddep_wait before they consume the previous kernel's output).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 template <int R, int CC>
 cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   static_assert(R >= 1 && R <= kRMax, "radius");
   constexpr int OB = 32 - 2 * R;
-  if (pl.smem_rec > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_recover<R, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pl.smem_rec);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e;
+  PassArgs b = a;
+  b.early_stage = pl.NG > 1 ? 1 : 0;   // k_recover follows k_reduced
   if (a.P > 1) {
-    dim3 bs(32, 4), gs((a.nsys + 31) / 32, (a.P + 3) / 4);
-    k_summary<R, CC><<<gs, bs, 0, st>>>(a);
-    k_reduced<R, CC><<<(a.nsys + 127) / 128, 128, 0, st>>>(a);
+    if ((e = set_smem(k_summary<R, CC>, pl.smem_sum)) != cudaSuccess) return e;
+    e = launch_pdl(k_summary<R, CC>, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), pl.smem_sum, st, b);
+    if (e != cudaSuccess) return e;
+    if (pl.NG > 1) {
+      const size_t red = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
+      if (red <= kReducedSmemMax) {
+        if ((e = set_smem(k_reduced<R, CC, true>, red)) != cudaSuccess) return e;
+        e = launch_pdl(k_reduced<R, CC, true>, dim3((a.nsys + 31) / 32), dim3(32, 8), red, st, b);
+      } else {
+        e = launch_pdl(k_reduced<R, CC, false>, dim3((a.nsys + 31) / 32), dim3(32, 1), 0, st, b);
+      }
+      if (e != cudaSuccess) return e;
+    }
   }
-  dim3 br(32, pl.warps_rec), gr((a.D + OB - 1) / OB, (a.P + pl.warps_rec - 1) / pl.warps_rec);
-  k_recover<R, CC><<<gr, br, pl.smem_rec, st>>>(a);
+  if ((e = set_smem(k_recover<R, CC>, pl.smem_rec)) != cudaSuccess) return e;
+  e = launch_pdl(k_recover<R, CC>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), pl.smem_rec, st, b);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -5,8 +5,8 @@
 // A_s is strictly diagonally dominant (diagonal minus the off-diagonal sum is
 // 1, from the Eq. 4 form), so an FP32 LDL^T without pivoting is stable.  The
 // paper factors each subsystem serially (its r-band LU, Eqs. 9-20); a GPU
-// needs more parallelism than one thread per subsystem, so each subsystem is
-// split along its lines into P chunks and solved exactly by one level of
+// needs far more parallelism than one thread per subsystem, so each
+// subsystem is split along its lines into P chunks and solved exactly by
 // Schur-complement (nested dissection) reduction:
 //
 //   chunk c covers lines [c h, min((c+1) h, L)), vector entries [b, end);
@@ -14,29 +14,40 @@
 //   c+1; the rest is the interior I_c = [b, e).  Interiors couple only to
 //   the separators on both sides (bandwidth r < 2r+1 = entries per line).
 //
-//   k_summary   one thread per (subsystem, chunk): factors A(I_c) = L D L^T,
-//               forms Y_T = L^{-1} A(I_c, S_{c-1}), Y_B = L^{-1} A(I_c, S_c),
-//               y = L^{-1} f(I_c) and writes the chunk's Schur contributions
-//                 KTT = Y_T' D^-1 Y_T, KTB = Y_T' D^-1 Y_B,
-//                 DS  = A(S_c, S_c) - Y_B' D^-1 Y_B,
-//                 HT  = Y_T' D^-1 y,   G = f(S_c) - Y_B' D^-1 y.
-//   k_reduced   one thread per subsystem: block Cholesky of the reduced block
-//               tridiagonal system on the separators (r x r blocks)
-//                 diag_c = DS_c - KTT_{c+1},  off_{c,c+1} = -KTB_{c+1},
-//                 rhs_c  = G_c - HT_{c+1},
-//               and back substitution -> separator values x(S_c).
-//   k_recover   one warp per (32 neighbouring centres, chunk): refactors the
-//               interior, solves A(I_c) x = f - A(I,S) x(S) (forward sweep
-//               into shared memory, backward sweep), writes the solution back
-//               into the strip and averages each pixel's 2r+1 values across
-//               the neighbouring centres' lanes with warp shuffles (steps 3-4
-//               of Sec. 2.3), then stores the output line by line.
+// Eliminating a chunk's interior leaves a "2-port" on (S_{c-1}, S_c):
+//   KTT = Y_T' D^-1 Y_T,  KTB = Y_T' D^-1 Y_B,  DS = A(S_c,S_c) - Y_B' D^-1 Y_B,
+//   HT  = Y_T' D^-1 y,    GS  = f(S_c) - Y_B' D^-1 y,
+// with A(I,I) = L D L^T, Y_T = L^-1 A(I,S_{c-1}), Y_B = L^-1 A(I,S_c),
+// y = L^-1 f(I).  Consecutive 2-ports merge by eliminating their shared
+// separator (an associative operation), so the reduction is hierarchical:
+//
+//   k_summary   block = 32 neighbouring subsystems (lanes) x G chunks (warps).
+//               The block stages its strip tile (estimate planes and guidance)
+//               in shared memory, every thread eliminates its chunk's
+//               interior (forward sweep), then warp 0 merges the block's G
+//               chunk 2-ports into one group 2-port, keeping the merge
+//               factors for the back-fill.
+//   k_reduced   one thread per subsystem: block Cholesky of the block
+//               tridiagonal system on the group separators (r x r blocks),
+//               forward elimination and back substitution.
+//   k_recover   block = 32 neighbouring centres x G chunks.  Warp 0 back-fills
+//               the separators inside the group from the merge factors; every
+//               thread then solves its interior with known separators
+//               (forward sweep into shared memory, backward sweep), writes the
+//               solution back into the strip and averages each pixel's 2r+1
+//               values across the neighbouring centres' lanes with warp
+//               shuffles (steps 3-4 of Sec. 2.3), one output line at a time.
+//
+// The sweeps run one line of the vector at a time with the line's parity
+// (snake direction) and its first/last role fixed at compile time, so every
+// index inside a line is static.
 #pragma once
 
 #include "sgwls_common.cuh"
 
 namespace sgwls {
 
+// Chunk summary fields (chunk 2-port, and group 2-port in the same format).
 template <int R, int CC>
 struct Fields {
   static constexpr int KTT = 0;
@@ -47,47 +58,204 @@ struct Fields {
   static constexpr int N = 3 * R * R + 2 * R * CC;
 };
 
-// Loads the guidance values of one line in vector order (entry j of the line).
-template <int R>
-__device__ __forceinline__ void load_g_line(const PassArgs& a, int k, int line, float (&gl)[2 * R + 1]) {
-  constexpr int n = 2 * R + 1;
-  if (line < 0 || line >= a.L) {
-#pragma unroll
-    for (int j = 0; j < n; ++j) gl[j] = 0.f;
-    return;
-  }
-  const bool rev = line & 1;
-#pragma unroll
-  for (int j = 0; j < n; ++j) {
-    const int off = rev ? (k + R - j) : (k - R + j);
-    gl[j] = ld_px(a.g, pix_index(a, line, off), a.g_dt);
-  }
-}
-
+// Merge factors kept for the back-fill: Cholesky factor of the eliminated
+// separator block, U = Lm^-1 E_YX, V = Lm^-1 E_YZ, w = Lm^-1 rhs_Y.
 template <int R, int CC>
-__device__ __forceinline__ void load_f_line(const PassArgs& a, int k, int line, float (&fl)[2 * R + 1][CC]) {
-  constexpr int n = 2 * R + 1;
-  const bool rev = line & 1;
-#pragma unroll
-  for (int j = 0; j < n; ++j) {
-    const int off = rev ? (k + R - j) : (k - R + j);
-    const long long idx = pix_index(a, line, off);
-#pragma unroll
-    for (int ch = 0; ch < CC; ++ch) fl[j][ch] = ld_px(a.in, idx + ch * a.plane, a.in_dt);
+struct MFields {
+  static constexpr int LM = 0;
+  static constexpr int U = R * R;
+  static constexpr int V = 2 * R * R;
+  static constexpr int W = 3 * R * R;
+  static constexpr int N = 3 * R * R + R * CC;
+};
+
+// ---------------------------------------------------------------------------
+// Shared-memory strip tile: planes 0..CC-1 = estimate channels, plane CC =
+// guidance; tile[(plane * ntl + tl) * pitch + col] holds (line tl0 + tl,
+// across-offset off0 + col), zero outside the image.  pitch is odd so the
+// transposed staging of the row direction is free of bank conflicts.
+struct Tile {
+  float* p;
+  int tl0, ntl, off0, pitch;
+  __device__ __forceinline__ const float* row(int plane, int line) const {
+    return p + (plane * ntl + (line - tl0)) * pitch;
+  }
+};
+
+// Mixed storage types (BF16 guidance with FP32 estimates): plain loop.
+template <int CC>
+__device__ __forceinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, int ncol) {
+  const int nthreads = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int per_plane = t.ntl * ncol;
+  for (int idx = tid; idx < (CC + 1) * per_plane; idx += nthreads) {
+    const int pl = idx / per_plane;
+    const int rest = idx - pl * per_plane;
+    const int tl = rest / ncol, col = rest - tl * ncol;
+    const int line = t.tl0 + tl, off = t.off0 + col;
+    float v = 0.f;
+    if (line >= 0 && line < a.L && off >= 0 && off < a.D) {
+      const long long pix = pix_index(a, line, off);
+      v = pl < CC ? ld_px(a.in, pix + pl * a.plane, a.in_dt) : ld_px(a.g, pix, a.g_dt);
+    }
+    t.p[(pl * t.ntl + tl) * t.pitch + col] = v;
   }
 }
 
-// lambda * w(p, p+t), t = 1..R, for entry j of the current line (Eq. 2).
+// Loads one value of plane `pl` (a.in channels, then the guidance).
+template <bool F32>
+__device__ __forceinline__ float ld_plane(const void* base, long long idx) {
+  if (F32) return __ldg(reinterpret_cast<const float*>(base) + idx);
+  const unsigned short raw = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+  return __uint_as_float(static_cast<unsigned>(raw) << 16);
+}
+
+// Stages planes x lines x ncol values, zero outside the image.  Column
+// direction: lanes along the offsets (contiguous in memory), warps over the
+// lines.  Row direction: lanes along the lines (contiguous in memory), warps
+// over the offsets.  Each thread issues U loads before its stores.
+template <int CC, bool F32>
+__device__ __forceinline__ void stage_tile_t(const PassArgs& a, const Tile& t, int ncol) {
+  const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
+  constexpr int U = 4;
+#pragma unroll 1
+  for (int pl = 0; pl <= CC; ++pl) {
+    const char* base = static_cast<const char*>(pl < CC ? a.in : a.g) +
+                       (pl < CC ? (size_t)pl * a.plane * (F32 ? 4 : 2) : 0);
+    float* dplane = t.p + pl * t.ntl * t.pitch;
+    if (a.dir == 0) {
+      // rows = lines; 2 columns per lane cover ncol <= 64
+      for (int tl0 = warp; tl0 < t.ntl; tl0 += U * nw) {
+        float v[U][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int tl = tl0 + u * nw;
+          const int line = t.tl0 + tl;
+          const bool lok = tl < t.ntl && line >= 0 && line < a.L;
+          const char* rowp = base + (size_t)(lok ? line : 0) * a.W * (F32 ? 4 : 2);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int off = t.off0 + lane + 32 * k;
+            const bool ok = lok && lane + 32 * k < ncol && off >= 0 && off < a.D;
+            v[u][k] = ok ? ld_plane<F32>(rowp, off) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int tl = tl0 + u * nw;
+          if (tl < t.ntl) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+              if (lane + 32 * k < ncol) dplane[tl * t.pitch + lane + 32 * k] = v[u][k];
+          }
+        }
+      }
+    } else {
+      // rows of the image = offsets; lanes along the lines
+      for (int c0 = warp; c0 < ncol; c0 += U * nw) {
+        for (int tb = 0; tb < t.ntl; tb += 32) {
+          const int tl = tb + lane;
+          const int line = t.tl0 + tl;
+          const bool lok = tl < t.ntl && line >= 0 && line < a.L;
+          float v[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int col = c0 + u * nw;
+            const int off = t.off0 + col;
+            const bool ok = lok && col < ncol && off >= 0 && off < a.D;
+            const char* rowp = base + (size_t)(ok ? off : 0) * a.W * (F32 ? 4 : 2);
+            v[u] = ok ? ld_plane<F32>(rowp, line) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int col = c0 + u * nw;
+            if (col < ncol && tl < t.ntl) dplane[tl * t.pitch + col] = v[u];
+          }
+        }
+      }
+    }
+  }
+}
+
+// FP32 tiles: every element is an asynchronous 4-byte global->shared copy
+// (cp.async; zero-filled outside the image), all of a thread's copies in
+// flight at once.  The caller waits with cp_async_wait_all + __syncthreads.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int CC>
+__device__ __forceinline__ void stage_tile_async(const PassArgs& a, const Tile& t, int ncol) {
+  const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
+#pragma unroll 1
+  for (int pl = 0; pl <= CC; ++pl) {
+    const float* base = static_cast<const float*>(pl < CC ? a.in : a.g) + (pl < CC ? (size_t)pl * a.plane : 0);
+    float* dplane = t.p + pl * t.ntl * t.pitch;
+    if (a.dir == 0) {
+      for (int tl = warp; tl < t.ntl; tl += nw) {
+        const int line = t.tl0 + tl;
+        const bool lok = line >= 0 && line < a.L;
+        const float* rowp = base + (size_t)(lok ? line : 0) * a.W;
+        for (int col = lane; col < ncol; col += 32) {
+          const int off = t.off0 + col;
+          const bool ok = lok && off >= 0 && off < a.D;
+          cp_async4(dplane + tl * t.pitch + col, ok ? rowp + off : base, ok);
+        }
+      }
+    } else {
+      for (int col = warp; col < ncol; col += nw) {
+        const int off = t.off0 + col;
+        const bool ook = off >= 0 && off < a.D;
+        const float* rowp = base + (size_t)(ook ? off : 0) * a.W;
+        for (int tl = lane; tl < t.ntl; tl += 32) {
+          const int line = t.tl0 + tl;
+          const bool ok = ook && line >= 0 && line < a.L;
+          cp_async4(dplane + tl * t.pitch + col, ok ? rowp + line : base, ok);
+        }
+      }
+    }
+  }
+}
+
+// The tile planes share one storage type when the estimate and the guidance
+// do (always, except for a BF16 guidance with FP32 intermediates).
+template <int CC>
+__device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t, int ncol) {
+  if (a.in_dt == DT_F32 && a.g_dt == DT_F32)
+    stage_tile_async<CC>(a, t, ncol);
+  else if (a.in_dt == DT_BF16 && a.g_dt == DT_BF16)
+    stage_tile_t<CC, false>(a, t, ncol);
+  else
+    stage_tile_mixed<CC>(a, t, ncol);
+}
+
+// Column (relative to the lane's strip start) of entry j of a line.
+template <int R, bool ODD>
+__device__ __forceinline__ constexpr int ecol(int j) { return ODD ? 2 * R - j : j; }
+
+// Entries of a line handled per loop trip: all of them (static indices) for
+// r <= 3, one (a rolled loop, smaller code) for larger r.
 template <int R>
-__device__ __forceinline__ void forward_weights(const PassArgs& a, int j, int p, int s,
-                                                const float (&gc)[2 * R + 1], const float (&gn)[2 * R + 1],
-                                                float (&wf)[R]) {
+struct LineUnroll {
+  static constexpr int value = R <= 3 ? 2 * R + 1 : 1;
+};
+
+// lambda * w(p, p+t), t = 1..R, for entry j of a line (Eq. 2).  gr / gnr:
+// guidance rows of this line and the next (lane-relative); `end_ok`: the next
+// line exists (pairs that cross into it are inside the vector).
+template <int R, bool ODD>
+__device__ __forceinline__ void forward_weights(const PassArgs& a, const float* gr, const float* gnr, int j,
+                                                bool end_ok, float (&wf)[R]) {
   constexpr int n = 2 * R + 1;
+  const float g0 = gr[ecol<R, ODD>(j)];
 #pragma unroll
   for (int t = 1; t <= R; ++t) {
-    const float gq = (j + t < n) ? gc[(j + t) % n] : gn[(j + t) % n];
-    const float w = a.sp[j * R + t - 1] * range_factor(a, gc[j] - gq);
-    wf[t - 1] = (p + t < s) ? w : 0.f;
+    const int jt = j + t;
+    const float gq = jt < n ? gr[ecol<R, ODD>(jt)] : gnr[ecol<R, !ODD>(jt - n)];
+    const float w = a.sp[j * R + t - 1] * range_factor(a, g0 - gq);
+    wf[t - 1] = (jt < n || end_ok) ? w : 0.f;
   }
 }
 
@@ -102,9 +270,8 @@ __device__ __forceinline__ void push_weights(float (&wh)[R][R], const float (&wf
 }
 
 // One LDL^T row for entry p.  wh[u-1][t-1] = lambda w(p-u, p-u+t); Lw[u-1][v-1]
-// = L[p-u, p-u-v]; Dw[u-1] = 1/D[p-u].  `lim` = number of previous entries
-// that belong to the factored interior (entries p-t with t > lim are outside).
-// Returns Lrow[t-1] = L[p, p-t] and 1/D[p].
+// = L[p-u, p-u-v]; Dw[u-1] = 1/D[p-u].  Entries p-t with t > lim are outside
+// the factored interior.  Returns Lrow[t-1] = L[p, p-t] and 1/D[p].
 template <int R>
 __device__ __forceinline__ float ldl_row(float diag, const float (&wh)[R][R], const float (&Lw)[R][R],
                                          const float (&Dw)[R], int lim, float (&Lrow)[R]) {
@@ -147,7 +314,7 @@ __device__ __forceinline__ void push_vec(float (&w)[R][K], const float (&x)[K]) 
   for (int i = 0; i < K; ++i) w[0][i] = x[i];
 }
 
-// y = rhs - sum_t L[p, p-t] win[t-1]  (forward substitution, K columns)
+// y -= sum_t L[p, p-t] win[t-1]  (forward substitution, K columns)
 template <int R, int K>
 __device__ __forceinline__ void fwd_subst(const float (&Lrow)[R], const float (&win)[R][K], float (&y)[K]) {
 #pragma unroll
@@ -156,8 +323,39 @@ __device__ __forceinline__ void fwd_subst(const float (&Lrow)[R], const float (&
     for (int i = 0; i < K; ++i) y[i] -= Lrow[t] * win[t][i];
 }
 
+// Runs body(odd, first, last, line) over the lines [line0, line1) with the
+// parity and the first/last role as compile-time constants.
+template <typename Body>
+__device__ __forceinline__ void for_lines(int line0, int line1, Body&& body) {
+  auto dispatch = [&](auto first, auto last, int line) {
+    if (line & 1)
+      body(std::true_type{}, first, last, line);
+    else
+      body(std::false_type{}, first, last, line);
+  };
+  if (line1 - line0 == 1) {
+    dispatch(std::true_type{}, std::true_type{}, line0);
+    return;
+  }
+  dispatch(std::true_type{}, std::false_type{}, line0);
+  for (int line = line0 + 1; line < line1 - 1; ++line) dispatch(std::false_type{}, std::false_type{}, line);
+  dispatch(std::false_type{}, std::true_type{}, line1 - 1);
+}
+
+// Backward order: body(odd, last, line) over lines line1-1 down to line0.
+template <typename Body>
+__device__ __forceinline__ void for_lines_rev(int line0, int line1, Body&& body) {
+  auto dispatch = [&](auto last, int line) {
+    if (line & 1)
+      body(std::true_type{}, last, line);
+    else
+      body(std::false_type{}, last, line);
+  };
+  dispatch(std::true_type{}, line1 - 1);
+  for (int line = line1 - 2; line >= line0; --line) dispatch(std::false_type{}, line);
+}
+
 // ---------------------------------------------------------------------------
-// Chunk geometry shared by the kernels.
 struct Chunk {
   int line0, line1;     // lines [line0, line1)
   int b, e, end;        // interior [b, e), chunk entries [b, end)
@@ -178,166 +376,30 @@ __device__ __forceinline__ Chunk make_chunk(const PassArgs& a, int c) {
   return ch;
 }
 
-// ---------------------------------------------------------------------------
-// k_summary: forward sweep of one chunk and its Schur contributions.
+// Weights of the line above a chunk (its top separator's line) into wh.
 template <int R, int CC>
-__global__ void __launch_bounds__(128) k_summary(const PassArgs a) {
+__device__ __forceinline__ void prologue_weights(const PassArgs& a, const Tile& t, int lane, int line,
+                                                 float (&wh)[R][R]) {
   constexpr int n = 2 * R + 1;
-  using F = Fields<R, CC>;
-  const int sys = blockIdx.x * 32 + threadIdx.x;
-  const int c = blockIdx.y * blockDim.y + threadIdx.y;
-  if (sys >= a.nsys || c >= a.P) return;
-  const int k = sys + R;
-  const int s = a.L * n;
-  const Chunk q = make_chunk<R>(a, c);
-
-  float wh[R][R] = {};
-  float Lw[R][R] = {};
-  float Dw[R] = {};
-  float yw[R][CC] = {};
-  float YTw[R][R] = {};
-  float YBw[R][R] = {};
-  float KTT[R][R] = {}, KTB[R][R] = {}, KBB[R][R] = {};
-  float HT[R][CC] = {}, HB[R][CC] = {};
-  float DS[R][R] = {};
-  float FS[R][CC] = {};
-  float gc[n], gn[n];
-  float wf[R];
-
-  if (q.top) {  // weights of the line above the chunk (the top separator's line)
-    load_g_line<R>(a, k, q.line0 - 1, gc);
-    load_g_line<R>(a, k, q.line0, gn);
-#pragma unroll
+  auto pro = [&](auto odd) {
+    constexpr bool ODD = decltype(odd)::value;
+    const float* gr = t.row(CC, line) + lane;
+    const float* gnr = t.row(CC, line + 1) + lane;
+    float wf[R];
+#pragma unroll LineUnroll<R>::value
     for (int j = 0; j < n; ++j) {
-      forward_weights<R>(a, j, (q.line0 - 1) * n + j, s, gc, gn, wf);
+      forward_weights<R, ODD>(a, gr, gnr, j, true, wf);
       push_weights<R>(wh, wf);
     }
-  }
-  load_g_line<R>(a, k, q.line0, gc);
-  for (int line = q.line0; line < q.line1; ++line) {
-    load_g_line<R>(a, k, line + 1, gn);
-    float fl[n][CC];
-    load_f_line<R, CC>(a, k, line, fl);
-    const bool first = line == q.line0;
-    const bool last = line == q.line1 - 1;
-#pragma unroll
-    for (int j = 0; j < n; ++j) {
-      const int p = line * n + j;
-      forward_weights<R>(a, j, p, s, gc, gn, wf);
-      float diag = 1.f;
-#pragma unroll
-      for (int t = 0; t < R; ++t) diag += wf[t] + wh[t][t];
-      const bool sep = last && q.bot && (j >= n - R);
-      if (!sep) {
-        const int lim = first ? j : R;
-        float Lrow[R];
-        const float dinv = ldl_row<R>(diag, wh, Lw, Dw, lim, Lrow);
-        float y[CC];
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) y[ch] = fl[j][ch];
-        fwd_subst<R, CC>(Lrow, yw, y);
-        float z[CC];
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) z[ch] = y[ch] * dinv;
-        float YT[R];
-        if (q.top) {
-          // E_T[p][i] = A[p, b-R+i] = -lambda w(p-t, p), t = j + R - i (first line)
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const int t = j + R - i;
-            YT[i] = (first && t >= 1 && t <= R) ? -wh[(t - 1) % R][(t - 1) % R] : 0.f;
-          }
-          fwd_subst<R, R>(Lrow, YTw, YT);
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float yd = YT[i] * dinv;
-#pragma unroll
-            for (int m = 0; m < R; ++m) KTT[i][m] += yd * YT[m];
-#pragma unroll
-            for (int ch = 0; ch < CC; ++ch) HT[i][ch] += YT[i] * z[ch];
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < R; ++i) YT[i] = 0.f;
-        }
-        float YB[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) YB[i] = 0.f;
-        if (q.bot && last && j >= n - 2 * R) {
-          // E_B[p][i] = A[p, e+i] = -lambda w(p, p+t), t = (n - R - j) + i
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const int t = (n - R - j) + i;
-            YB[i] = (t >= 1 && t <= R) ? -wf[(t - 1) % R] : 0.f;
-          }
-          fwd_subst<R, R>(Lrow, YBw, YB);
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float yd = YB[i] * dinv;
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-              KBB[i][m] += yd * YB[m];
-              KTB[m][i] += yd * YT[m];
-            }
-#pragma unroll
-            for (int ch = 0; ch < CC; ++ch) HB[i][ch] += YB[i] * z[ch];
-          }
-        }
-        push_factor<R>(Lw, Dw, Lrow, dinv);
-        push_vec<R, CC>(yw, y);
-        push_vec<R, R>(YTw, YT);
-        push_vec<R, R>(YBw, YB);
-      } else {
-        const int i = j - (n - R);
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-          if (m == i) DS[i][i] = diag;
-          // A[e+i, e+i-t] = -lambda w(e+i-t, e+i), t = i - m
-          if (m < i) {
-            const int t = i - m;
-            DS[i][m] = -wh[(t - 1) % R][(t - 1) % R];
-            DS[m][i] = DS[i][m];
-          }
-        }
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) FS[i][ch] = fl[j][ch];
-      }
-      push_weights<R>(wh, wf);
-    }
-#pragma unroll
-    for (int j = 0; j < n; ++j) gc[j] = gn[j];
-  }
-
-  float* base = a.summ + (long long)c * F::N * a.nsys + sys;
-  auto put = [&](int field, float v) { base[(long long)field * a.nsys] = v; };
-  if (q.top) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        put(F::KTT + i * R + m, KTT[i][m]);
-        put(F::KTB + i * R + m, KTB[i][m]);
-      }
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) put(F::HT + i * CC + ch, HT[i][ch]);
-    }
-  }
-  if (q.bot) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-#pragma unroll
-      for (int m = 0; m < R; ++m) put(F::DS + i * R + m, DS[i][m] - KBB[i][m]);
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) put(F::GS + i * CC + ch, FS[i][ch] - HB[i][ch]);
-    }
-  }
+  };
+  if (line & 1) pro(std::true_type{}); else pro(std::false_type{});
 }
 
 // ---------------------------------------------------------------------------
-// Small dense helpers for the reduced solve (R x R blocks, registers).
+// Small dense helpers (R x R blocks in registers).
 
-// In-place Cholesky M = L L^T (lower triangle of M overwritten by L; the
-// diagonal holds 1/L_ii for cheap solves).
+// In-place Cholesky M = Lm Lm^T (lower triangle holds Lm, the diagonal holds
+// 1 / Lm_ii).
 template <int R>
 __device__ __forceinline__ void chol_inplace(float (&M)[R][R]) {
 #pragma unroll
@@ -357,7 +419,7 @@ __device__ __forceinline__ void chol_inplace(float (&M)[R][R]) {
   }
 }
 
-// X <- L^{-1} X for the Cholesky factor stored by chol_inplace.
+// X <- Lm^{-1} X
 template <int R, int K>
 __device__ __forceinline__ void lsolve(const float (&Lm)[R][R], float (&X)[R][K]) {
 #pragma unroll
@@ -372,7 +434,7 @@ __device__ __forceinline__ void lsolve(const float (&Lm)[R][R], float (&X)[R][K]
   }
 }
 
-// X <- L^{-T} X
+// X <- Lm^{-T} X
 template <int R, int K>
 __device__ __forceinline__ void ltsolve(const float (&Lm)[R][R], float (&X)[R][K]) {
 #pragma unroll
@@ -387,54 +449,343 @@ __device__ __forceinline__ void ltsolve(const float (&Lm)[R][R], float (&X)[R][K
   }
 }
 
-// k_reduced: block Cholesky of the separator system, one thread per subsystem.
-// Overwrites DS_c with the factor L_c, GS_c with w_c = L_c^{-1}(...), KTB_c with
-// Z_c = L_{c-1}^{-1} (-KTB_c), and writes the separator values to xsep.
-template <int R, int CC>
-__global__ void __launch_bounds__(128) k_reduced(const PassArgs a) {
-  using F = Fields<R, CC>;
-  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sys >= a.nsys || a.P < 2) return;
-  const long long ns = a.nsys;
-  auto fld = [&](int c, int field) -> float* { return a.summ + ((long long)c * F::N + field) * ns + sys; };
+// C (+)= sign * A^T B for R x R A and R x K B.
+template <int R, int K>
+__device__ __forceinline__ void add_atb(float (&Cm)[R][K], const float (&A)[R][R], const float (&B)[R][K], float sign) {
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float v = 0.f;
+#pragma unroll
+      for (int l = 0; l < R; ++l) v += A[l][i] * B[l][k];
+      Cm[i][k] += sign * v;
+    }
+}
 
-  float Lp[R][R];    // L_{c-1}
-  float wp[R][CC];   // w_{c-1}
-  for (int c = 0; c <= a.P - 2; ++c) {
-    float M[R][R];
-    float rhs[R][CC];
+// Strided access to the field block of one lane: base[field * stride].
+struct Strided {
+  float* base;
+  int stride;
+  __device__ __forceinline__ float& operator[](int field) const { return base[field * stride]; }
+};
+struct StridedG {
+  float* base;
+  long long stride;
+  __device__ __forceinline__ float& operator[](int field) const { return base[field * stride]; }
+};
+
+// ---------------------------------------------------------------------------
+// Forward sweep of one chunk for the summary: eliminates the interior and
+// writes its 2-port to `out`.
+template <int R, int CC>
+__device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int lane, int c, Strided out) {
+  constexpr int n = 2 * R + 1;
+  using F = Fields<R, CC>;
+  const Chunk q = make_chunk<R>(a, c);
+  const int pstride = t.ntl * t.pitch;
+
+  float wh[R][R] = {};
+  float Lw[R][R] = {};
+  float Dw[R] = {};
+  float yw[R][CC] = {};
+  float YTw[R][R] = {};
+  float YBw[R][R] = {};
+  float KTT[R][R] = {}, KTB[R][R] = {}, KBB[R][R] = {};
+  float HT[R][CC] = {}, HB[R][CC] = {};
+  float DS[R][R] = {};
+  float FS[R][CC] = {};
+
+  if (q.top) prologue_weights<R, CC>(a, t, lane, q.line0 - 1, wh);
+
+  for_lines(q.line0, q.line1, [&](auto odd, auto first, auto last, int line) {
+    constexpr bool ODD = decltype(odd)::value;
+    constexpr bool FIRST = decltype(first)::value;
+    constexpr bool LAST = decltype(last)::value;
+    const float* gr = t.row(CC, line) + lane;
+    const float* gnr = t.row(CC, line + 1) + lane;
+    const float* fr = t.row(0, line) + lane;
+    const bool end_ok = line + 1 < a.L;
+#pragma unroll LineUnroll<R>::value
+    for (int j = 0; j < n; ++j) {
+      float wf[R];
+      forward_weights<R, ODD>(a, gr, gnr, j, end_ok, wf);
+      float diag = 1.f;
+#pragma unroll
+      for (int tt = 0; tt < R; ++tt) diag += wf[tt] + wh[tt][tt];
+      float fj[CC];
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) fj[ch] = fr[ch * pstride + ecol<R, ODD>(j)];
+      const bool sep = LAST && q.bot && j >= n - R;
+      if (!sep) {
+        const int lim = FIRST ? min(j, R) : R;
+        float Lrow[R];
+        const float dinv = ldl_row<R>(diag, wh, Lw, Dw, lim, Lrow);
+        float y[CC];
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) y[ch] = fj[ch];
+        fwd_subst<R, CC>(Lrow, yw, y);
+        float YT[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) YT[i] = 0.f;
+        if (q.top) {
+          if (FIRST) {
+            // E_T[p][i] = A[p, b-R+i] = -lambda w(p-tt, p), tt = j + R - i
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+              for (int tt = 1; tt <= R; ++tt)
+                if (tt == j + R - i) YT[i] = -wh[tt - 1][tt - 1];
+          }
+          fwd_subst<R, R>(Lrow, YTw, YT);
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const float yd = YT[i] * dinv;
+#pragma unroll
+            for (int m = 0; m < R; ++m) KTT[i][m] += yd * YT[m];
+#pragma unroll
+            for (int ch = 0; ch < CC; ++ch) HT[i][ch] += yd * y[ch];
+          }
+        }
+        float YB[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) YB[i] = 0.f;
+        if (LAST) {
+          if (q.bot && j >= n - 2 * R) {
+            // E_B[p][i] = A[p, e+i] = -lambda w(p, p+tt), tt = (n - R - j) + i
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+              for (int tt = 1; tt <= R; ++tt)
+                if (tt == n - R - j + i) YB[i] = -wf[tt - 1];
+            fwd_subst<R, R>(Lrow, YBw, YB);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              const float yd = YB[i] * dinv;
+#pragma unroll
+              for (int m = 0; m < R; ++m) {
+                KBB[i][m] += yd * YB[m];
+                KTB[m][i] += yd * YT[m];
+              }
+#pragma unroll
+              for (int ch = 0; ch < CC; ++ch) HB[i][ch] += yd * y[ch];
+            }
+          }
+          push_vec<R, R>(YBw, YB);
+        }
+        push_factor<R>(Lw, Dw, Lrow, dinv);
+        push_vec<R, CC>(yw, y);
+        push_vec<R, R>(YTw, YT);
+      } else {
+        // separator entry e + i: its diagonal, its couplings inside S_c, f(S_c)
+        const int isep = j - (n - R);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if (i == isep) {
+            DS[i][i] = diag;
+#pragma unroll
+            for (int m = 0; m < i; ++m) {  // A[e+i, e+m] = -lambda w(e+m, e+i)
+              DS[i][m] = -wh[i - m - 1][i - m - 1];
+              DS[m][i] = DS[i][m];
+            }
+#pragma unroll
+            for (int ch = 0; ch < CC; ++ch) FS[i][ch] = fj[ch];
+          }
+        }
+      }
+      push_weights<R>(wh, wf);
+    }
+  });
+
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      out[F::KTT + i * R + m] = KTT[i][m];
+      out[F::KTB + i * R + m] = KTB[i][m];
+      out[F::DS + i * R + m] = DS[i][m] - KBB[i][m];
+    }
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) {
+      out[F::HT + i * CC + ch] = HT[i][ch];
+      out[F::GS + i * CC + ch] = FS[i][ch] - HB[i][ch];
+    }
+  }
+}
+
+// Tile geometry of a block of G chunks starting at chunk c0.
+__device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int off0, int r, float* p, Tile& t) {
+  t.tl0 = c0 * a.h - 1;
+  t.ntl = min((c0 + G) * a.h, a.L) + 1 - t.tl0;
+  t.off0 = off0;
+  t.pitch = 33 + 2 * r;
+  t.p = p;
+}
+
+// ---------------------------------------------------------------------------
+// k_summary: chunk eliminations and the in-block merge into a group 2-port.
+// Grid (ceil(nsys / 32), NG), block (32, G).
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_summary(const PassArgs a) {
+  using F = Fields<R, CC>;
+  using MF = MFields<R, CC>;
+  extern __shared__ float smem[];
+  const int lane = threadIdx.x;
+  const int G = blockDim.y;
+  const int sys = blockIdx.x * 32 + lane;
+  const int grp = blockIdx.y;
+  const int c0 = grp * G;
+  const int nch = min(G, a.P - c0);
+  const int c = c0 + threadIdx.y;
+
+  Tile t;
+  group_tile(a, c0, G, blockIdx.x * 32, R, smem, t);
+  float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
+  griddep_wait();
+  griddep_launch();
+  stage_tile<CC>(a, t, 32 + 2 * R);
+  cp_async_wait_all();
+  __syncthreads();
+
+  const bool active = sys < a.nsys;
+  if (active && threadIdx.y < nch) {
+    chunk_summary<R, CC>(a, t, lane, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
+  }
+  __syncthreads();
+  if (threadIdx.y != 0 || !active) return;
+
+  // ---- merge the block's chunk 2-ports (element form E = -K etc.)
+  const long long ns = a.nsys;
+  Strided cs{csum + lane, 32};
+  float ETT[R][R], ETB[R][R], EBB[R][R], qT[R][CC], qB[R][CC];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      ETT[i][m] = -cs[F::KTT + i * R + m];
+      ETB[i][m] = -cs[F::KTB + i * R + m];
+      EBB[i][m] = cs[F::DS + i * R + m];
+    }
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) {
+      qT[i][ch] = -cs[F::HT + i * CC + ch];
+      qB[i][ch] = cs[F::GS + i * CC + ch];
+    }
+  }
+  const bool acc_top = c0 > 0;
+  for (int i = 1; i < nch; ++i) {
+    const bool b_bot = c0 + i < a.P - 1;
+    Strided bs{csum + i * F::N * 32 + lane, 32};
+    float M[R][R], U[R][R], V[R][R], w[R][CC];
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        M[y][m] = EBB[y][m] - bs[F::KTT + y * R + m];
+        U[y][m] = ETB[m][y];                       // E_YX = E_XY^T
+        V[y][m] = -bs[F::KTB + y * R + m];         // E_YZ
+      }
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) w[y][ch] = qB[y][ch] - bs[F::HT + y * CC + ch];
+    }
+    chol_inplace<R>(M);
+    lsolve<R, R>(M, U);
+    lsolve<R, R>(M, V);
+    lsolve<R, CC>(M, w);
+    if (acc_top) {
+      add_atb<R, R>(ETT, U, U, -1.f);
+      add_atb<R, CC>(qT, U, w, -1.f);
+    }
+#pragma unroll
+    for (int y = 0; y < R; ++y)
+#pragma unroll
+      for (int m = 0; m < R; ++m) ETB[y][m] = 0.f;
+    if (acc_top && b_bot) add_atb<R, R>(ETB, U, V, -1.f);
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) EBB[y][m] = b_bot ? bs[F::DS + y * R + m] : 0.f;
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) qB[y][ch] = b_bot ? bs[F::GS + y * CC + ch] : 0.f;
+    }
+    if (b_bot) {
+      add_atb<R, R>(EBB, V, V, -1.f);
+      add_atb<R, CC>(qB, V, w, -1.f);
+    }
+    StridedG md{a.mdata + ((long long)(grp * (G - 1) + (i - 1)) * MF::N) * ns + sys, ns};
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        md[MF::LM + y * R + m] = M[y][m];
+        md[MF::U + y * R + m] = U[y][m];
+        md[MF::V + y * R + m] = V[y][m];
+      }
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) md[MF::W + y * CC + ch] = w[y][ch];
+    }
+  }
+  StridedG gs{a.summ + (long long)grp * F::N * ns + sys, ns};
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      gs[F::KTT + i * R + m] = -ETT[i][m];
+      gs[F::KTB + i * R + m] = -ETB[i][m];
+      gs[F::DS + i * R + m] = EBB[i][m];
+    }
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) {
+      gs[F::HT + i * CC + ch] = -qT[i][ch];
+      gs[F::GS + i * CC + ch] = qB[i][ch];
+    }
+  }
+}
+
+// Block Cholesky of the group-separator system of one subsystem (the serial
+// chain).  `fld(g, field)` addresses the group 2-ports; the inputs of step
+// g+1 are read before step g is computed.  The factors L_g, Z_g =
+// L_{g-1}^{-1} (-KTB_g) and w_g are written over DS_g, KTB_g and GS_g; the
+// separator values go to xsep.
+template <int R, int CC, typename Fld>
+__device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& fld) {
+  using F = Fields<R, CC>;
+  const int NG = a.ngroups;
+  const long long ns = a.nsys;
+  // inputs of step g: M0 = DS_g - KTT_{g+1}, r0 = GS_g - HT_{g+1}, B = -KTB_g
+  auto load_step = [&](int g, float (&M)[R][R], float (&rhs)[R][CC], float (&B)[R][R]) {
 #pragma unroll
     for (int i = 0; i < R; ++i) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) M[i][m] = *fld(c, F::DS + i * R + m) - *fld(c + 1, F::KTT + i * R + m);
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) rhs[i][ch] = *fld(c, F::GS + i * CC + ch) - *fld(c + 1, F::HT + i * CC + ch);
-    }
-    if (c >= 1) {
-      float Z[R][R];
-#pragma unroll
-      for (int i = 0; i < R; ++i)
-#pragma unroll
-        for (int m = 0; m < R; ++m) Z[i][m] = -*fld(c, F::KTB + i * R + m);
-      lsolve<R, R>(Lp, Z);
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-          float v = 0.f;
-#pragma unroll
-          for (int l = 0; l < R; ++l) v += Z[l][i] * Z[l][m];
-          M[i][m] -= v;
-          *fld(c, F::KTB + i * R + m) = Z[i][m];
-        }
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) {
-          float v = 0.f;
-#pragma unroll
-          for (int l = 0; l < R; ++l) v += Z[l][i] * wp[l][ch];
-          rhs[i][ch] -= v;
-        }
+      for (int m = 0; m < R; ++m) {
+        M[i][m] = fld(g, F::DS + i * R + m) - fld(g + 1, F::KTT + i * R + m);
+        B[i][m] = g >= 1 ? -fld(g, F::KTB + i * R + m) : 0.f;
       }
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) rhs[i][ch] = fld(g, F::GS + i * CC + ch) - fld(g + 1, F::HT + i * CC + ch);
+    }
+  };
+  float Lp[R][R];    // L_{g-1}
+  float wp[R][CC];   // w_{g-1}
+  float Mn[R][R], rn[R][CC], Bn[R][R];
+  load_step(0, Mn, rn, Bn);
+  for (int g = 0; g <= NG - 2; ++g) {
+    float M[R][R], rhs[R][CC], Z[R][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        M[i][m] = Mn[i][m];
+        Z[i][m] = Bn[i][m];
+      }
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) rhs[i][ch] = rn[i][ch];
+    }
+    if (g + 1 <= NG - 2) load_step(g + 1, Mn, rn, Bn);
+    if (g >= 1) {
+      lsolve<R, R>(Lp, Z);
+      add_atb<R, R>(M, Z, Z, -1.f);
+      add_atb<R, CC>(rhs, Z, wp, -1.f);
     }
     chol_inplace<R>(M);
     lsolve<R, CC>(M, rhs);
@@ -442,153 +793,305 @@ __global__ void __launch_bounds__(128) k_reduced(const PassArgs a) {
     for (int i = 0; i < R; ++i) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        *fld(c, F::DS + i * R + m) = M[i][m];
+        if (g >= 1) fld(g, F::KTB + i * R + m) = Z[i][m];
+        fld(g, F::DS + i * R + m) = M[i][m];
         Lp[i][m] = M[i][m];
       }
 #pragma unroll
       for (int ch = 0; ch < CC; ++ch) {
-        *fld(c, F::GS + i * CC + ch) = rhs[i][ch];
+        fld(g, F::GS + i * CC + ch) = rhs[i][ch];
         wp[i][ch] = rhs[i][ch];
       }
     }
   }
-  // back substitution
+  // back substitution: x_g = L_g^{-T} (w_g - Z_{g+1} x_{g+1})
   float x[R][CC];
-  for (int c = a.P - 2; c >= 0; --c) {
-    float Lc[R][R];
-    float v[R][CC];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) x[i][ch] = wp[i][ch];
+  ltsolve<R, CC>(Lp, x);
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) a.xsep[((long long)(NG - 2) * R * CC + i * CC + ch) * ns + sys] = x[i][ch];
+  float Lc[R][R], v[R][CC], Zc[R][R];
+  auto load_back = [&](int g) {
 #pragma unroll
     for (int i = 0; i < R; ++i) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) Lc[i][m] = *fld(c, F::DS + i * R + m);
+      for (int m = 0; m < R; ++m) {
+        Lc[i][m] = fld(g, F::DS + i * R + m);
+        Zc[i][m] = fld(g + 1, F::KTB + i * R + m);
+      }
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) v[i][ch] = *fld(c, F::GS + i * CC + ch);
+      for (int ch = 0; ch < CC; ++ch) v[i][ch] = fld(g, F::GS + i * CC + ch);
     }
-    if (c < a.P - 2) {
+  };
+  if (NG >= 3) load_back(NG - 3);
+  for (int g = NG - 3; g >= 0; --g) {
+    float Lg[R][R], vg[R][CC], Zg[R][R];
 #pragma unroll
-      for (int i = 0; i < R; ++i)
+    for (int i = 0; i < R; ++i) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-          const float zz = *fld(c + 1, F::KTB + i * R + m);
+      for (int m = 0; m < R; ++m) {
+        Lg[i][m] = Lc[i][m];
+        Zg[i][m] = Zc[i][m];
+      }
 #pragma unroll
-          for (int ch = 0; ch < CC; ++ch) v[i][ch] -= zz * x[m][ch];
-        }
+      for (int ch = 0; ch < CC; ++ch) vg[i][ch] = v[i][ch];
     }
-    ltsolve<R, CC>(Lc, v);
+    if (g >= 1) load_back(g - 1);
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int m = 0; m < R; ++m)
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) vg[i][ch] -= Zg[i][m] * x[m][ch];
+    ltsolve<R, CC>(Lg, vg);
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
       for (int ch = 0; ch < CC; ++ch) {
-        x[i][ch] = v[i][ch];
-        a.xsep[((long long)c * R * CC + i * CC + ch) * ns + sys] = v[i][ch];
+        x[i][ch] = vg[i][ch];
+        a.xsep[((long long)g * R * CC + i * CC + ch) * ns + sys] = vg[i][ch];
       }
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_recover: exact interior solve with known separators, write-back and
-// averaging.  Block = (32, warps); lane = centre, warp = chunk.
-template <int R, int CC>
-__global__ void __launch_bounds__(128) k_recover(const PassArgs a) {
-  constexpr int n = 2 * R + 1;
-  constexpr int NF = R + 1 + CC;   // stored per entry: L[p, p-1..p-R], 1/D, z
-  constexpr int OB = 32 - 2 * R;   // outputs per warp
+// k_reduced: one thread per subsystem, 32 subsystems per block.  With
+// SMEM the block first copies its subsystems' group 2-ports into shared
+// memory (every load in flight at once) and runs the chain there; otherwise
+// the chain reads global memory directly.
+template <int R, int CC, bool SMEM>
+__global__ void __launch_bounds__(256) k_reduced(const PassArgs a) {
+  using F = Fields<R, CC>;
   extern __shared__ float smem[];
   const int lane = threadIdx.x;
-  const int c = blockIdx.y * blockDim.y + threadIdx.y;
-  if (c >= a.P) return;  // warp-uniform
+  const int sys = blockIdx.x * 32 + lane;
+  const int NG = a.ngroups;
+  griddep_wait();
+  griddep_launch();
+  if (NG < 2) return;
+  const long long ns = a.nsys;
+  const bool ok = sys < a.nsys;
+  if (SMEM) {
+    // all warps copy the block's group 2-ports; warp 0 then runs the chains
+    const int nrow = NG * F::N;
+    constexpr int U = 8;
+    for (int r0 = threadIdx.y; r0 < nrow; r0 += U * blockDim.y) {
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int row = r0 + u * blockDim.y;
+        v[u] = (ok && row < nrow) ? a.summ[(long long)row * ns + sys] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int row = r0 + u * blockDim.y;
+        if (row < nrow) smem[row * 32 + lane] = v[u];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.y != 0 || !ok) return;
+    reduced_chain<R, CC>(a, sys, [&](int g, int field) -> float& { return smem[(g * F::N + field) * 32 + lane]; });
+  } else {
+    if (threadIdx.y != 0 || !ok) return;
+    float* const S = a.summ;
+    reduced_chain<R, CC>(a, sys, [&](int g, int field) -> float& { return S[((long long)g * F::N + field) * ns + sys]; });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_recover: back-fill of the group's separators, exact interior solves with
+// known separators, write-back and averaging.  Grid (ceil(D / OB), NG),
+// block (32, G); lane = centre, warp = chunk.
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_recover(const PassArgs a) {
+  constexpr int n = 2 * R + 1;
+  constexpr int NF = R + CC;       // stored per entry: L[p, p-1..p-R], z
+  constexpr int OB = 32 - 2 * R;   // outputs per warp
+  constexpr int XS = R * CC;       // values per separator
+  using MF = MFields<R, CC>;
+  extern __shared__ float smem[];
+  const int lane = threadIdx.x;
+  const int G = blockDim.y;
+  const int grp = blockIdx.y;
+  const int c0 = grp * G;
+  const int nch = min(G, a.P - c0);
+  const int c = c0 + threadIdx.y;
   const int kc = blockIdx.x * OB - R + lane;  // this lane's centre
   const int sys_raw = kc - R;
   const bool valid = sys_raw >= 0 && sys_raw < a.nsys;
   const int sys = min(max(sys_raw, 0), a.nsys - 1);
-  const int k = sys + R;
-  const int s = a.L * n;
-  const Chunk q = make_chunk<R>(a, c);
   const int mcap = a.h * n;
-  float* st = smem + (size_t)threadIdx.y * mcap * NF * 32 + lane;
-
-  // separator values from the reduced solve
-  float xT[R][CC], xB[R][CC];
   const long long ns = a.nsys;
-#pragma unroll
-  for (int i = 0; i < R; ++i)
-#pragma unroll
-    for (int ch = 0; ch < CC; ++ch) {
-      xT[i][ch] = q.top ? a.xsep[((long long)(c - 1) * R * CC + i * CC + ch) * ns + sys] : 0.f;
-      xB[i][ch] = q.bot ? a.xsep[((long long)c * R * CC + i * CC + ch) * ns + sys] : 0.f;
-    }
 
-  // ---- forward sweep over the interior, storing L row, 1/D and z per entry
+  Tile t;
+  group_tile(a, c0, G, blockIdx.x * OB - 2 * R, R, smem, t);
+  float* ports = smem + (CC + 1) * t.ntl * t.pitch;   // [G][2][XS][32]
+  float* mbuf = ports + G * 2 * XS * 32;               // [G-1][MF::N][32] merge factors + [2][XS][32]
+  float* store = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [G][mcap][NF][32]
+  // The input tile and the merge factors come from kernels that completed
+  // before the preceding k_reduced started; with a single chunk the
+  // preceding kernel produced the input itself, so wait first.
+  if (!a.early_stage) griddep_wait();
+  stage_tile<CC>(a, t, 32 + 2 * R);
+  // merge factors and the group's outer separators, one warp per merge
+  for (int i = threadIdx.y; i < nch - 1; i += G) {
+    const float* src = a.mdata + ((long long)(grp * (G - 1) + i) * MF::N) * ns + sys;
+    float* dst = mbuf + i * MF::N * 32 + lane;
+#pragma unroll
+    for (int f = 0; f < MF::N; ++f) dst[f * 32] = src[f * ns];
+  }
+  if (a.early_stage) griddep_wait();
+  griddep_launch();
+  if (threadIdx.y == G - 1) {
+    float* dst = mbuf + (G - 1) * MF::N * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < XS; ++i) {
+      dst[i * 32] = c0 > 0 ? a.xsep[((long long)(grp - 1) * XS + i) * ns + sys] : 0.f;
+      dst[(XS + i) * 32] = grp < a.ngroups - 1 ? a.xsep[((long long)grp * XS + i) * ns + sys] : 0.f;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---- back-fill the separators inside the group (warp 0, lane = subsystem)
+  if (threadIdx.y == 0) {
+    const bool acc_top = c0 > 0;
+    const float* xo = mbuf + (G - 1) * MF::N * 32 + lane;
+    float xX[R][CC], xZ[R][CC];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) {
+        xX[i][ch] = xo[(i * CC + ch) * 32];
+        xZ[i][ch] = xo[(XS + i * CC + ch) * 32];
+      }
+    for (int i = nch - 1; i >= 1; --i) {
+      const bool b_bot = c0 + i < a.P - 1;
+      Strided md{mbuf + (i - 1) * MF::N * 32 + lane, 32};
+      float Lm[R][R], v[R][CC];
+#pragma unroll
+      for (int y = 0; y < R; ++y) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) Lm[y][m] = md[MF::LM + y * R + m];
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) {
+          float acc = md[MF::W + y * CC + ch];
+#pragma unroll
+          for (int m = 0; m < R; ++m) {
+            if (acc_top) acc -= md[MF::U + y * R + m] * xX[m][ch];
+            if (b_bot) acc -= md[MF::V + y * R + m] * xZ[m][ch];
+          }
+          v[y][ch] = acc;
+        }
+      }
+      ltsolve<R, CC>(Lm, v);
+      float* pp = ports + (i * 2) * XS * 32 + lane;
+#pragma unroll
+      for (int y = 0; y < R; ++y)
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) {
+          pp[(y * CC + ch) * 32] = v[y][ch];            // top of chunk c0+i
+          pp[(XS + y * CC + ch) * 32] = xZ[y][ch];      // bottom of chunk c0+i
+          xZ[y][ch] = v[y][ch];
+        }
+    }
+    float* pp = ports + lane;
+#pragma unroll
+    for (int y = 0; y < R; ++y)
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) {
+        pp[(y * CC + ch) * 32] = xX[y][ch];
+        pp[(XS + y * CC + ch) * 32] = xZ[y][ch];
+      }
+  }
+  __syncthreads();
+  if (threadIdx.y >= nch) return;  // warp-uniform
+
+  const Chunk q = make_chunk<R>(a, c);
+  float xT[R][CC], xB[R][CC];
+  {
+    const float* pp = ports + (threadIdx.y * 2) * XS * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) {
+        xT[i][ch] = pp[(i * CC + ch) * 32];
+        xB[i][ch] = pp[(XS + i * CC + ch) * 32];
+      }
+  }
+  float* const st = store + threadIdx.y * mcap * NF * 32 + lane;
+
+  // ---- forward sweep over the interior: L row and z = y / D per entry
+  const int pstride = t.ntl * t.pitch;
   {
     float wh[R][R] = {};
     float Lw[R][R] = {};
     float Dw[R] = {};
     float yw[R][CC] = {};
-    float gc[n], gn[n];
-    float wf[R];
-    if (q.top) {
-      load_g_line<R>(a, k, q.line0 - 1, gc);
-      load_g_line<R>(a, k, q.line0, gn);
-#pragma unroll
+    if (q.top) prologue_weights<R, CC>(a, t, lane, q.line0 - 1, wh);
+    for_lines(q.line0, q.line1, [&](auto odd, auto first, auto last, int line) {
+      constexpr bool ODD = decltype(odd)::value;
+      constexpr bool FIRST = decltype(first)::value;
+      constexpr bool LAST = decltype(last)::value;
+      const float* gr = t.row(CC, line) + lane;
+      const float* gnr = t.row(CC, line + 1) + lane;
+      const float* fr = t.row(0, line) + lane;
+      const bool end_ok = line + 1 < a.L;
+      float* lslot = st + (line - q.line0) * n * NF * 32;
+#pragma unroll LineUnroll<R>::value
       for (int j = 0; j < n; ++j) {
-        forward_weights<R>(a, j, (q.line0 - 1) * n + j, s, gc, gn, wf);
-        push_weights<R>(wh, wf);
-      }
-    }
-    load_g_line<R>(a, k, q.line0, gc);
-    for (int line = q.line0; line < q.line1; ++line) {
-      load_g_line<R>(a, k, line + 1, gn);
-      float fl[n][CC];
-      load_f_line<R, CC>(a, k, line, fl);
-      const bool first = line == q.line0;
-      const bool last = line == q.line1 - 1;
-#pragma unroll
-      for (int j = 0; j < n; ++j) {
-        const int p = line * n + j;
-        forward_weights<R>(a, j, p, s, gc, gn, wf);
-        const bool sep = last && q.bot && (j >= n - R);
+        float wf[R];
+        forward_weights<R, ODD>(a, gr, gnr, j, end_ok, wf);
+        const bool sep = LAST && q.bot && j >= n - R;
         if (!sep) {
           float diag = 1.f;
 #pragma unroll
-          for (int t = 0; t < R; ++t) diag += wf[t] + wh[t][t];
+          for (int tt = 0; tt < R; ++tt) diag += wf[tt] + wh[tt][tt];
           float Lrow[R];
-          const float dinv = ldl_row<R>(diag, wh, Lw, Dw, first ? j : R, Lrow);
+          const float dinv = ldl_row<R>(diag, wh, Lw, Dw, FIRST ? min(j, R) : R, Lrow);
           float y[CC];
 #pragma unroll
-          for (int ch = 0; ch < CC; ++ch) y[ch] = fl[j][ch];
-          if (first && q.top) {
-            // + lambda w(p-t, p) x(b-R+i) for separator entries above, i = j + R - t
+          for (int ch = 0; ch < CC; ++ch) y[ch] = fr[ch * pstride + ecol<R, ODD>(j)];
+          if (FIRST) {
+            if (q.top) {
+              // + lambda w(p-tt, p) x(b-R+i) for separator entries above, tt = j + R - i
 #pragma unroll
-            for (int t = j + 1; t <= R; ++t)
+              for (int i = 0; i < R; ++i)
 #pragma unroll
-              for (int ch = 0; ch < CC; ++ch) y[ch] += wh[t - 1][t - 1] * xT[j + R - t][ch];
+                for (int tt = 1; tt <= R; ++tt)
+                  if (tt == j + R - i)
+#pragma unroll
+                    for (int ch = 0; ch < CC; ++ch) y[ch] += wh[tt - 1][tt - 1] * xT[i][ch];
+            }
           }
-          if (last && q.bot) {
-            // + lambda w(p, p+t) x(e+i) for separator entries below, i = j + t - (n - R)
+          if (LAST) {
+            if (q.bot) {
+              // + lambda w(p, p+tt) x(e+i) for separator entries below, i = j + tt - (n - R)
 #pragma unroll
-            for (int t = 1; t <= R; ++t) {
-              const int i = j + t - (n - R);
-              if (i >= 0 && i < R) {
+              for (int i = 0; i < R; ++i)
 #pragma unroll
-                for (int ch = 0; ch < CC; ++ch) y[ch] += wf[t - 1] * xB[i][ch];
-              }
+                for (int tt = 1; tt <= R; ++tt)
+                  if (i == j + tt - (n - R))
+#pragma unroll
+                    for (int ch = 0; ch < CC; ++ch) y[ch] += wf[tt - 1] * xB[i][ch];
             }
           }
           fwd_subst<R, CC>(Lrow, yw, y);
-          float* slot = st + (size_t)(p - q.b) * NF * 32;
+          float* slot = lslot + j * NF * 32;
 #pragma unroll
-          for (int t = 0; t < R; ++t) slot[t * 32] = Lrow[t];
-          slot[R * 32] = dinv;
+          for (int tt = 0; tt < R; ++tt) slot[tt * 32] = Lrow[tt];
 #pragma unroll
-          for (int ch = 0; ch < CC; ++ch) slot[(R + 1 + ch) * 32] = y[ch] * dinv;
+          for (int ch = 0; ch < CC; ++ch) slot[(R + ch) * 32] = y[ch] * dinv;
           push_factor<R>(Lw, Dw, Lrow, dinv);
           push_vec<R, CC>(yw, y);
         }
         push_weights<R>(wh, wf);
       }
-#pragma unroll
-      for (int j = 0; j < n; ++j) gc[j] = gn[j];
-    }
+    });
   }
 
   // ---- backward sweep, write-back and averaging per line
@@ -601,54 +1104,77 @@ __global__ void __launch_bounds__(128) k_recover(const PassArgs a) {
   }
   float Lb[R][R] = {};   // Lb[u-1][t-1] = L[p+u, p+u-t]
   float xw[R][CC] = {};  // x of entries p+1 .. p+R (interior only)
-  for (int line = q.line1 - 1; line >= q.line0; --line) {
-    const bool last = line == q.line1 - 1;
-    float xl[n][CC];
-#pragma unroll
-    for (int jj = n - 1; jj >= 0; --jj) {
-      const int p = line * n + jj;
-      if (last && q.bot && jj >= n - R) {
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) xl[jj][ch] = xB[jj - (n - R)][ch];
-        continue;
-      }
-      const float* slot = st + (size_t)(p - q.b) * NF * 32;
-      float Lrow[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) Lrow[t] = slot[t * 32];
+  const long long ostride = a.dir == 0 ? 1 : a.W;
+  const long long lstride = a.dir == 0 ? a.W : 1;
+  float* const outp = reinterpret_cast<float*>(a.out);
+  constexpr bool XREG = LineUnroll<R>::value > 1;   // line values in registers
+  for_lines_rev(q.line0, q.line1, [&](auto odd, auto last, int line) {
+    constexpr bool ODD = decltype(odd)::value;
+    constexpr bool LAST = decltype(last)::value;
+    float xl[XREG ? n : 1][CC];
+    float* lslot = st + (line - q.line0) * n * NF * 32;
+#pragma unroll LineUnroll<R>::value
+    for (int j = n - 1; j >= 0; --j) {
       float x[CC];
+      float* slot = lslot + j * NF * 32;
+      if (LAST && q.bot && j >= n - R) {
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) x[ch] = slot[(R + 1 + ch) * 32];
+        for (int i = 0; i < R; ++i)
+          if (i == j - (n - R))
 #pragma unroll
-      for (int t = 1; t <= R; ++t)
+            for (int ch = 0; ch < CC; ++ch) x[ch] = xB[i][ch];
+      } else {
+        float Lrow[R];
 #pragma unroll
-        for (int ch = 0; ch < CC; ++ch) x[ch] -= Lb[t - 1][t - 1] * xw[t - 1][ch];
+        for (int tt = 0; tt < R; ++tt) Lrow[tt] = slot[tt * 32];
 #pragma unroll
-      for (int u = R - 1; u > 0; --u)
+        for (int ch = 0; ch < CC; ++ch) x[ch] = slot[(R + ch) * 32];
 #pragma unroll
-        for (int t = 0; t < R; ++t) Lb[u][t] = Lb[u - 1][t];
+        for (int tt = 1; tt <= R; ++tt)
 #pragma unroll
-      for (int t = 0; t < R; ++t) Lb[0][t] = Lrow[t];
-      push_vec<R, CC>(xw, x);
+          for (int ch = 0; ch < CC; ++ch) x[ch] -= Lb[tt - 1][tt - 1] * xw[tt - 1][ch];
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) xl[jj][ch] = x[ch];
+        for (int u = R - 1; u > 0; --u)
+#pragma unroll
+          for (int tt = 0; tt < R; ++tt) Lb[u][tt] = Lb[u - 1][tt];
+#pragma unroll
+        for (int tt = 0; tt < R; ++tt) Lb[0][tt] = Lrow[tt];
+        push_vec<R, CC>(xw, x);
+      }
+      if constexpr (XREG) {
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) xl[j][ch] = x[ch];
+      } else {
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) slot[(R + ch) * 32] = x[ch];
+      }
     }
     // inverse construction + averaging: value at across-offset kc - R + e
-    const bool rev = line & 1;
+    const long long pix = (long long)line * lstride + (long long)o * ostride;
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) {
       float voff[n];
 #pragma unroll
-      for (int e2 = 0; e2 < n; ++e2) voff[e2] = valid ? (rev ? xl[n - 1 - e2][ch] : xl[e2][ch]) : 0.f;
+      for (int e2 = 0; e2 < n; ++e2) {
+        float v;
+        if constexpr (XREG) v = xl[ecol<R, ODD>(e2)][ch];
+        else v = lslot[ecol<R, ODD>(e2) * NF * 32 + (R + ch) * 32];
+        voff[e2] = valid ? v : 0.f;
+      }
       float sum = voff[R];
 #pragma unroll
       for (int d = 1; d <= R; ++d) {
         sum += __shfl_down_sync(0xffffffffu, voff[R - d], d);  // from centre kc + d
         sum += __shfl_up_sync(0xffffffffu, voff[R + d], d);    // from centre kc - d
       }
-      if (writer) st_px(a.out, pix_index(a, line, o) + ch * a.plane, a.out_dt, sum * inv_cnt);
+      if (writer) {
+        if (a.out_dt == DT_F32)
+          outp[pix + ch * a.plane] = sum * inv_cnt;
+        else
+          st_px(a.out, pix + ch * a.plane, a.out_dt, sum * inv_cnt);
+      }
     }
-  }
+  });
 }
 
 }  // namespace sgwls

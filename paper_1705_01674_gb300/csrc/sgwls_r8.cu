@@ -3,6 +3,11 @@
 
 namespace sgwls {
 cudaError_t launch_pass_r8(const PassArgs& a, const Plan& pl, int CC, cudaStream_t st) {
+#ifdef SGWLS_STUB_RADIUS
+  (void)a, (void)pl, (void)CC, (void)st;
+  return cudaErrorNotSupported;
+#else
   return launch_pass_r<8>(a, pl, CC, st);
+#endif
 }
 }  // namespace sgwls
