@@ -133,6 +133,27 @@ sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int
                                float lambda, const sgwls_params* p, int direction, void* ws,
                                size_t ws_bytes, void* stream);
 
+/* One pass like sgwls_filter_pass, for callers that cannot allocate device
+ * memory when they filter (a host with a fixed device-memory budget, or a
+ * code path that must not enter the allocator): it takes no workspace.  The
+ * paper has no counterpart; this is an interface convenience.
+ *   Scratch: a file-scope device array of 16 MiB inside libsgwls.so, held by
+ *   every GPU that loads the library until the process exits.  Requests
+ *   whose scratch (sgwls_workspace_bytes with iters = 0) exceeds 16 MiB
+ *   return SGWLS_E_WORKSPACE; e.g. RGB FP32 at r = 1 fits up to about
+ *   1920 x 1080.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   with that device current (cudaGetSymbolAddress) and keeps it; make that
+ *   first call before any stream capture.
+ *   Sharing: all calls share the one array and leave their contents in it
+ *   (every value the kernels read is written earlier in the same call, so
+ *   nothing needs clearing); calls that overlap on the GPU (other streams,
+ *   other host threads) race on it -- serialise them.
+ *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Other arguments and results as sgwls_filter_pass. */
+sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, void* u, int H, int W, int C,
+                                       float lambda, const sgwls_params* p, int direction, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all devices).  Diagnostics: lets a caller count the kernels
  * behind a sequence of calls.  Host-only. */

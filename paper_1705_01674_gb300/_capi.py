@@ -89,6 +89,8 @@ def _declare(lib):
     lib.sgwls_filter.restype = ci
     lib.sgwls_filter_pass.argtypes = [vp, vp, vp, ci, ci, ci, cf, P, ci, vp, sz, vp]
     lib.sgwls_filter_pass.restype = ci
+    lib.sgwls_filter_pass_noalloc.argtypes = [vp, vp, vp, ci, ci, ci, cf, P, ci, vp]
+    lib.sgwls_filter_pass_noalloc.restype = ci
     lib.sgwls_launch_count.argtypes = []
     lib.sgwls_launch_count.restype = ctypes.c_ulonglong
     if hasattr(lib, "sgwls_batched_workspace_bytes"):
