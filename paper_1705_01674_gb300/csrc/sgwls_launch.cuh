@@ -14,14 +14,16 @@ struct Plan {
 };
 
 // Shared memory of the two tiled kernels for a plan (bytes).
-inline size_t tile_floats(int r, int CC, int h, int G) { return (size_t)(CC + 1) * (G * h + 2) * (33 + 2 * r); }
+inline size_t tile_floats(int r, int CC, int h, int G) { return (size_t)(CC + 1) * (G * h + 2) * tile_pitch_max(r); }
 inline size_t smem_summary(int r, int CC, int h, int G) {
   return 4 * (tile_floats(r, CC, h, G) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
 }
 inline size_t smem_recover(int r, int CC, int h, int G) {
   const int n = 2 * r + 1;
   const size_t merge = (size_t)(G - 1) * (3 * r * r + r * CC) * 32 + 2 * (size_t)r * CC * 32;
-  return 4 * (tile_floats(r, CC, h, G) + (size_t)G * 2 * r * CC * 32 + merge + (size_t)G * h * n * (r + CC) * 32);
+  const size_t otile = (size_t)CC * (32 - 2 * r) * ((G * h) | 1);
+  return 4 * (tile_floats(r, CC, h, G) + (size_t)G * 2 * r * CC * 32 + merge + (size_t)G * h * n * (r + CC) * 32 +
+              otile);
 }
 
 constexpr size_t kReducedSmemMax = 96 * 1024;

@@ -77,14 +77,25 @@ struct MFields {
 struct Tile {
   float* p;
   int tl0, ntl, off0, pitch;
+  int cs;   // physical column of across-offset off0 (vector-aligned staging)
   __device__ __forceinline__ const float* row(int plane, int line) const {
-    return p + (plane * ntl + (line - tl0)) * pitch;
+    return p + (plane * ntl + (line - tl0)) * pitch + cs;
   }
 };
 
+// Row pitch of the tile in floats: column direction, rows of whole 16-byte
+// quads starting at the 16-byte boundary at or before off0; row direction,
+// an odd pitch (transposed staging without bank conflicts).
+__host__ __device__ constexpr int tile_pitch(int r, int dir) {
+  return dir == 0 ? 4 * ((32 + 2 * r + 3 + 3) / 4) : 33 + 2 * r;
+}
+__host__ __device__ constexpr int tile_pitch_max(int r) {
+  return tile_pitch(r, 0) > tile_pitch(r, 1) ? tile_pitch(r, 0) : tile_pitch(r, 1);
+}
+
 // Mixed storage types (BF16 guidance with FP32 estimates): plain loop.
 template <int CC>
-__device__ __forceinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, int ncol) {
+__device__ __noinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, int ncol) {
   const int nthreads = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int per_plane = t.ntl * ncol;
@@ -115,7 +126,7 @@ __device__ __forceinline__ float ld_plane(const void* base, long long idx) {
 // lines.  Row direction: lanes along the lines (contiguous in memory), warps
 // over the offsets.  Each thread issues U loads before its stores.
 template <int CC, bool F32>
-__device__ __forceinline__ void stage_tile_t(const PassArgs& a, const Tile& t, int ncol) {
+__device__ __noinline__ void stage_tile_t(const PassArgs& a, const Tile& t, int ncol) {
   const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
   constexpr int U = 4;
 #pragma unroll 1
@@ -186,33 +197,130 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <int CC>
-__device__ __forceinline__ void stage_tile_async(const PassArgs& a, const Tile& t, int ncol) {
-  const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
+template <int CC, int NCOL>
+__device__ __noinline__ void stage_tile_async(const PassArgs& a, const Tile& t) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  const long long W = a.W;
 #pragma unroll 1
   for (int pl = 0; pl <= CC; ++pl) {
     const float* base = static_cast<const float*>(pl < CC ? a.in : a.g) + (pl < CC ? (size_t)pl * a.plane : 0);
     float* dplane = t.p + pl * t.ntl * t.pitch;
     if (a.dir == 0) {
-      for (int tl = warp; tl < t.ntl; tl += nw) {
+      // flat over (line, offset); NCOL is a compile-time constant
+      const int nel = t.ntl * NCOL;
+      for (int idx = tid; idx < nel; idx += nthreads) {
+        const int tl = idx / NCOL;
+        const int col = idx - tl * NCOL;
+        const int line = t.tl0 + tl, off = t.off0 + col;
+        const bool ok = line >= 0 && line < a.L && off >= 0 && off < a.D;
+        const float* src = ok ? base + (line * W + off) : base;
+        cp_async4(dplane + tl * t.pitch + col, src, ok);
+      }
+    } else {
+      // 8 lines x 4 offsets per warp instruction: lanes along the lines are
+      // contiguous in memory (one 32-byte sector per offset)
+      constexpr int NCB = (NCOL + 3) / 4;
+      const int nlb = (t.ntl + 7) / 8;
+      const int ls = threadIdx.x & 7, cs = threadIdx.x >> 3;
+      for (int tile = threadIdx.y; tile < nlb * NCB; tile += blockDim.y) {
+        const int lb = tile / NCB;
+        const int cb = tile - lb * NCB;
+        const int tl = lb * 8 + ls, col = cb * 4 + cs;
+        const int line = t.tl0 + tl, off = t.off0 + col;
+        const bool in_tile = tl < t.ntl && col < NCOL;
+        const bool ok = in_tile && line >= 0 && line < a.L && off >= 0 && off < a.D;
+        const float* src = ok ? base + (off * W + line) : base;
+        if (in_tile) cp_async4(dplane + tl * t.pitch + col, src, ok);
+      }
+    }
+  }
+}
+
+// 16-byte asynchronous global->shared copy; bytes past src_bytes are zero.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// FP32 tiles with 16-byte transfers (image rows 16-byte aligned).
+// Column direction: asynchronous 16-byte copies along the offsets into quads
+// of the tile (its column origin is the quad boundary, cs = off0 mod 4); only
+// quads that start left of the image use scalar loads.  Row direction: each
+// warp instruction loads 8 quads (32 consecutive lines) of 4 image rows, U
+// loads in flight per thread, scattered into the transposed tile.
+template <int CC, int NCOL>
+__device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthreads = blockDim.x * blockDim.y;
+  const long long W = a.W;
+#pragma unroll 1
+  for (int pl = 0; pl <= CC; ++pl) {
+    const float* base = static_cast<const float*>(pl < CC ? a.in : a.g) + (pl < CC ? (size_t)pl * a.plane : 0);
+    float* dplane = t.p + pl * t.ntl * t.pitch;
+    if (a.dir == 0) {
+      constexpr int PQ = (NCOL + 3 + 3) / 4;
+      const int x0 = t.off0 - t.cs;
+      const int nq = t.ntl * PQ;
+      for (int idx = tid; idx < nq; idx += nthreads) {
+        const int tl = idx / PQ;
+        const int q = idx - tl * PQ;
         const int line = t.tl0 + tl;
+        const int x = x0 + 4 * q;
+        float* dst = dplane + tl * t.pitch + 4 * q;
         const bool lok = line >= 0 && line < a.L;
-        const float* rowp = base + (size_t)(lok ? line : 0) * a.W;
-        for (int col = lane; col < ncol; col += 32) {
-          const int off = t.off0 + col;
-          const bool ok = lok && off >= 0 && off < a.D;
-          cp_async4(dplane + tl * t.pitch + col, ok ? rowp + off : base, ok);
+        if (x >= 0) {
+          const int valid = lok ? max(0, min(4, a.D - x)) : 0;
+          cp_async16(dst, valid > 0 ? base + (line * W + x) : base, 4 * valid);
+        } else {
+          const float* rp = base + (lok ? line : 0) * W;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) dst[i] = (lok && x + i >= 0 && x + i < a.D) ? __ldg(rp + x + i) : 0.f;
         }
       }
     } else {
-      for (int col = warp; col < ncol; col += nw) {
-        const int off = t.off0 + col;
-        const bool ook = off >= 0 && off < a.D;
-        const float* rowp = base + (size_t)(ook ? off : 0) * a.W;
-        for (int tl = lane; tl < t.ntl; tl += 32) {
-          const int line = t.tl0 + tl;
-          const bool ok = ook && line >= 0 && line < a.L;
-          cp_async4(dplane + tl * t.pitch + col, ok ? rowp + line : base, ok);
+      constexpr int NCB = (NCOL + 3) / 4;
+      constexpr int U = 4;
+      const int x0 = t.tl0 & ~3;                 // first quad's line
+      const int nql = (t.tl0 + t.ntl - x0 + 3) / 4;
+      const int nqb = (nql + 7) / 8;
+      const int qs = threadIdx.x & 7, csub = threadIdx.x >> 3;
+      const int ntile = nqb * NCB;
+      for (int tb = threadIdx.y; tb < ntile; tb += U * blockDim.y) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int tile = tb + u * blockDim.y;
+          const int qb = tile / NCB;
+          const int cb = tile - qb * NCB;
+          const int q = qb * 8 + qs, col = cb * 4 + csub;
+          const int off = t.off0 + col;
+          const int x = x0 + 4 * q;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (tile < ntile && q < nql && col < NCOL && off >= 0 && off < a.D) {
+            const float* rp = base + off * W;
+            if (x >= 0 && x + 3 < a.L) {
+              v[u] = __ldg(reinterpret_cast<const float4*>(rp + x));
+            } else {
+              if (x >= 0 && x < a.L) v[u].x = __ldg(rp + x);
+              if (x + 1 >= 0 && x + 1 < a.L) v[u].y = __ldg(rp + x + 1);
+              if (x + 2 >= 0 && x + 2 < a.L) v[u].z = __ldg(rp + x + 2);
+              if (x + 3 >= 0 && x + 3 < a.L) v[u].w = __ldg(rp + x + 3);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int tile = tb + u * blockDim.y;
+          const int qb = tile / NCB;
+          const int cb = tile - qb * NCB;
+          const int q = qb * 8 + qs, col = cb * 4 + csub;
+          if (tile >= ntile || q >= nql || col >= NCOL) continue;
+          const int tlq = x0 + 4 * q - t.tl0;   // tile line of v.x
+          const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (tlq + i >= 0 && tlq + i < t.ntl) dplane[(tlq + i) * t.pitch + col] = e[i];
         }
       }
     }
@@ -221,10 +329,15 @@ __device__ __forceinline__ void stage_tile_async(const PassArgs& a, const Tile& 
 
 // The tile planes share one storage type when the estimate and the guidance
 // do (always, except for a BF16 guidance with FP32 intermediates).
-template <int CC>
-__device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t, int ncol) {
-  if (a.in_dt == DT_F32 && a.g_dt == DT_F32)
-    stage_tile_async<CC>(a, t, ncol);
+template <int CC, int NCOL>
+__device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t) {
+  const int ncol = NCOL;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 &&
+                       (a.W & 3) == 0;
+  if (a.in_dt == DT_F32 && a.g_dt == DT_F32 && aligned)
+    stage_tile_vec<CC, NCOL>(a, t);
+  else if (a.in_dt == DT_F32 && a.g_dt == DT_F32)
+    stage_tile_async<CC, NCOL>(a, t);
   else if (a.in_dt == DT_BF16 && a.g_dt == DT_BF16)
     stage_tile_t<CC, false>(a, t, ncol);
   else
@@ -323,23 +436,19 @@ __device__ __forceinline__ void fwd_subst(const float (&Lrow)[R], const float (&
     for (int i = 0; i < K; ++i) y[i] -= Lrow[t] * win[t][i];
 }
 
-// Runs body(odd, first, last, line) over the lines [line0, line1) with the
-// parity and the first/last role as compile-time constants.
+// Runs body(odd, first, last, line) over the lines [line0, line1): the
+// parity and the last-line role are compile-time constants, the first-line
+// role a runtime flag (keeps the kernels' code small).
 template <typename Body>
 __device__ __forceinline__ void for_lines(int line0, int line1, Body&& body) {
-  auto dispatch = [&](auto first, auto last, int line) {
+  auto dispatch = [&](bool first, auto last, int line) {
     if (line & 1)
       body(std::true_type{}, first, last, line);
     else
       body(std::false_type{}, first, last, line);
   };
-  if (line1 - line0 == 1) {
-    dispatch(std::true_type{}, std::true_type{}, line0);
-    return;
-  }
-  dispatch(std::true_type{}, std::false_type{}, line0);
-  for (int line = line0 + 1; line < line1 - 1; ++line) dispatch(std::false_type{}, std::false_type{}, line);
-  dispatch(std::false_type{}, std::true_type{}, line1 - 1);
+  for (int line = line0; line < line1 - 1; ++line) dispatch(line == line0, std::false_type{}, line);
+  dispatch(line1 - 1 == line0, std::true_type{}, line1 - 1);
 }
 
 // Backward order: body(odd, last, line) over lines line1-1 down to line0.
@@ -498,9 +607,8 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
 
   if (q.top) prologue_weights<R, CC>(a, t, lane, q.line0 - 1, wh);
 
-  for_lines(q.line0, q.line1, [&](auto odd, auto first, auto last, int line) {
+  for_lines(q.line0, q.line1, [&](auto odd, const bool FIRST, auto last, int line) {
     constexpr bool ODD = decltype(odd)::value;
-    constexpr bool FIRST = decltype(first)::value;
     constexpr bool LAST = decltype(last)::value;
     const float* gr = t.row(CC, line) + lane;
     const float* gnr = t.row(CC, line + 1) + lane;
@@ -618,43 +726,22 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int
   t.tl0 = c0 * a.h - 1;
   t.ntl = min((c0 + G) * a.h, a.L) + 1 - t.tl0;
   t.off0 = off0;
-  t.pitch = 33 + 2 * r;
+  const bool vec = a.dir == 0 && a.in_dt == DT_F32 && a.g_dt == DT_F32 &&
+                   ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 &&
+                   (a.W & 3) == 0;
+  t.cs = vec ? (off0 & 3) : 0;
+  t.pitch = tile_pitch(r, a.dir);
   t.p = p;
 }
 
-// ---------------------------------------------------------------------------
-// k_summary: chunk eliminations and the in-block merge into a group 2-port.
-// Grid (ceil(nsys / 32), NG), block (32, G).
+// Merges the block's chunk 2-ports into the group 2-port (warp 0, lane =
+// subsystem) and writes the merge factors for the back-fill.  Out of line:
+// it runs once per block and keeps the sweep's code small.
 template <int R, int CC>
-__global__ void __launch_bounds__(256) k_summary(const PassArgs a) {
+__device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lane, int sys, int grp, int c0,
+                                         int nch, int G) {
   using F = Fields<R, CC>;
   using MF = MFields<R, CC>;
-  extern __shared__ float smem[];
-  const int lane = threadIdx.x;
-  const int G = blockDim.y;
-  const int sys = blockIdx.x * 32 + lane;
-  const int grp = blockIdx.y;
-  const int c0 = grp * G;
-  const int nch = min(G, a.P - c0);
-  const int c = c0 + threadIdx.y;
-
-  Tile t;
-  group_tile(a, c0, G, blockIdx.x * 32, R, smem, t);
-  float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
-  griddep_wait();
-  griddep_launch();
-  stage_tile<CC>(a, t, 32 + 2 * R);
-  cp_async_wait_all();
-  __syncthreads();
-
-  const bool active = sys < a.nsys;
-  if (active && threadIdx.y < nch) {
-    chunk_summary<R, CC>(a, t, lane, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
-  }
-  __syncthreads();
-  if (threadIdx.y != 0 || !active) return;
-
-  // ---- merge the block's chunk 2-ports (element form E = -K etc.)
   const long long ns = a.nsys;
   Strided cs{csum + lane, 32};
   float ETT[R][R], ETB[R][R], EBB[R][R], qT[R][CC], qB[R][CC];
@@ -740,6 +827,41 @@ __global__ void __launch_bounds__(256) k_summary(const PassArgs a) {
       gs[F::GS + i * CC + ch] = qB[i][ch];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// k_summary: chunk eliminations and the in-block merge into a group 2-port.
+// Grid (ceil(nsys / 32), NG), block (32, G).
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
+  using F = Fields<R, CC>;
+  using MF = MFields<R, CC>;
+  extern __shared__ float smem[];
+  const int lane = threadIdx.x;
+  const int G = blockDim.y;
+  const int sys = blockIdx.x * 32 + lane;
+  const int grp = blockIdx.y;
+  const int c0 = grp * G;
+  const int nch = min(G, a.P - c0);
+  const int c = c0 + threadIdx.y;
+
+  Tile t;
+  group_tile(a, c0, G, blockIdx.x * 32, R, smem, t);
+  float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
+  griddep_wait();
+  griddep_launch();
+  stage_tile<CC, 32 + 2 * R>(a, t);
+  cp_async_wait_all();
+  __syncthreads();
+
+  const bool active = sys < a.nsys;
+  if (active && threadIdx.y < nch) {
+    chunk_summary<R, CC>(a, t, lane, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
+  }
+  __syncthreads();
+  if (threadIdx.y != 0 || !active) return;
+
+  merge_block<R, CC>(a, csum, lane, sys, grp, c0, nch, G);
 }
 
 // Block Cholesky of the group-separator system of one subsystem (the serial
@@ -864,7 +986,7 @@ __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& 
 // memory (every load in flight at once) and runs the chain there; otherwise
 // the chain reads global memory directly.
 template <int R, int CC, bool SMEM>
-__global__ void __launch_bounds__(256) k_reduced(const PassArgs a) {
+__global__ void __launch_bounds__(256) k_reduced(const __grid_constant__ PassArgs a) {
   using F = Fields<R, CC>;
   extern __shared__ float smem[];
   const int lane = threadIdx.x;
@@ -907,7 +1029,7 @@ __global__ void __launch_bounds__(256) k_reduced(const PassArgs a) {
 // known separators, write-back and averaging.  Grid (ceil(D / OB), NG),
 // block (32, G); lane = centre, warp = chunk.
 template <int R, int CC>
-__global__ void __launch_bounds__(256) k_recover(const PassArgs a) {
+__global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArgs a) {
   constexpr int n = 2 * R + 1;
   constexpr int NF = R + CC;       // stored per entry: L[p, p-1..p-R], z
   constexpr int OB = 32 - 2 * R;   // outputs per warp
@@ -936,7 +1058,7 @@ __global__ void __launch_bounds__(256) k_recover(const PassArgs a) {
   // before the preceding k_reduced started; with a single chunk the
   // preceding kernel produced the input itself, so wait first.
   if (!a.early_stage) griddep_wait();
-  stage_tile<CC>(a, t, 32 + 2 * R);
+  stage_tile<CC, 32 + 2 * R>(a, t);
   // merge factors and the group's outer separators, one warp per merge
   for (int i = threadIdx.y; i < nch - 1; i += G) {
     const float* src = a.mdata + ((long long)(grp * (G - 1) + i) * MF::N) * ns + sys;
@@ -1009,8 +1131,13 @@ __global__ void __launch_bounds__(256) k_recover(const PassArgs a) {
       }
   }
   __syncthreads();
-  if (threadIdx.y >= nch) return;  // warp-uniform
+  // Row direction: the block's output lines are staged as [CC][OB][lines]
+  // (odd pitch) and written out along the lines at the end.
+  const int oline0 = c0 * a.h;
+  const int opitch = (G * a.h) | 1;
+  float* const otile = store + G * mcap * NF * 32;
 
+  if (threadIdx.y < nch) {  // warp-uniform
   const Chunk q = make_chunk<R>(a, c);
   float xT[R][CC], xB[R][CC];
   {
@@ -1033,9 +1160,8 @@ __global__ void __launch_bounds__(256) k_recover(const PassArgs a) {
     float Dw[R] = {};
     float yw[R][CC] = {};
     if (q.top) prologue_weights<R, CC>(a, t, lane, q.line0 - 1, wh);
-    for_lines(q.line0, q.line1, [&](auto odd, auto first, auto last, int line) {
+    for_lines(q.line0, q.line1, [&](auto odd, const bool FIRST, auto last, int line) {
       constexpr bool ODD = decltype(odd)::value;
-      constexpr bool FIRST = decltype(first)::value;
       constexpr bool LAST = decltype(last)::value;
       const float* gr = t.row(CC, line) + lane;
       const float* gnr = t.row(CC, line + 1) + lane;
@@ -1168,13 +1294,36 @@ __global__ void __launch_bounds__(256) k_recover(const PassArgs a) {
         sum += __shfl_up_sync(0xffffffffu, voff[R + d], d);    // from centre kc - d
       }
       if (writer) {
-        if (a.out_dt == DT_F32)
+        if (a.dir != 0)
+          otile[(ch * OB + (lane - R)) * opitch + (line - oline0)] = sum * inv_cnt;
+        else if (a.out_dt == DT_F32)
           outp[pix + ch * a.plane] = sum * inv_cnt;
         else
           st_px(a.out, pix + ch * a.plane, a.out_dt, sum * inv_cnt);
       }
     }
   });
+  }  // this warp's chunk
+
+  if (a.dir != 0) {
+    __syncthreads();
+    const int nl = min((c0 + G) * a.h, a.L) - oline0;
+    for (int row = threadIdx.y; row < CC * OB; row += G) {
+      const int ch = row / OB;
+      const int o = row - ch * OB;
+      const int oabs = blockIdx.x * OB + o;
+      if (oabs >= a.D) continue;
+      const float* src = otile + row * opitch;
+      const long long gbase = ch * a.plane + (long long)oabs * a.W + oline0;
+      float* const outw = reinterpret_cast<float*>(a.out);
+      for (int l = lane; l < nl; l += 32) {
+        if (a.out_dt == DT_F32)
+          outw[gbase + l] = src[l];
+        else
+          st_px(a.out, gbase + l, a.out_dt, src[l]);
+      }
+    }
+  }
 }
 
 }  // namespace sgwls
