@@ -133,6 +133,36 @@ sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int
                                float lambda, const sgwls_params* p, int direction, void* ws,
                                size_t ws_bytes, void* stream);
 
+/* Workspace bytes sgwls_filter_backward needs (0 if the arguments are
+ * invalid).  Host-only. */
+size_t sgwls_backward_workspace_bytes(int H, int W, int C, const sgwls_params* p);
+
+/* Reverse-mode derivative of sgwls_filter (the paper has no backward pass;
+ * this is the chain rule through Eqs. 2, 4, 5 and the four steps of
+ * Sec. 2.3).  Per pass, walked in reverse order, for every subsystem with
+ * u = A_s^-1 f (recomputed from the checkpoint) and v = A_s^-1 ubar, where
+ * ubar gathers dLoss/d(pass output) divided by each pixel's subsystem count:
+ *   dLoss/d(pass input) = sum over subsystems of v scattered to the pixels;
+ *   dLoss/dlambda      += -sum_pairs w_pq (v_p - v_q).(u_p - u_q);
+ *   dLoss/dG           += -lambda (v_p - v_q).(u_p - u_q) dw_pq/dG
+ * (the dot runs over channels, which share A_s).
+ *   grad_u      device FP32 C x H x W, dLoss/du
+ *   g           device FP32 H x W guidance used in the forward call
+ *   saved       device FP32 2*iters*C*H*W per-pass checkpoints written by
+ *               sgwls_filter (p->inter_storage must be SGWLS_F32)
+ *   lambda, p   as in the forward call (FP32 storage; frac weights need
+ *               alpha_r >= 1, otherwise SGWLS_E_UNSUPPORTED)
+ *   grad_f      device FP32 C x H x W output, dLoss/df (may not alias grad_u)
+ *   grad_g      device FP32 H x W output, dLoss/dg, or NULL
+ *   grad_lambda device pointer to one float, dLoss/dlambda, or NULL
+ *   ws          workspace of sgwls_backward_workspace_bytes bytes, 256-byte
+ *               aligned
+ * Gradients w.r.t. g and lambda are accumulated with floating-point atomics:
+ * their last bits depend on the order of accumulation. */
+sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void* saved, int H, int W, int C,
+                                   float lambda, const sgwls_params* p, void* grad_f, void* grad_g,
+                                   float* grad_lambda, void* ws, size_t ws_bytes, void* stream);
+
 /* One pass like sgwls_filter_pass, for callers that cannot allocate device
  * memory when they filter (a host with a fixed device-memory budget, or a
  * code path that must not enter the allocator): it takes no workspace.  The

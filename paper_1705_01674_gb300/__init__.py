@@ -21,7 +21,8 @@ import torch
 from . import _capi
 from ._capi import SgwlsError, make_params
 
-__all__ = ["sgwls_filter", "sgwls_filter_pass", "workspace_bytes", "launch_count", "make_params", "SgwlsError"]
+__all__ = ["sgwls", "sgwls_filter", "sgwls_filter_pass", "sgwls_filter_backward", "SGWLSFunction",
+           "workspace_bytes", "launch_count", "make_params", "SgwlsError"]
 
 _DT = {torch.float32: _capi.F32, torch.bfloat16: _capi.BF16}
 
@@ -119,3 +120,67 @@ def sgwls_filter_pass(f: torch.Tensor, g: torch.Tensor, lam: float, direction: i
 def launch_count() -> int:
     """Kernels launched by libsgwls.so in this process so far."""
     return int(_capi.lib().sgwls_launch_count())
+
+
+def sgwls_filter_backward(grad_u: torch.Tensor, g: torch.Tensor, saved: torch.Tensor, lam: float, *,
+                          stream: torch.cuda.Stream | None = None, **kw):
+    """dLoss/df, dLoss/dg, dLoss/dlambda through ``sgwls_filter_backward``.
+
+    grad_u: (C,H,W) FP32; g: (H,W) FP32; saved: the (2*iters, C, H, W)
+    checkpoints written by ``sgwls_filter(..., saved=saved)``.
+    Returns (grad_f, grad_g, grad_lambda) with grad_lambda a 0-d tensor."""
+    for x, name in ((grad_u, "grad_u"), (g, "g"), (saved, "saved")):
+        _check_tensor(x, name)
+        if x.dtype != torch.float32:
+            raise TypeError(f"{name} must be float32 for the backward")
+    C, H, W = _chw(grad_u)
+    p = make_params(**kw)
+    lib = _capi.lib()
+    grad_f = torch.empty_like(grad_u)
+    grad_g = torch.empty((H, W), dtype=torch.float32, device=grad_u.device)
+    grad_lam = torch.empty((), dtype=torch.float32, device=grad_u.device)
+    nws = lib.sgwls_backward_workspace_bytes(H, W, C, ctypes.byref(p))
+    ws = torch.empty(max(nws, 1), dtype=torch.uint8, device=grad_u.device)
+    st = stream if stream is not None else torch.cuda.current_stream(grad_u.device)
+    status = lib.sgwls_filter_backward(
+        ctypes.c_void_p(grad_u.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(saved.data_ptr()),
+        H, W, C, ctypes.c_float(float(lam)), ctypes.byref(p), ctypes.c_void_p(grad_f.data_ptr()),
+        ctypes.c_void_p(grad_g.data_ptr()), ctypes.c_void_p(grad_lam.data_ptr()),
+        ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), ctypes.c_void_p(st.cuda_stream))
+    _capi.check(status, "sgwls_filter_backward")
+    return grad_f, grad_g, grad_lam
+
+
+class SGWLSFunction(torch.autograd.Function):
+    """Differentiable SG-WLS: forward through ``sgwls_filter`` with per-pass
+    checkpoints (memory 2*iters images), backward through
+    ``sgwls_filter_backward``.  Gradients for f, g and lambda."""
+
+    @staticmethod
+    def forward(ctx, f, g, lam, kw):
+        lam_f = float(lam)
+        T = int(kw.get("iters", 1))
+        saved = torch.empty((2 * T,) + tuple(f.shape), dtype=torch.float32, device=f.device)
+        u = sgwls_filter(f.contiguous(), g.contiguous(), lam_f, saved=saved, **kw)
+        ctx.save_for_backward(g, saved)
+        ctx.lam = lam_f
+        ctx.kw = kw
+        ctx.lam_is_tensor = isinstance(lam, torch.Tensor)
+        ctx.f_shape = f.shape
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        g, saved = ctx.saved_tensors
+        gu = grad_u.contiguous().reshape(saved.shape[1:]).to(torch.float32)
+        grad_f, grad_g, grad_lam = sgwls_filter_backward(gu, g, saved, ctx.lam, **ctx.kw)
+        gl = grad_lam if ctx.lam_is_tensor else None
+        return grad_f.reshape(ctx.f_shape), grad_g, gl, None
+
+
+def sgwls(f: torch.Tensor, g: torch.Tensor, lam, **kw) -> torch.Tensor:
+    """SG-WLS filter; differentiable w.r.t. f, g and lam (if a tensor)."""
+    needs = f.requires_grad or g.requires_grad or (isinstance(lam, torch.Tensor) and lam.requires_grad)
+    if needs:
+        return SGWLSFunction.apply(f, g, lam, kw)
+    return sgwls_filter(f, g, float(lam), **kw)

@@ -32,26 +32,26 @@ constexpr size_t kSmemBlockTarget = 110 * 1024;   // two blocks per SM
 constexpr size_t kSmemBlockMax = 200 * 1024;
 constexpr int kGMax = 8;
 
-Plan make_plan(int L, int D, int r, int CC, int chunk_lines) {
+Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false) {
   const int bands = (D + (32 - 2 * r) - 1) / (32 - 2 * r);
   // enough chunks for ~kTargetWarps warps in flight: h <= L * bands / target
   int h = std::max(1, (int)(((long long)L * bands) / kTargetWarps));
   // blocks of G = 8 chunk-warps, two blocks per SM: shrink h to fit
-  while (h > 1 && smem_recover(r, CC, h, kGMax) > kSmemBlockTarget) --h;
+  while (h > 1 && smem_recover(r, CC, h, kGMax, bwd) > kSmemBlockTarget) --h;
   if (chunk_lines > 0) h = std::min(chunk_lines, L);
-  while (h > 1 && smem_recover(r, CC, h, 1) > kSmemBlockMax) --h;
+  while (h > 1 && smem_recover(r, CC, h, 1, bwd) > kSmemBlockMax) --h;
   h = std::min(h, L);
   Plan pl;
   pl.h = h;
   pl.P = (L + h - 1) / h;
   int G = 1;
-  while (G < kGMax && G < pl.P && smem_recover(r, CC, h, 2 * G) <= kSmemBlockMax &&
+  while (G < kGMax && G < pl.P && smem_recover(r, CC, h, 2 * G, bwd) <= kSmemBlockMax &&
          smem_summary(r, CC, h, 2 * G) <= kSmemBlockMax)
     G *= 2;
   pl.G = G;
   pl.NG = (pl.P + G - 1) / G;
   pl.smem_sum = smem_summary(r, CC, h, G);
-  pl.smem_rec = smem_recover(r, CC, h, G);
+  pl.smem_rec = smem_recover(r, CC, h, G, bwd);
   return pl;
 }
 
@@ -149,6 +149,7 @@ void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
     a.range_k = p->alpha_r;
   }
   a.eps = p->eps;
+  a.dgk = (float)(1.0 / ((double)p->sigma_r * (double)p->sigma_r));
   // Spatial factor of the pair (p, p+t) with j = p % n: same line -> distance
   // t; next line -> one line over and |4r + 1 - 2j - t| across (the snake
   // turns), for both directions.
@@ -168,6 +169,7 @@ void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
         sp = 1.0 / (pow(sqrt(d2), (double)p->alpha_s) + (double)p->eps);
       }
       a.sp[j * r + t - 1] = (float)(lambda * sp);
+      a.sp0[j * r + t - 1] = (float)sp;
     }
   }
 }
@@ -221,6 +223,8 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.P = pl.P;
     a.ngroups = pl.NG;
     a.in = static_cast<const char*>(in) + (size_t)c0 * plane * dt_size(in_dt);
+    a.in2 = a.in;
+    a.n_in1 = CC;
     a.out = static_cast<char*>(out) + (size_t)c0 * plane * dt_size(out_dt);
     cudaError_t e = launch(a, pl, CC, st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -268,6 +272,128 @@ sgwls_status run_filter(const void* f, const void* g, void* u, int H, int W, int
     if (s != SGWLS_OK) return s;
     cur = dst;
     cur_dt = dst_dt;
+  }
+  return SGWLS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Backward (adjoint) of the filter.
+
+namespace {
+
+struct BwdLayout {
+  size_t img0, img1, gbuf, summ, xsep, mdata, total;
+};
+
+BwdLayout make_bwd_layout(int H, int W, int C, const sgwls_params* p) {
+  const int r = p->r;
+  const int nch = std::min(C, 2);
+  size_t summ = 0, xsep = 0, mdata = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int L = dir == 0 ? H : W;
+    const int D = dir == 0 ? W : H;
+    const int nsys = D - 2 * r;
+    for (int c0 = 0; c0 < C; c0 += 2) {
+      const int CC = 2 * std::min(2, C - c0);
+      const Plan pl = make_plan(L, D, r, CC, p->chunk_lines, true);
+      summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
+      xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
+      mdata = std::max(mdata, (size_t)pl.NG * std::max(pl.G - 1, 1) * n_mfields(r, CC) * nsys * sizeof(float));
+    }
+  }
+  (void)nch;
+  const size_t img = align256((size_t)C * H * W * sizeof(float));
+  BwdLayout lo;
+  lo.img0 = 0;
+  lo.img1 = img;
+  lo.gbuf = 2 * img;
+  lo.summ = lo.gbuf + align256(((size_t)H * W + 64) * sizeof(float));
+  lo.xsep = lo.summ + align256(summ);
+  lo.mdata = lo.xsep + align256(xsep);
+  lo.total = lo.mdata + align256(mdata);
+  return lo;
+}
+
+// vbar' = vbar / (number of subsystems containing the pixel), for the pass
+// direction `dir` (the transpose of step 4 of Sec. 2.3).
+__global__ void k_bwd_scale(const float* __restrict__ vin, float* __restrict__ vout, int H, int W, int C, int r,
+                            int dir) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long plane = (long long)H * W;
+  if (i >= plane * C) return;
+  const long long pix = i % plane;
+  const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
+  const int o = dir == 0 ? x : y;
+  const int D = dir == 0 ? W : H;
+  const int lo = max(r, o - r), hi = min(D - 1 - r, o + r);
+  vout[i] = vin[i] / (float)(hi - lo + 1);
+}
+
+}  // namespace
+
+sgwls_status run_backward(const float* grad_u, const float* g, const float* saved, int H, int W, int C,
+                          float lambda, const sgwls_params* p, float* grad_f, float* grad_g, float* grad_lam,
+                          void* ws, cudaStream_t st) {
+  const BwdLayout lo = make_bwd_layout(H, W, C, p);
+  char* wsb = static_cast<char*>(ws);
+  float* w0 = reinterpret_cast<float*>(wsb + lo.img0);   // vbar / count
+  float* w1 = reinterpret_cast<float*>(wsb + lo.img1);   // vbar of the next pass down
+  float* gb = reinterpret_cast<float*>(wsb + lo.gbuf);
+  if (!grad_g) grad_g = gb;
+  if (!grad_lam) grad_lam = gb + (size_t)H * W;
+  const long long plane = (long long)H * W;
+  const long long count = plane * C;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(grad_g, 0, (size_t)plane * sizeof(float), st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(grad_lam, 0, sizeof(float), st)) != cudaSuccess) return cuda_fail(e);
+  const int npass = 2 * p->iters;
+  if (npass == 0) {
+    e = cudaMemcpyAsync(grad_f, grad_u, (size_t)count * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? SGWLS_OK : cuda_fail(e);
+  }
+  const PassLauncher launch = launcher_for(p->r);
+  const float* vbar = grad_u;
+  for (int t = npass - 1; t >= 0; --t) {
+    const int dir = ((t & 1) == 0) ? p->axis_order : 1 - p->axis_order;
+    k_bwd_scale<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(vbar, w0, H, W, C, p->r, dir);
+    __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    float* dst = t == 0 ? grad_f : w1;
+    const float* uin = saved + (size_t)t * count;
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.plane = plane;
+    a.H = H;
+    a.W = W;
+    a.g_dt = DT_F32;
+    a.in_dt = DT_F32;
+    a.out_dt = DT_F32;
+    a.dir = dir;
+    a.L = dir == 0 ? H : W;
+    a.D = dir == 0 ? W : H;
+    a.nsys = a.D - 2 * p->r;
+    a.summ = reinterpret_cast<float*>(wsb + lo.summ);
+    a.xsep = reinterpret_cast<float*>(wsb + lo.xsep);
+    a.mdata = reinterpret_cast<float*>(wsb + lo.mdata);
+    a.grad_g = grad_g;
+    a.grad_lam = grad_lam;
+    fill_weights(a, p, lambda);
+    for (int c0 = 0; c0 < C; c0 += 2) {
+      const int nch = std::min(2, C - c0);
+      const Plan pl = make_plan(a.L, a.D, p->r, 2 * nch, p->chunk_lines, true);
+      a.h = pl.h;
+      a.P = pl.P;
+      a.ngroups = pl.NG;
+      a.in = uin + (size_t)c0 * plane;
+      a.in2 = w0 + (size_t)c0 * plane;
+      a.n_in1 = nch;
+      a.out = dst + (size_t)c0 * plane;
+      e = launch(a, pl, -2 * nch, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? (pl.NG > 1 ? 3 : 2) : 1), __ATOMIC_RELAXED);
+    }
+    vbar = dst;
   }
   return SGWLS_OK;
 }
@@ -342,5 +468,31 @@ sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int
 }
 
 unsigned long long sgwls_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+}  // extern "C"
+
+extern "C" {
+
+size_t sgwls_backward_workspace_bytes(int H, int W, int C, const sgwls_params* p) {
+  if (check_params(H, W, C, p) != SGWLS_OK) return 0;
+  return make_bwd_layout(H, W, C, p).total;
+}
+
+sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void* saved, int H, int W, int C,
+                                   float lambda, const sgwls_params* p, void* grad_f, void* grad_g,
+                                   float* grad_lambda, void* ws, size_t ws_bytes, void* stream) {
+  sgwls_status s = check_params(H, W, C, p);
+  if (s != SGWLS_OK) return s;
+  if (!grad_u || !g || !grad_f || (p->iters > 0 && !saved)) return SGWLS_E_INVALID;
+  if (grad_f == grad_u) return SGWLS_E_INVALID;
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
+  if (p->storage != SGWLS_F32 || p->inter_storage != SGWLS_F32) return SGWLS_E_UNSUPPORTED;
+  if (p->weight == SGWLS_W_FRAC && p->alpha_r < 1.f) return SGWLS_E_UNSUPPORTED;
+  const size_t need = make_bwd_layout(H, W, C, p).total;
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
+  return run_backward(static_cast<const float*>(grad_u), static_cast<const float*>(g),
+                      static_cast<const float*>(saved), H, W, C, lambda, p, static_cast<float*>(grad_f),
+                      static_cast<float*>(grad_g), grad_lambda, ws, static_cast<cudaStream_t>(stream));
+}
 
 }  // extern "C"

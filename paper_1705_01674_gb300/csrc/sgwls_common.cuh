@@ -50,6 +50,17 @@ struct PassArgs {
   float* xsep;         // group separators  [NG-1][r*CC][nsys]
   float* mdata;        // merge factors     [NG][G-1][MFields::N][nsys]
   int early_stage;     // k_recover may stage its tile before griddep_wait
+  // Planes 0 .. n_in1-1 come from `in`, planes n_in1 .. CC-1 from `in2`
+  // (the backward solves u = A^-1 f and v = A^-1 ubar together).
+  const void* in2;
+  int n_in1;
+  // backward only: accumulated d loss / d guidance (FP32, the pass's pixel
+  // grid) and d loss / d lambda (one float); the spatial factor without
+  // lambda, sp0[j * r + t - 1]; dgk = 1 / sigma_r^2 (exp weights)
+  float* grad_g;
+  float* grad_lam;
+  float sp0[(2 * kRMax + 1) * kRMax];
+  float dgk;
 };
 
 __device__ __forceinline__ float ld_px(const void* base, long long idx, int dt) {

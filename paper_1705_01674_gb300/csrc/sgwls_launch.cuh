@@ -18,12 +18,14 @@ inline size_t tile_floats(int r, int CC, int h, int G) { return (size_t)(CC + 1)
 inline size_t smem_summary(int r, int CC, int h, int G) {
   return 4 * (tile_floats(r, CC, h, G) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
 }
-inline size_t smem_recover(int r, int CC, int h, int G) {
+inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
   const int n = 2 * r + 1;
   const size_t merge = (size_t)(G - 1) * (3 * r * r + r * CC) * 32 + 2 * (size_t)r * CC * 32;
-  const size_t otile = (size_t)CC * (32 - 2 * r) * ((G * h) | 1);
+  const int nout = bwd ? CC / 2 : CC;
+  const size_t otile = (size_t)nout * (32 - 2 * r) * ((G * h) | 1);
+  const size_t gacc = bwd ? (size_t)(G * h + 2) * (32 + 2 * r) : 0;
   return 4 * (tile_floats(r, CC, h, G) + (size_t)G * 2 * r * CC * 32 + merge + (size_t)G * h * n * (r + CC) * 32 +
-              otile);
+              otile + gacc);
 }
 
 constexpr size_t kReducedSmemMax = 96 * 1024;
@@ -55,7 +57,7 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int R, int CC>
+template <int R, int CC, bool BWD = false>
 cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   static_assert(R >= 1 && R <= kRMax, "radius");
   constexpr int OB = 32 - 2 * R;
@@ -77,12 +79,14 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
       if (e != cudaSuccess) return e;
     }
   }
-  if ((e = set_smem(k_recover<R, CC>, pl.smem_rec)) != cudaSuccess) return e;
-  e = launch_pdl(k_recover<R, CC>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), pl.smem_rec, st, b);
+  if ((e = set_smem(k_recover<R, CC, BWD>, pl.smem_rec)) != cudaSuccess) return e;
+  e = launch_pdl(k_recover<R, CC, BWD>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), pl.smem_rec, st, b);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
+// CC > 0: forward pass over CC channels.  CC < 0: backward pass over -CC
+// right-hand sides (u and v planes of -CC/2 channels).
 template <int R>
 cudaError_t launch_pass_r(const PassArgs& a, const Plan& pl, int CC, cudaStream_t st) {
   switch (CC) {
@@ -90,6 +94,8 @@ cudaError_t launch_pass_r(const PassArgs& a, const Plan& pl, int CC, cudaStream_
     case 2: return launch_pass_rc<R, 2>(a, pl, st);
     case 3: return launch_pass_rc<R, 3>(a, pl, st);
     case 4: return launch_pass_rc<R, 4>(a, pl, st);
+    case -2: return launch_pass_rc<R, 2, true>(a, pl, st);
+    case -4: return launch_pass_rc<R, 4, true>(a, pl, st);
     default: return cudaErrorInvalidValue;
   }
 }

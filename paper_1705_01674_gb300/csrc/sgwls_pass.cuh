@@ -93,6 +93,15 @@ __host__ __device__ constexpr int tile_pitch_max(int r) {
   return tile_pitch(r, 0) > tile_pitch(r, 1) ? tile_pitch(r, 0) : tile_pitch(r, 1);
 }
 
+// Base of tile plane pl: estimate planes from `in` (then `in2`), the
+// guidance last.  `elem` is the element size of the estimate planes.
+template <int CC>
+__device__ __forceinline__ const char* plane_base(const PassArgs& a, int pl, int elem) {
+  if (pl < a.n_in1) return static_cast<const char*>(a.in) + (size_t)pl * a.plane * elem;
+  if (pl < CC) return static_cast<const char*>(a.in2) + (size_t)(pl - a.n_in1) * a.plane * elem;
+  return static_cast<const char*>(a.g);
+}
+
 // Mixed storage types (BF16 guidance with FP32 estimates): plain loop.
 template <int CC>
 __device__ __noinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, int ncol) {
@@ -107,7 +116,7 @@ __device__ __noinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, 
     float v = 0.f;
     if (line >= 0 && line < a.L && off >= 0 && off < a.D) {
       const long long pix = pix_index(a, line, off);
-      v = pl < CC ? ld_px(a.in, pix + pl * a.plane, a.in_dt) : ld_px(a.g, pix, a.g_dt);
+      v = pl < CC ? ld_px(plane_base<CC>(a, pl, a.in_dt == DT_F32 ? 4 : 2), pix, a.in_dt) : ld_px(a.g, pix, a.g_dt);
     }
     t.p[(pl * t.ntl + tl) * t.pitch + col] = v;
   }
@@ -131,8 +140,7 @@ __device__ __noinline__ void stage_tile_t(const PassArgs& a, const Tile& t, int 
   constexpr int U = 4;
 #pragma unroll 1
   for (int pl = 0; pl <= CC; ++pl) {
-    const char* base = static_cast<const char*>(pl < CC ? a.in : a.g) +
-                       (pl < CC ? (size_t)pl * a.plane * (F32 ? 4 : 2) : 0);
+    const char* base = plane_base<CC>(a, pl, F32 ? 4 : 2);
     float* dplane = t.p + pl * t.ntl * t.pitch;
     if (a.dir == 0) {
       // rows = lines; 2 columns per lane cover ncol <= 64
@@ -204,7 +212,7 @@ __device__ __noinline__ void stage_tile_async(const PassArgs& a, const Tile& t) 
   const long long W = a.W;
 #pragma unroll 1
   for (int pl = 0; pl <= CC; ++pl) {
-    const float* base = static_cast<const float*>(pl < CC ? a.in : a.g) + (pl < CC ? (size_t)pl * a.plane : 0);
+    const float* base = reinterpret_cast<const float*>(plane_base<CC>(a, pl, 4));
     float* dplane = t.p + pl * t.ntl * t.pitch;
     if (a.dir == 0) {
       // flat over (line, offset); NCOL is a compile-time constant
@@ -256,7 +264,7 @@ __device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t)
   const long long W = a.W;
 #pragma unroll 1
   for (int pl = 0; pl <= CC; ++pl) {
-    const float* base = static_cast<const float*>(pl < CC ? a.in : a.g) + (pl < CC ? (size_t)pl * a.plane : 0);
+    const float* base = reinterpret_cast<const float*>(plane_base<CC>(a, pl, 4));
     float* dplane = t.p + pl * t.ntl * t.pitch;
     if (a.dir == 0) {
       constexpr int PQ = (NCOL + 3 + 3) / 4;
@@ -332,8 +340,8 @@ __device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t)
 template <int CC, int NCOL>
 __device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t) {
   const int ncol = NCOL;
-  const bool aligned = ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 &&
-                       (a.W & 3) == 0;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.in2) |
+                         reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 && (a.W & 3) == 0;
   if (a.in_dt == DT_F32 && a.g_dt == DT_F32 && aligned)
     stage_tile_vec<CC, NCOL>(a, t);
   else if (a.in_dt == DT_F32 && a.g_dt == DT_F32)
@@ -727,8 +735,8 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int
   t.ntl = min((c0 + G) * a.h, a.L) + 1 - t.tl0;
   t.off0 = off0;
   const bool vec = a.dir == 0 && a.in_dt == DT_F32 && a.g_dt == DT_F32 &&
-                   ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 &&
-                   (a.W & 3) == 0;
+                   ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.in2) |
+                     reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 && (a.W & 3) == 0;
   t.cs = vec ? (off0 & 3) : 0;
   t.pitch = tile_pitch(r, a.dir);
   t.p = p;
@@ -1028,12 +1036,19 @@ __global__ void __launch_bounds__(256) k_reduced(const __grid_constant__ PassArg
 // k_recover: back-fill of the group's separators, exact interior solves with
 // known separators, write-back and averaging.  Grid (ceil(D / OB), NG),
 // block (32, G); lane = centre, warp = chunk.
-template <int R, int CC>
+//
+// BWD: the adjoint of the pass.  The CC right-hand sides are u-planes (the
+// pass input, NOUT = CC/2 channels) and v-planes (dLoss/d(pass output) /
+// count); the kernel writes dLoss/d(pass input) = sum over subsystems of v,
+// and accumulates dLoss/dG and dLoss/dlambda from every pair of entries.
+template <int R, int CC, bool BWD = false>
 __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArgs a) {
   constexpr int n = 2 * R + 1;
   constexpr int NF = R + CC;       // stored per entry: L[p, p-1..p-R], z
   constexpr int OB = 32 - 2 * R;   // outputs per warp
   constexpr int XS = R * CC;       // values per separator
+  constexpr int NOUT = BWD ? CC / 2 : CC;   // output channels
+  constexpr int NCOL = 32 + 2 * R;
   using MF = MFields<R, CC>;
   extern __shared__ float smem[];
   const int lane = threadIdx.x;
@@ -1136,6 +1151,13 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
   const int oline0 = c0 * a.h;
   const int opitch = (G * a.h) | 1;
   float* const otile = store + G * mcap * NF * 32;
+  float* const gacc = otile + NOUT * OB * opitch;   // BWD: [ntl][NCOL] dLoss/dG
+  float lam_acc = 0.f;
+  const bool owner = valid && lane >= R && lane < 32 - R;
+  if constexpr (BWD) {
+    for (int i = threadIdx.y * 32 + lane; i < t.ntl * NCOL; i += G * 32) gacc[i] = 0.f;
+    __syncthreads();
+  }
 
   if (threadIdx.y < nch) {  // warp-uniform
   const Chunk q = make_chunk<R>(a, c);
@@ -1230,6 +1252,37 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
   }
   float Lb[R][R] = {};   // Lb[u-1][t-1] = L[p+u, p+u-t]
   float xw[R][CC] = {};  // x of entries p+1 .. p+R (interior only)
+  float xpw[R][CC] = {}; // BWD: x of entries p+1 .. p+R of the chunk (with its separator)
+  // BWD pair term of entries p (line lp, entry jp) and q = p + tq, owned by
+  // this chunk: dLoss/dG and dLoss/dlambda contributions.
+  auto pair_terms = [&](auto oddp, int lp, int jp, const float (&xp)[CC], int tq, const float (&xq)[CC]) {
+    constexpr bool ODDP = decltype(oddp)::value;
+    const int jq = jp + tq;
+    const int lq = jq < n ? lp : lp + 1;
+    const int colp = lane + ecol<R, ODDP>(jp);
+    const int colq = lane + (jq < n ? ecol<R, ODDP>(jq) : ecol<R, !ODDP>(jq - n));
+    const float gp = t.row(CC, lp)[colp];
+    const float gq = t.row(CC, lq)[colq];
+    float sdot = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < NOUT; ++ch) sdot += (xp[NOUT + ch] - xq[NOUT + ch]) * (xp[ch] - xq[ch]);
+    const float dg = gp - gq;
+    const float sp = a.sp0[jp * R + tq - 1];
+    float w, dw;
+    if (a.weight == 0) {
+      w = sp * fast_ex2(dg * dg * a.range_k);
+      dw = -w * dg * a.dgk;
+    } else {
+      const float ad = fabsf(dg);
+      const float hh = 1.0f / (powf(ad, a.range_k) + a.eps);
+      w = sp * hh;
+      dw = ad > 0.f ? -sp * hh * hh * a.range_k * powf(ad, a.range_k - 1.0f) * (dg > 0.f ? 1.f : -1.f) : 0.f;
+    }
+    lam_acc -= w * sdot;
+    const float gb = -a.lam * sdot * dw;
+    atomicAdd_block(&gacc[(lp - t.tl0) * NCOL + colp], gb);
+    atomicAdd_block(&gacc[(lq - t.tl0) * NCOL + colq], -gb);
+  };
   const long long ostride = a.dir == 0 ? 1 : a.W;
   const long long lstride = a.dir == 0 ? a.W : 1;
   float* const outp = reinterpret_cast<float*>(a.out);
@@ -1267,6 +1320,14 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
         for (int tt = 0; tt < R; ++tt) Lb[0][tt] = Lrow[tt];
         push_vec<R, CC>(xw, x);
       }
+      if constexpr (BWD) {
+        if (owner) {
+#pragma unroll
+          for (int tq = 1; tq <= R; ++tq)
+            if (!LAST || j + tq < n) pair_terms(odd, line, j, x, tq, xpw[tq - 1]);
+        }
+        push_vec<R, CC>(xpw, x);
+      }
       if constexpr (XREG) {
 #pragma unroll
         for (int ch = 0; ch < CC; ++ch) xl[j][ch] = x[ch];
@@ -1277,14 +1338,16 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
     }
     // inverse construction + averaging: value at across-offset kc - R + e
     const long long pix = (long long)line * lstride + (long long)o * ostride;
+    constexpr int CH0 = BWD ? NOUT : 0;   // BWD: the v-planes
+    const float scale = BWD ? 1.f : inv_cnt;
 #pragma unroll
-    for (int ch = 0; ch < CC; ++ch) {
+    for (int ch = 0; ch < NOUT; ++ch) {
       float voff[n];
 #pragma unroll
       for (int e2 = 0; e2 < n; ++e2) {
         float v;
-        if constexpr (XREG) v = xl[ecol<R, ODD>(e2)][ch];
-        else v = lslot[ecol<R, ODD>(e2) * NF * 32 + (R + ch) * 32];
+        if constexpr (XREG) v = xl[ecol<R, ODD>(e2)][CH0 + ch];
+        else v = lslot[ecol<R, ODD>(e2) * NF * 32 + (R + CH0 + ch) * 32];
         voff[e2] = valid ? v : 0.f;
       }
       float sum = voff[R];
@@ -1295,20 +1358,39 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
       }
       if (writer) {
         if (a.dir != 0)
-          otile[(ch * OB + (lane - R)) * opitch + (line - oline0)] = sum * inv_cnt;
+          otile[(ch * OB + (lane - R)) * opitch + (line - oline0)] = sum * scale;
         else if (a.out_dt == DT_F32)
-          outp[pix + ch * a.plane] = sum * inv_cnt;
+          outp[pix + ch * a.plane] = sum * scale;
         else
-          st_px(a.out, pix + ch * a.plane, a.out_dt, sum * inv_cnt);
+          st_px(a.out, pix + ch * a.plane, a.out_dt, sum * scale);
       }
     }
   });
+  if constexpr (BWD) {
+    // pairs from the separator above into this chunk's first entries
+    if (q.top && owner) {
+      const int lp = q.line0 - 1;
+      auto virt = [&](auto oddp) {
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+          float xv[CC];
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch) xv[ch] = xT[R - d][ch];
+#pragma unroll
+          for (int tq = 1; tq <= R; ++tq)
+            if (tq >= d) pair_terms(oddp, lp, n - d, xv, tq, xpw[tq - 1]);
+          push_vec<R, CC>(xpw, xv);
+        }
+      };
+      if (lp & 1) virt(std::true_type{}); else virt(std::false_type{});
+    }
+  }
   }  // this warp's chunk
 
+  if (a.dir != 0 || BWD) __syncthreads();
   if (a.dir != 0) {
-    __syncthreads();
     const int nl = min((c0 + G) * a.h, a.L) - oline0;
-    for (int row = threadIdx.y; row < CC * OB; row += G) {
+    for (int row = threadIdx.y; row < NOUT * OB; row += G) {
       const int ch = row / OB;
       const int o = row - ch * OB;
       const int oabs = blockIdx.x * OB + o;
@@ -1322,6 +1404,21 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
         else
           st_px(a.out, gbase + l, a.out_dt, src[l]);
       }
+    }
+  }
+  if constexpr (BWD) {
+    // dLoss/dlambda: warp sum, one atomic per warp
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) lam_acc += __shfl_down_sync(0xffffffffu, lam_acc, d);
+    if (lane == 0 && lam_acc != 0.f) atomicAdd(a.grad_lam, lam_acc);
+    // dLoss/dG of this block's pairs
+    for (int i = threadIdx.y * 32 + lane; i < t.ntl * NCOL; i += G * 32) {
+      const float v = gacc[i];
+      if (v == 0.f) continue;
+      const int tl = i / NCOL;
+      const int col = i - tl * NCOL;
+      const int line = t.tl0 + tl, off = t.off0 + col;
+      if (line >= 0 && line < a.L && off >= 0 && off < a.D) atomicAdd(a.grad_g + pix_index(a, line, off), v);
     }
   }
 }
