@@ -133,6 +133,31 @@ sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int
                                float lambda, const sgwls_params* p, int direction, void* ws,
                                size_t ws_bytes, void* stream);
 
+/* One image of a batched call (all pointers device pointers). */
+typedef struct {
+  const void* f;   /* C x H x W input (p->storage)                   */
+  const void* g;   /* H x W guidance (p->storage)                    */
+  void* u;         /* C x H x W output (p->storage), not aliasing f  */
+  int H, W, C;     /* C must be the same for every image, 1 <= C <= 4 */
+  float lambda;    /* per-image lambda >= 0                           */
+  void* saved;     /* must be NULL (no checkpoints in batched calls)  */
+} sgwls_image;
+
+/* Workspace bytes sgwls_filter_batched needs for these images (0 if the
+ * arguments are invalid).  Host-only; `imgs` is a host array. */
+size_t sgwls_batched_workspace_bytes(int B, const sgwls_image* imgs, const sgwls_params* p);
+
+/* SG-WLS filter of B images of uneven sizes (Sec. 2.3 per image, each with
+ * its own lambda, the same r / T / weights).  Every pass runs as one launch
+ * per kernel over all images (up to 64 images per launch; larger batches use
+ * several): each block finds its image from the per-image block ranges
+ * carried in the kernel arguments, so no descriptor is uploaded and the call
+ * can be captured in a CUDA graph.
+ *   imgs  host array of B images; ws: workspace of
+ *         sgwls_batched_workspace_bytes bytes, 256-byte aligned. */
+sgwls_status sgwls_filter_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws,
+                                  size_t ws_bytes, void* stream);
+
 /* Workspace bytes sgwls_filter_backward needs (0 if the arguments are
  * invalid).  Host-only. */
 size_t sgwls_backward_workspace_bytes(int H, int W, int C, const sgwls_params* p);

@@ -21,7 +21,8 @@ import torch
 from . import _capi
 from ._capi import SgwlsError, make_params
 
-__all__ = ["sgwls", "sgwls_filter", "sgwls_filter_pass", "sgwls_filter_backward", "SGWLSFunction",
+__all__ = ["sgwls", "sgwls_filter", "sgwls_filter_pass", "sgwls_filter_backward", "sgwls_filter_batched",
+           "batched_workspace_bytes", "SGWLSFunction",
            "workspace_bytes", "launch_count", "make_params", "SgwlsError"]
 
 _DT = {torch.float32: _capi.F32, torch.bfloat16: _capi.BF16}
@@ -184,3 +185,48 @@ def sgwls(f: torch.Tensor, g: torch.Tensor, lam, **kw) -> torch.Tensor:
     if needs:
         return SGWLSFunction.apply(f, g, lam, kw)
     return sgwls_filter(f, g, float(lam), **kw)
+
+
+def _image_table(fs, gs, lams, outs):
+    n = len(fs)
+    if not (len(gs) == n and len(lams) == n and len(outs) == n):
+        raise ValueError("fs, gs, lams (and outs) must have the same length")
+    tab = (_capi.SgwlsImage * n)()
+    for i, (f, g, lam, u) in enumerate(zip(fs, gs, lams, outs)):
+        _check_tensor(f, f"fs[{i}]")
+        _check_tensor(g, f"gs[{i}]")
+        C, H, W = _chw(f)
+        if tuple(g.shape) != (H, W) or g.dtype != f.dtype:
+            raise ValueError(f"gs[{i}] must be (H, W) with the dtype of fs[{i}]")
+        tab[i].f, tab[i].g, tab[i].u = f.data_ptr(), g.data_ptr(), u.data_ptr()
+        tab[i].H, tab[i].W, tab[i].C = H, W, C
+        tab[i].lam = float(lam)
+        tab[i].saved = None
+    return tab
+
+
+def batched_workspace_bytes(fs, gs, lams, **kw) -> int:
+    tab = _image_table(fs, gs, lams, fs)
+    p = make_params(**kw)
+    return int(_capi.lib().sgwls_batched_workspace_bytes(len(fs), tab, ctypes.byref(p)))
+
+
+def sgwls_filter_batched(fs, gs, lams, *, outs=None, workspace: torch.Tensor | None = None,
+                         stream: torch.cuda.Stream | None = None, **kw):
+    """SG-WLS of many images of uneven sizes through ``sgwls_filter_batched``
+    (one launch per kernel per pass over all images).  fs / gs / lams:
+    sequences of (C,H,W) inputs, (H,W) guidance tensors and lambdas."""
+    if outs is None:
+        outs = [torch.empty_like(f) for f in fs]
+    kw.setdefault("storage", "bf16" if fs[0].dtype == torch.bfloat16 else "f32")
+    tab = _image_table(fs, gs, lams, outs)
+    p = make_params(**kw)
+    lib = _capi.lib()
+    nws = lib.sgwls_batched_workspace_bytes(len(fs), tab, ctypes.byref(p))
+    if workspace is None or workspace.numel() < nws:
+        workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=fs[0].device)
+    st = stream if stream is not None else torch.cuda.current_stream(fs[0].device)
+    status = lib.sgwls_filter_batched(len(fs), tab, ctypes.byref(p), ctypes.c_void_p(workspace.data_ptr()),
+                                      ctypes.c_size_t(workspace.numel()), ctypes.c_void_p(st.cuda_stream))
+    _capi.check(status, "sgwls_filter_batched")
+    return outs

@@ -6,11 +6,29 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "../../include/sgwls.h"
 #include "sgwls_launch.cuh"
 
 namespace sgwls {
+
+cudaError_t set_smem_raw(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = done[{kernel, dev}];
+  if (cur >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 namespace {
 
 thread_local char g_cuda_err[256] = "";
@@ -277,6 +295,214 @@ sgwls_status run_filter(const void* f, const void* g, void* u, int H, int W, int
 }
 
 // ---------------------------------------------------------------------------
+// Batched filter: many images of uneven sizes, one launch per kernel per pass.
+
+namespace {
+
+BatchLauncher batch_launcher_for(int r) {
+  switch (r) {
+    case 1: return launch_batch_r1;
+    case 2: return launch_batch_r2;
+    case 3: return launch_batch_r3;
+    case 4: return launch_batch_r4;
+    case 5: return launch_batch_r5;
+    case 6: return launch_batch_r6;
+    case 7: return launch_batch_r7;
+    case 8: return launch_batch_r8;
+    default: return nullptr;
+  }
+}
+
+// Lines per chunk shared by every image of a batch (blocks of kGMax chunks,
+// two blocks per SM).
+int batch_h(int r, int CC) {
+  int h = 64;
+  while (h > 1 && smem_recover(r, CC, h, kGMax) > kSmemBlockTarget) --h;
+  return h;
+}
+
+Plan batch_plan(int L, int r, int CC, int h0) {
+  Plan pl;
+  pl.h = std::min(h0, L);
+  pl.P = (L + pl.h - 1) / pl.h;
+  pl.G = kGMax;
+  pl.NG = (pl.P + kGMax - 1) / kGMax;
+  pl.smem_sum = smem_summary(r, CC, h0, kGMax);
+  pl.smem_rec = smem_recover(r, CC, h0, kGMax);
+  return pl;
+}
+
+struct BatchImgLayout {
+  size_t img, summ, xsep, mdata, end;
+};
+
+// Workspace of image i starts at `base`; returns its layout.
+BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_params* p) {
+  const int r = p->r;
+  const int h0 = batch_h(r, C);
+  size_t summ = 0, xsep = 0, mdata = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int L = dir == 0 ? H : W;
+    const int D = dir == 0 ? W : H;
+    const int nsys = D - 2 * r;
+    const Plan pl = batch_plan(L, r, C, h0);
+    summ = std::max(summ, (size_t)pl.NG * n_fields(r, C) * nsys * sizeof(float));
+    xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * C * nsys * sizeof(float));
+    mdata = std::max(mdata, (size_t)pl.NG * (kGMax - 1) * n_mfields(r, C) * nsys * sizeof(float));
+  }
+  const int n_img = (p->iters > 0) ? (p->inter_storage == p->storage ? 1 : 2) : 0;
+  BatchImgLayout lo;
+  lo.img = base;
+  lo.summ = lo.img + align256((size_t)n_img * C * H * W * dt_size(p->inter_storage));
+  lo.xsep = lo.summ + align256(summ);
+  lo.mdata = lo.xsep + align256(xsep);
+  lo.end = lo.mdata + align256(mdata);
+  return lo;
+}
+
+sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) {
+  if (B < 1 || !imgs || !p) return SGWLS_E_INVALID;
+  const int C = imgs[0].C;
+  if (C < 1 || C > kGroupMax) return C < 1 ? SGWLS_E_SHAPE : SGWLS_E_UNSUPPORTED;
+  for (int i = 0; i < B; ++i) {
+    const sgwls_image& im = imgs[i];
+    sgwls_status s = check_params(im.H, im.W, im.C, p);
+    if (s != SGWLS_OK) return s;
+    if (im.C != C) return SGWLS_E_UNSUPPORTED;
+    if (!im.f || !im.g || !im.u || im.f == im.u) return SGWLS_E_INVALID;
+    if (!(im.lambda >= 0.f) || !isfinite(im.lambda)) return SGWLS_E_INVALID;
+    if (im.saved) return SGWLS_E_UNSUPPORTED;
+  }
+  return SGWLS_OK;
+}
+
+size_t batch_workspace(int B, const sgwls_image* imgs, const sgwls_params* p) {
+  size_t off = 0;
+  for (int i = 0; i < B; ++i) off = batch_img_layout(off, imgs[i].H, imgs[i].W, imgs[i].C, p).end;
+  return off;
+}
+
+}  // namespace
+
+sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st) {
+  const int C = imgs[0].C;
+  const int r = p->r;
+  const int sdt = p->storage, idt = p->inter_storage;
+  char* wsb = static_cast<char*>(ws);
+  if (p->iters == 0) {
+    for (int i = 0; i < B; ++i) {
+      sgwls_status s = copy_image(imgs[i].f, sdt, imgs[i].u, sdt, (long long)imgs[i].H * imgs[i].W * C, st);
+      if (s != SGWLS_OK) return s;
+    }
+    return SGWLS_OK;
+  }
+  const int h0 = batch_h(r, C);
+  const BatchLauncher launch = batch_launcher_for(r);
+  const int OB = 32 - 2 * r;
+  const int npass = 2 * p->iters;
+  std::vector<BatchImgLayout> lay(B);
+  {
+    size_t off = 0;
+    for (int i = 0; i < B; ++i) {
+      lay[i] = batch_img_layout(off, imgs[i].H, imgs[i].W, C, p);
+      off = lay[i].end;
+    }
+  }
+  static thread_local BatchArgs batch_args;   // host-side argument block (the kernels get a copy)
+  BatchArgs* ba = &batch_args;
+  for (int t = 0; t < npass; ++t) {
+    const int dir = ((t & 1) == 0) ? p->axis_order : 1 - p->axis_order;
+    for (int i0 = 0; i0 < B; i0 += kBatchMax) {
+      const int nb = std::min(kBatchMax, B - i0);
+      memset(ba, 0, sizeof(BatchArgs));
+      PassArgs& a = ba->base;
+      a.dir = dir;
+      a.in_dt = t == 0 ? sdt : idt;
+      a.g_dt = sdt;
+      a.n_in1 = C;
+      fill_weights(a, p, 1.0f);   // sp0 (lambda applied per image)
+      ba->nimg = nb;
+      BatchLaunch bl = {};
+      bl.G = kGMax;
+      size_t red_max = 0;
+      int b[3] = {0, 0, 0};
+      for (int k = 0; k < nb; ++k) {
+        const sgwls_image& im = imgs[i0 + k];
+        const BatchImgLayout& lo = lay[i0 + k];
+        ImgDesc& d = ba->img[k];
+        const size_t count = (size_t)im.H * im.W * C;
+        const size_t ib = count * dt_size(idt);
+        void* img = wsb + lo.img;
+        const void* src;
+        void* dst;
+        int dst_dt;
+        if (t == 0) {
+          src = im.f;
+        } else if (idt == sdt) {
+          src = ((npass - t) & 1) ? img : im.u;
+        } else {
+          src = static_cast<char*>(img) + (size_t)((t - 1) & 1) * ib;
+        }
+        if (t == npass - 1) {
+          dst = im.u;
+          dst_dt = sdt;
+        } else if (idt == sdt) {
+          dst = ((npass - 1 - t) & 1) ? img : im.u;
+          dst_dt = sdt;
+        } else {
+          dst = static_cast<char*>(img) + (size_t)(t & 1) * ib;
+          dst_dt = idt;
+        }
+        (void)dst_dt;
+        d.in = src;
+        d.g = im.g;
+        d.out = dst;
+        d.summ = reinterpret_cast<float*>(wsb + lo.summ);
+        d.xsep = reinterpret_cast<float*>(wsb + lo.xsep);
+        d.mdata = reinterpret_cast<float*>(wsb + lo.mdata);
+        d.plane = (long long)im.H * im.W;
+        d.H = im.H;
+        d.W = im.W;
+        d.L = dir == 0 ? im.H : im.W;
+        d.D = dir == 0 ? im.W : im.H;
+        d.nsys = d.D - 2 * r;
+        const Plan pl = batch_plan(d.L, r, C, h0);
+        d.h = pl.h;
+        d.P = pl.P;
+        d.ngroups = pl.NG;
+        d.lam = im.lambda;
+        d.nbx[0] = (d.nsys + 31) / 32;
+        d.nbx[1] = (d.nsys + 31) / 32;
+        d.nbx[2] = (d.D + OB - 1) / OB;
+        d.b0[0] = b[0];
+        d.b0[1] = b[1];
+        d.b0[2] = b[2];
+        b[0] += d.nbx[0] * pl.NG;
+        b[1] += d.nbx[1];
+        b[2] += d.nbx[2] * pl.NG;
+        bl.any_multi |= pl.P > 1;
+        bl.any_red |= pl.NG > 1;
+        red_max = std::max(red_max, (size_t)pl.NG * n_fields(r, C) * 32 * sizeof(float));
+        bl.smem[0] = pl.smem_sum;
+        bl.smem[2] = pl.smem_rec;
+      }
+      // the output type of intermediate passes is the intermediate type
+      a.out_dt = (t == npass - 1) ? sdt : (idt == sdt ? sdt : idt);
+      bl.nblk[0] = b[0];
+      bl.nblk[1] = b[1];
+      bl.nblk[2] = b[2];
+      bl.red_smem = red_max <= kReducedSmemMax;
+      bl.smem[1] = bl.red_smem ? red_max : 0;
+      cudaError_t e = launch(*ba, bl, C, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+      __atomic_add_fetch(&g_launches, (unsigned long long)(1 + (bl.any_multi ? 1 : 0) + (bl.any_red ? 1 : 0)),
+                         __ATOMIC_RELAXED);
+    }
+  }
+  return SGWLS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Backward (adjoint) of the filter.
 
 namespace {
@@ -493,6 +719,24 @@ sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void
   return run_backward(static_cast<const float*>(grad_u), static_cast<const float*>(g),
                       static_cast<const float*>(saved), H, W, C, lambda, p, static_cast<float*>(grad_f),
                       static_cast<float*>(grad_g), grad_lambda, ws, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+extern "C" {
+
+size_t sgwls_batched_workspace_bytes(int B, const sgwls_image* imgs, const sgwls_params* p) {
+  if (check_batch(B, imgs, p) != SGWLS_OK) return 0;
+  return batch_workspace(B, imgs, p);
+}
+
+sgwls_status sgwls_filter_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  sgwls_status s = check_batch(B, imgs, p);
+  if (s != SGWLS_OK) return s;
+  const size_t need = batch_workspace(B, imgs, p);
+  if (need > 0 && (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255))) return SGWLS_E_WORKSPACE;
+  return run_batched(B, imgs, p, ws, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -1,7 +1,7 @@
 // sgwls_launch.cuh -- launch plan of one pass and the per-radius launchers.
 #pragma once
 
-#include "sgwls_pass.cuh"
+#include "sgwls_batch.cuh"
 
 namespace sgwls {
 
@@ -51,10 +51,14 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device):
+// later launches (for example inside a CUDA-graph capture) make no call.
+cudaError_t set_smem_raw(const void* kernel, size_t bytes);
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return set_smem_raw(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 template <int R, int CC, bool BWD = false>
@@ -99,6 +103,62 @@ cudaError_t launch_pass_r(const PassArgs& a, const Plan& pl, int CC, cudaStream_
     default: return cudaErrorInvalidValue;
   }
 }
+
+// Batched pass: one launch per kernel over all images of `ba`.
+struct BatchLaunch {
+  int nblk[3];       // blocks of the summary / reduced / recover launches
+  int G;             // chunks (warps) per block, common to all images
+  size_t smem[3];
+  bool red_smem;     // reduced chain in shared memory
+  bool any_multi;    // some image has more than one chunk
+  bool any_red;      // some image has more than one chunk group
+};
+
+template <int R, int CC>
+cudaError_t launch_batch_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st) {
+  cudaError_t e;
+  BatchArgs b = ba;
+  b.base.early_stage = bl.any_red ? 1 : 0;
+  if (bl.any_multi) {
+    if ((e = set_smem(k_summary_b<R, CC>, bl.smem[0])) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_summary_b<R, CC>, dim3(bl.nblk[0]), dim3(32, bl.G), bl.smem[0], st, b)) != cudaSuccess)
+      return e;
+    if (bl.any_red) {
+      if (bl.red_smem) {
+        if ((e = set_smem(k_reduced_b<R, CC, true>, bl.smem[1])) != cudaSuccess) return e;
+        e = launch_pdl(k_reduced_b<R, CC, true>, dim3(bl.nblk[1]), dim3(32, 8), bl.smem[1], st, b);
+      } else {
+        e = launch_pdl(k_reduced_b<R, CC, false>, dim3(bl.nblk[1]), dim3(32, 1), 0, st, b);
+      }
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if ((e = set_smem(k_recover_b<R, CC>, bl.smem[2])) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_recover_b<R, CC>, dim3(bl.nblk[2]), dim3(32, bl.G), bl.smem[2], st, b)) != cudaSuccess)
+    return e;
+  return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_batch_r(const BatchArgs& ba, const BatchLaunch& bl, int CC, cudaStream_t st) {
+  switch (CC) {
+    case 1: return launch_batch_rc<R, 1>(ba, bl, st);
+    case 2: return launch_batch_rc<R, 2>(ba, bl, st);
+    case 3: return launch_batch_rc<R, 3>(ba, bl, st);
+    case 4: return launch_batch_rc<R, 4>(ba, bl, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+using BatchLauncher = cudaError_t (*)(const BatchArgs&, const BatchLaunch&, int CC, cudaStream_t);
+cudaError_t launch_batch_r1(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
+cudaError_t launch_batch_r2(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
+cudaError_t launch_batch_r3(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
+cudaError_t launch_batch_r4(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
+cudaError_t launch_batch_r5(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
+cudaError_t launch_batch_r6(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
+cudaError_t launch_batch_r7(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
+cudaError_t launch_batch_r8(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
 
 cudaError_t launch_pass_r1(const PassArgs&, const Plan&, int, cudaStream_t);
 cudaError_t launch_pass_r2(const PassArgs&, const Plan&, int, cudaStream_t);

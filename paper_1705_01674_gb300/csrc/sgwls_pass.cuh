@@ -841,20 +841,19 @@ __device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lan
 // k_summary: chunk eliminations and the in-block merge into a group 2-port.
 // Grid (ceil(nsys / 32), NG), block (32, G).
 template <int R, int CC>
-__global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
+__device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, float* smem) {
   using F = Fields<R, CC>;
   using MF = MFields<R, CC>;
-  extern __shared__ float smem[];
   const int lane = threadIdx.x;
   const int G = blockDim.y;
-  const int sys = blockIdx.x * 32 + lane;
-  const int grp = blockIdx.y;
+  const int sys = bx * 32 + lane;
+  const int grp = by;
   const int c0 = grp * G;
   const int nch = min(G, a.P - c0);
   const int c = c0 + threadIdx.y;
 
   Tile t;
-  group_tile(a, c0, G, blockIdx.x * 32, R, smem, t);
+  group_tile(a, c0, G, bx * 32, R, smem, t);
   float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
   griddep_wait();
   griddep_launch();
@@ -870,6 +869,12 @@ __global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArg
   if (threadIdx.y != 0 || !active) return;
 
   merge_block<R, CC>(a, csum, lane, sys, grp, c0, nch, G);
+}
+
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
+  extern __shared__ float smem[];
+  body_summary<R, CC>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 // Block Cholesky of the group-separator system of one subsystem (the serial
@@ -994,11 +999,10 @@ __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& 
 // memory (every load in flight at once) and runs the chain there; otherwise
 // the chain reads global memory directly.
 template <int R, int CC, bool SMEM>
-__global__ void __launch_bounds__(256) k_reduced(const __grid_constant__ PassArgs a) {
+__device__ __forceinline__ void body_reduced(const PassArgs& a, int bx, float* smem) {
   using F = Fields<R, CC>;
-  extern __shared__ float smem[];
   const int lane = threadIdx.x;
-  const int sys = blockIdx.x * 32 + lane;
+  const int sys = bx * 32 + lane;
   const int NG = a.ngroups;
   griddep_wait();
   griddep_launch();
@@ -1032,6 +1036,12 @@ __global__ void __launch_bounds__(256) k_reduced(const __grid_constant__ PassArg
   }
 }
 
+template <int R, int CC, bool SMEM>
+__global__ void __launch_bounds__(256) k_reduced(const __grid_constant__ PassArgs a) {
+  extern __shared__ float smem[];
+  body_reduced<R, CC, SMEM>(a, blockIdx.x, smem);
+}
+
 // ---------------------------------------------------------------------------
 // k_recover: back-fill of the group's separators, exact interior solves with
 // known separators, write-back and averaging.  Grid (ceil(D / OB), NG),
@@ -1042,7 +1052,7 @@ __global__ void __launch_bounds__(256) k_reduced(const __grid_constant__ PassArg
 // count); the kernel writes dLoss/d(pass input) = sum over subsystems of v,
 // and accumulates dLoss/dG and dLoss/dlambda from every pair of entries.
 template <int R, int CC, bool BWD = false>
-__global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArgs a) {
+__device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, float* smem) {
   constexpr int n = 2 * R + 1;
   constexpr int NF = R + CC;       // stored per entry: L[p, p-1..p-R], z
   constexpr int OB = 32 - 2 * R;   // outputs per warp
@@ -1050,14 +1060,13 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
   constexpr int NOUT = BWD ? CC / 2 : CC;   // output channels
   constexpr int NCOL = 32 + 2 * R;
   using MF = MFields<R, CC>;
-  extern __shared__ float smem[];
   const int lane = threadIdx.x;
   const int G = blockDim.y;
-  const int grp = blockIdx.y;
+  const int grp = by;
   const int c0 = grp * G;
   const int nch = min(G, a.P - c0);
   const int c = c0 + threadIdx.y;
-  const int kc = blockIdx.x * OB - R + lane;  // this lane's centre
+  const int kc = bx * OB - R + lane;  // this lane's centre
   const int sys_raw = kc - R;
   const bool valid = sys_raw >= 0 && sys_raw < a.nsys;
   const int sys = min(max(sys_raw, 0), a.nsys - 1);
@@ -1065,7 +1074,7 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
   const long long ns = a.nsys;
 
   Tile t;
-  group_tile(a, c0, G, blockIdx.x * OB - 2 * R, R, smem, t);
+  group_tile(a, c0, G, bx * OB - 2 * R, R, smem, t);
   float* ports = smem + (CC + 1) * t.ntl * t.pitch;   // [G][2][XS][32]
   float* mbuf = ports + G * 2 * XS * 32;               // [G-1][MF::N][32] merge factors + [2][XS][32]
   float* store = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [G][mcap][NF][32]
@@ -1393,7 +1402,7 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
     for (int row = threadIdx.y; row < NOUT * OB; row += G) {
       const int ch = row / OB;
       const int o = row - ch * OB;
-      const int oabs = blockIdx.x * OB + o;
+      const int oabs = bx * OB + o;
       if (oabs >= a.D) continue;
       const float* src = otile + row * opitch;
       const long long gbase = ch * a.plane + (long long)oabs * a.W + oline0;
@@ -1421,6 +1430,12 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
       if (line >= 0 && line < a.L && off >= 0 && off < a.D) atomicAdd(a.grad_g + pix_index(a, line, off), v);
     }
   }
+}
+
+template <int R, int CC, bool BWD>
+__global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArgs a) {
+  extern __shared__ float smem[];
+  body_recover<R, CC, BWD>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 }  // namespace sgwls

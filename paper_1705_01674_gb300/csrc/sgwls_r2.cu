@@ -10,4 +10,13 @@ cudaError_t launch_pass_r2(const PassArgs& a, const Plan& pl, int CC, cudaStream
   return launch_pass_r<2>(a, pl, CC, st);
 #endif
 }
+
+cudaError_t launch_batch_r2(const BatchArgs& ba, const BatchLaunch& bl, int CC, cudaStream_t st) {
+#ifdef SGWLS_STUB_RADIUS
+  (void)ba, (void)bl, (void)CC, (void)st;
+  return cudaErrorNotSupported;
+#else
+  return launch_batch_r<2>(ba, bl, CC, st);
+#endif
+}
 }  // namespace sgwls

@@ -1,0 +1,98 @@
+"""GPU parity of the batched entry point (many images of uneven sizes, one
+launch per kernel per pass) against the FP64 oracle, and its equality with
+single-image calls; CUDA-graph capture of a whole batched filter."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import Params, sgwls
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_01674_gb300 import build
+    build.build()
+    import paper_1705_01674_gb300 as m
+    return m
+
+
+def _batch(n, seed, lo, hi, C=1):
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(lo, hi + 1, size=(n, 2))
+    lams = rng.uniform(0.5, 4.0, size=n)
+    if C == 1:
+        imgs = [synth.rect_gray(int(h), int(w), seed=1000 * seed + b) for b, (h, w) in enumerate(sizes)]
+        guides = [im[0] for im in imgs]
+    else:
+        imgs = [synth.rgb_scene(int(h), int(w), seed=1000 * seed + b, n_rect=10, n_disk=2)
+                for b, (h, w) in enumerate(sizes)]
+        guides = [synth.luminance(im) for im in imgs]
+    return imgs, guides, [float(x) for x in lams]
+
+
+@pytest.mark.parametrize("r,C", [(2, 1), (1, 3), (3, 1)])
+def test_batched_uneven_matches_oracle(api, r, C):
+    import torch
+    imgs, guides, lams = _batch(7, seed=40 + r, lo=2 * r + 1, hi=90, C=C)
+    kw = dict(r=r, iters=2, sigma_r=0.1)
+    fs = [torch.from_numpy(x).cuda() for x in imgs]
+    gs = [torch.from_numpy(x).cuda() for x in guides]
+    outs = api.sgwls_filter_batched(fs, gs, lams, **kw)
+    torch.cuda.synchronize()
+    prm = Params(r=r, iters=2, sigma_s=float(r), sigma_r=0.1)
+    for x, g, lam, u in zip(imgs, guides, lams, outs):
+        ref = sgwls(x.astype(np.float64), g.astype(np.float64), lam, prm)
+        err = float(np.abs(u.cpu().numpy().astype(np.float64) - ref).max())
+        assert err <= TOL, (x.shape, err)
+
+
+def test_batched_equals_single_calls_many_images(api):
+    """70 images (two launches per pass: 64 + 6) of sides 64..300."""
+    import torch
+    imgs, guides, lams = _batch(70, seed=4, lo=64, hi=300)
+    kw = dict(r=2, iters=2, sigma_r=0.1)
+    fs = [torch.from_numpy(x).cuda() for x in imgs]
+    gs = [torch.from_numpy(x).cuda() for x in guides]
+    outs = api.sgwls_filter_batched(fs, gs, lams, **kw)
+    singles = [api.sgwls_filter(f, g, lam, **kw) for f, g, lam in zip(fs, gs, lams)]
+    torch.cuda.synchronize()
+    for u, v in zip(outs, singles):
+        assert float((u - v).abs().max()) <= TOL
+
+
+def test_batched_cuda_graph(api):
+    """The whole batched filter (all passes) captured in a CUDA graph and
+    replayed on new inputs."""
+    import torch
+    imgs, guides, lams = _batch(5, seed=11, lo=40, hi=200)
+    kw = dict(r=2, iters=2, sigma_r=0.1)
+    fs = [torch.from_numpy(x).cuda() for x in imgs]
+    gs = [torch.from_numpy(x).cuda() for x in guides]
+    outs = [torch.empty_like(f) for f in fs]
+    nws = api.batched_workspace_bytes(fs, gs, lams, **kw)
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        api.sgwls_filter_batched(fs, gs, lams, outs=outs, workspace=ws, stream=s, **kw)   # warm-up
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        api.sgwls_filter_batched(fs, gs, lams, outs=outs, workspace=ws, stream=s, **kw)
+    new = [synth.rect_gray(x.shape[1], x.shape[2], seed=999 + i) for i, x in enumerate(imgs)]
+    for f, g, x in zip(fs, gs, new):
+        f.copy_(torch.from_numpy(x))
+        g.copy_(torch.from_numpy(x[0]))
+    graph.replay()
+    torch.cuda.synchronize()
+    prm = Params(r=2, iters=2, sigma_s=2.0, sigma_r=0.1)
+    for x, lam, u in zip(new, lams, outs):
+        ref = sgwls(x.astype(np.float64), x[0].astype(np.float64), lam, prm)
+        assert float(np.abs(u.cpu().numpy().astype(np.float64) - ref).max()) <= TOL
