@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     return ap.parse_args()
 
 
@@ -358,6 +359,9 @@ def run_ours(args):
         "gpu_launches": int(n1 - n0),
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_secondary:
+        line["secondary"] = run_secondary(sg, dev, stream, flush)
+        line["secondary"]["bf16_storage"]["speedup_vs_fp32"] = line["secondary"]["bf16_storage"]["value"] / value
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if err is not None:
@@ -368,6 +372,104 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# --------------------------------------------------------- secondary workloads
+
+def _timed(fn, steps, warmup, flush, stream):
+    """Device time (ms) of `steps` calls of fn(i), L2 flushed before each."""
+    import torch
+    evs = []
+    with torch.cuda.stream(stream):
+        for i in range(warmup):
+            fn(i)
+        for i in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(i)
+            e1.record(stream)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
+    """Forward+backward (16 RGB 512x512, r=1, T=3), batched uneven sizes
+    (64 gray images, sides U[256, 2048], r=2, T=2, lambda U[0.5, 4]) against
+    single-image calls, and BF16 storage of the main workload."""
+    import numpy as np
+    import torch
+
+    import synth
+    out = {}
+
+    # forward + backward through the C ABI (checkpoints kept by the forward)
+    F, Tg = synth.diff_batch(n=16, H=512, W=512, seed=5)
+    fs = torch.from_numpy(F).to(dev)
+    ts = torch.from_numpy(Tg).to(dev)
+    gs = torch.stack([torch.from_numpy(synth.luminance(x)) for x in F]).to(dev)
+    kw = dict(r=1, iters=3, sigma_r=0.1)
+    saved = torch.empty((6, 3, 512, 512), device=dev)
+    u = torch.empty_like(fs[0])
+
+    def fwd_bwd(i):
+        for b in range(fs.shape[0]):
+            sg.sgwls_filter(fs[b], gs[b], 1.0, out=u, saved=saved, stream=stream, **kw)
+            gu = 2.0 * (u - ts[b])
+            sg.sgwls_filter_backward(gu, gs[b], saved, 1.0, stream=stream, **kw)
+
+    def fwd_only(i):
+        for b in range(fs.shape[0]):
+            sg.sgwls_filter(fs[b], gs[b], 1.0, out=u, stream=stream, **kw)
+
+    mp = fs.shape[0] * 512 * 512 / 1e6 * 3
+    ms_fb = _timed(fwd_bwd, steps, warmup, flush, stream) / steps
+    ms_f = _timed(fwd_only, steps, warmup, flush, stream) / steps
+    out["fwd_bwd"] = {"workload": "16 x RGB 512x512, r=1, T=3, loss sum((U - target)^2)",
+                      "value": mp / (ms_fb / 1e3), "unit": UNIT, "ms_per_step": ms_fb,
+                      "fwd_value": mp / (ms_f / 1e3)}
+    del fs, ts, gs, saved
+
+    # batched uneven sizes: one batched call vs. a loop of single calls
+    imgs, lams = synth.batch_uneven_gray(n=64, seed=4)
+    bf = [torch.from_numpy(x).to(dev) for x in imgs]
+    bg = [x[0] for x in bf]
+    bo = [torch.empty_like(x) for x in bf]
+    kwb = dict(r=2, iters=2, sigma_r=0.1)
+    nws = sg.batched_workspace_bytes(bf, bg, lams, **kwb)
+    bws = torch.empty(nws, dtype=torch.uint8, device=dev)
+    mpb = sum(x.shape[1] * x.shape[2] for x in imgs) / 1e6 * 2
+
+    def batched(i):
+        sg.sgwls_filter_batched(bf, bg, lams, outs=bo, workspace=bws, stream=stream, **kwb)
+
+    def singles(i):
+        for f, g, lam, o in zip(bf, bg, lams, bo):
+            sg.sgwls_filter(f, g, lam, out=o, stream=stream, **kwb)
+
+    ms_b = _timed(batched, max(2, steps // 2), 1, flush, stream) / max(2, steps // 2)
+    ms_s = _timed(singles, max(2, steps // 2), 1, flush, stream) / max(2, steps // 2)
+    out["batched"] = {"workload": f"64 gray images, sides U[256,2048] ({mpb / 2:.1f} MP), r=2, T=2",
+                      "value": mpb / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b,
+                      "single_calls_value": mpb / (ms_s / 1e3), "speedup_vs_single_calls": ms_s / ms_b}
+    del bf, bg, bo, bws
+
+    # BF16 storage of the main workload
+    F2, G2 = _inputs(WL["seed"])
+    fb = torch.from_numpy(F2).to(dev).to(torch.bfloat16)
+    gb = torch.from_numpy(G2).to(dev).to(torch.bfloat16)
+    ub = torch.empty_like(fb)
+    kw2 = dict(r=WL["r"], iters=WL["iters"], sigma_r=WL["sigma_r"])
+
+    def bf16(i):
+        sg.sgwls_filter(fb, gb, WL["lams"][i % 2], out=ub, stream=stream, **kw2)
+
+    ms_h = _timed(bf16, steps, warmup, flush, stream) / steps
+    mp2 = WL["H"] * WL["W"] / 1e6 * WL["iters"]
+    out["bf16_storage"] = {"workload": WL["name"] + " (BF16 input/guidance/output, FP32 intermediates)",
+                           "value": mp2 / (ms_h / 1e3), "unit": UNIT, "ms_per_step": ms_h}
+    return out
 
 
 def main():
