@@ -200,9 +200,10 @@ sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void
  *   Set-up: the first call on a device looks up the array's device address
  *   with that device current (cudaGetSymbolAddress) and keeps it; make that
  *   first call before any stream capture.
- *   Sharing: all calls share the one array and leave their contents in it
- *   (every value the kernels read is written earlier in the same call, so
- *   nothing needs clearing); calls that overlap on the GPU (other streams,
+ *   Sharing: all calls share the one array and leave their contents in it;
+ *   each call clears the array's small block-counter region on its stream
+ *   before its kernels (every other value the kernels read is written
+ *   earlier in the same call); calls that overlap on the GPU (other streams,
  *   other host threads) race on it -- serialise them.
  *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  * Other arguments and results as sgwls_filter_pass. */

@@ -81,8 +81,14 @@ struct Layout {
   size_t summ_off, summ_bytes;
   size_t xsep_off, xsep_bytes;
   size_t mdata_off, mdata_bytes;
+  size_t cnt_off, cnt_bytes;   // per-band block counters of k_summary
   size_t total;
 };
+
+size_t counter_bytes(int H, int W, int r) {
+  const int bands = (std::max(H, W) - 2 * r + 31) / 32;
+  return align256((size_t)bands * sizeof(int));
+}
 
 // Largest per-pass scratch over both directions and all channel groups.
 Layout make_layout(int H, int W, int C, const sgwls_params* p) {
@@ -92,7 +98,7 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
-    const int nsys = D - 2 * r;
+    const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
     for (int c0 = 0; c0 < C; c0 += kGroupMax) {
       const int CC = std::min(kGroupMax, C - c0);
       const Plan pl = make_plan(L, D, r, CC, p->chunk_lines);
@@ -114,7 +120,9 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   lo.xsep_bytes = align256(xsep);
   lo.mdata_off = lo.xsep_off + lo.xsep_bytes;
   lo.mdata_bytes = align256(mdata);
-  lo.total = lo.mdata_off + lo.mdata_bytes;
+  lo.cnt_off = lo.mdata_off + lo.mdata_bytes;
+  lo.cnt_bytes = counter_bytes(H, W, r);
+  lo.total = lo.cnt_off + lo.cnt_bytes;
   return lo;
 }
 
@@ -212,9 +220,13 @@ sgwls_status copy_image(const void* src, int sdt, void* dst, int ddt, long long 
 
 // One pass along `dir` (Sec. 2.3, the four steps): out = pass(in).
 sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const void* g, int H, int W, int C,
-                      float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st) {
+                      float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st, bool zero_counters) {
   const Layout lo = make_layout(H, W, C, p);
   char* wsb = static_cast<char*>(ws);
+  if (zero_counters) {
+    cudaError_t e = cudaMemsetAsync(wsb + lo.cnt_off, 0, lo.cnt_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   const long long plane = (long long)H * W;
   PassArgs a;
   memset(&a, 0, sizeof(a));
@@ -229,9 +241,11 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
   a.L = dir == 0 ? H : W;
   a.D = dir == 0 ? W : H;
   a.nsys = a.D - 2 * p->r;
+  a.sstride = (a.nsys + 31) / 32 * 32;
   a.summ = reinterpret_cast<float*>(wsb + lo.summ_off);
   a.xsep = reinterpret_cast<float*>(wsb + lo.xsep_off);
   a.mdata = reinterpret_cast<float*>(wsb + lo.mdata_off);
+  a.band_cnt = reinterpret_cast<int*>(wsb + lo.cnt_off);
   fill_weights(a, p, lambda);
   const PassLauncher launch = launcher_for(p->r);
   for (int c0 = 0; c0 < C; c0 += kGroupMax) {
@@ -246,7 +260,7 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.out = static_cast<char*>(out) + (size_t)c0 * plane * dt_size(out_dt);
     cudaError_t e = launch(a, pl, CC, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? (pl.NG > 1 ? 3 : 2) : 1), __ATOMIC_RELAXED);
+    __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 2 : 1), __ATOMIC_RELAXED);
   }
   return SGWLS_OK;
 }
@@ -286,7 +300,7 @@ sgwls_status run_filter(const void* f, const void* g, void* u, int H, int W, int
       dst = static_cast<char*>(img) + (size_t)(t & 1) * inter_bytes;
       dst_dt = idt;
     }
-    sgwls_status s = run_pass(cur, cur_dt, dst, dst_dt, g, H, W, C, lambda, p, dir, ws, st);
+    sgwls_status s = run_pass(cur, cur_dt, dst, dst_dt, g, H, W, C, lambda, p, dir, ws, st, t == 0);
     if (s != SGWLS_OK) return s;
     cur = dst;
     cur_dt = dst_dt;
@@ -333,7 +347,7 @@ Plan batch_plan(int L, int r, int CC, int h0) {
 }
 
 struct BatchImgLayout {
-  size_t img, summ, xsep, mdata, end;
+  size_t img, summ, xsep, mdata, cnt, end;
 };
 
 // Workspace of image i starts at `base`; returns its layout.
@@ -344,7 +358,7 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
-    const int nsys = D - 2 * r;
+    const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
     const Plan pl = batch_plan(L, r, C, h0);
     summ = std::max(summ, (size_t)pl.NG * n_fields(r, C) * nsys * sizeof(float));
     xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * C * nsys * sizeof(float));
@@ -356,6 +370,7 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
   lo.summ = lo.img + align256((size_t)n_img * C * H * W * dt_size(p->inter_storage));
   lo.xsep = lo.summ + align256(summ);
   lo.mdata = lo.xsep + align256(xsep);
+  lo.cnt = 0;   // (counters live in the batch's shared counter region)
   lo.end = lo.mdata + align256(mdata);
   return lo;
 }
@@ -376,8 +391,16 @@ sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) 
   return SGWLS_OK;
 }
 
+// Batched workspace: the band counters of all images first (one region,
+// cleared once per call), then every image's layout.
+size_t batch_counters(int B, const sgwls_image* imgs, const sgwls_params* p) {
+  size_t c = 0;
+  for (int i = 0; i < B; ++i) c += counter_bytes(imgs[i].H, imgs[i].W, p->r);
+  return c;
+}
+
 size_t batch_workspace(int B, const sgwls_image* imgs, const sgwls_params* p) {
-  size_t off = 0;
+  size_t off = batch_counters(B, imgs, p);
   for (int i = 0; i < B; ++i) off = batch_img_layout(off, imgs[i].H, imgs[i].W, imgs[i].C, p).end;
   return off;
 }
@@ -401,12 +424,19 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
   const int OB = 32 - 2 * r;
   const int npass = 2 * p->iters;
   std::vector<BatchImgLayout> lay(B);
+  std::vector<size_t> cnt_off(B);
   {
-    size_t off = 0;
+    const size_t ncnt = batch_counters(B, imgs, p);
+    size_t off = ncnt, coff = 0;
     for (int i = 0; i < B; ++i) {
       lay[i] = batch_img_layout(off, imgs[i].H, imgs[i].W, C, p);
       off = lay[i].end;
+      cnt_off[i] = coff;
+      coff += counter_bytes(imgs[i].H, imgs[i].W, r);
     }
+    // the band counters of all images, cleared once (each pass leaves them at 0)
+    cudaError_t e = cudaMemsetAsync(wsb, 0, ncnt, st);
+    if (e != cudaSuccess) return cuda_fail(e);
   }
   static thread_local BatchArgs batch_args;   // host-side argument block (the kernels get a copy)
   BatchArgs* ba = &batch_args;
@@ -460,12 +490,14 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
         d.summ = reinterpret_cast<float*>(wsb + lo.summ);
         d.xsep = reinterpret_cast<float*>(wsb + lo.xsep);
         d.mdata = reinterpret_cast<float*>(wsb + lo.mdata);
+        d.band_cnt = reinterpret_cast<int*>(wsb + cnt_off[i0 + k]);
         d.plane = (long long)im.H * im.W;
         d.H = im.H;
         d.W = im.W;
         d.L = dir == 0 ? im.H : im.W;
         d.D = dir == 0 ? im.W : im.H;
         d.nsys = d.D - 2 * r;
+        d.sstride = (d.nsys + 31) / 32 * 32;
         const Plan pl = batch_plan(d.L, r, C, h0);
         d.h = pl.h;
         d.P = pl.P;
@@ -495,8 +527,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
       bl.smem[1] = bl.red_smem ? red_max : 0;
       cudaError_t e = launch(*ba, bl, C, st);
       if (e != cudaSuccess) return cuda_fail(e);
-      __atomic_add_fetch(&g_launches, (unsigned long long)(1 + (bl.any_multi ? 1 : 0) + (bl.any_red ? 1 : 0)),
-                         __ATOMIC_RELAXED);
+      __atomic_add_fetch(&g_launches, (unsigned long long)(1 + (bl.any_multi ? 1 : 0)), __ATOMIC_RELAXED);
     }
   }
   return SGWLS_OK;
@@ -508,7 +539,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
 namespace {
 
 struct BwdLayout {
-  size_t img0, img1, gbuf, summ, xsep, mdata, total;
+  size_t img0, img1, gbuf, summ, xsep, mdata, cnt, total;
 };
 
 BwdLayout make_bwd_layout(int H, int W, int C, const sgwls_params* p) {
@@ -518,7 +549,7 @@ BwdLayout make_bwd_layout(int H, int W, int C, const sgwls_params* p) {
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
-    const int nsys = D - 2 * r;
+    const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
     for (int c0 = 0; c0 < C; c0 += 2) {
       const int CC = 2 * std::min(2, C - c0);
       const Plan pl = make_plan(L, D, r, CC, p->chunk_lines, true);
@@ -536,7 +567,8 @@ BwdLayout make_bwd_layout(int H, int W, int C, const sgwls_params* p) {
   lo.summ = lo.gbuf + align256(((size_t)H * W + 64) * sizeof(float));
   lo.xsep = lo.summ + align256(summ);
   lo.mdata = lo.xsep + align256(xsep);
-  lo.total = lo.mdata + align256(mdata);
+  lo.cnt = lo.mdata + align256(mdata);
+  lo.total = lo.cnt + counter_bytes(H, W, r);
   return lo;
 }
 
@@ -572,6 +604,7 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
   cudaError_t e;
   if ((e = cudaMemsetAsync(grad_g, 0, (size_t)plane * sizeof(float), st)) != cudaSuccess) return cuda_fail(e);
   if ((e = cudaMemsetAsync(grad_lam, 0, sizeof(float), st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(wsb + lo.cnt, 0, lo.total - lo.cnt, st)) != cudaSuccess) return cuda_fail(e);
   const int npass = 2 * p->iters;
   if (npass == 0) {
     e = cudaMemcpyAsync(grad_f, grad_u, (size_t)count * sizeof(float), cudaMemcpyDeviceToDevice, st);
@@ -599,9 +632,11 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
     a.L = dir == 0 ? H : W;
     a.D = dir == 0 ? W : H;
     a.nsys = a.D - 2 * p->r;
+    a.sstride = (a.nsys + 31) / 32 * 32;
     a.summ = reinterpret_cast<float*>(wsb + lo.summ);
     a.xsep = reinterpret_cast<float*>(wsb + lo.xsep);
     a.mdata = reinterpret_cast<float*>(wsb + lo.mdata);
+    a.band_cnt = reinterpret_cast<int*>(wsb + lo.cnt);
     a.grad_g = grad_g;
     a.grad_lam = grad_lam;
     fill_weights(a, p, lambda);
@@ -617,7 +652,7 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
       a.out = dst + (size_t)c0 * plane;
       e = launch(a, pl, -2 * nch, st);
       if (e != cudaSuccess) return cuda_fail(e);
-      __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? (pl.NG > 1 ? 3 : 2) : 1), __ATOMIC_RELAXED);
+      __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 2 : 1), __ATOMIC_RELAXED);
     }
     vbar = dst;
   }
@@ -690,7 +725,7 @@ sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int
   const Layout lo = make_layout(H, W, C, p);
   if (!ws || ws_bytes < lo.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
   return run_pass(f, p->storage, u, p->storage, g, H, W, C, lambda, p, direction, ws,
-                  static_cast<cudaStream_t>(stream));
+                  static_cast<cudaStream_t>(stream), true);
 }
 
 unsigned long long sgwls_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }

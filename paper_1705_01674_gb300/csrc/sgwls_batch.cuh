@@ -21,10 +21,11 @@ struct ImgDesc {
   float* summ;
   float* xsep;
   float* mdata;
+  int* band_cnt;
   long long plane;
-  int H, W, L, D, nsys, h, P, ngroups;
+  int H, W, L, D, nsys, sstride, h, P, ngroups;
   float lam;
-  int b0[3];    // first block of this image in the summary / reduced / recover launch
+  int b0[3];    // first block of this image in the summary / (unused) / recover launch
   int nbx[3];   // blocks along the across direction in each launch
 };
 
@@ -64,12 +65,14 @@ __device__ __forceinline__ void build_args(const BatchArgs& ba, int i, PassArgs&
     sa.summ = d.summ;
     sa.xsep = d.xsep;
     sa.mdata = d.mdata;
+    sa.band_cnt = d.band_cnt;
     sa.plane = d.plane;
     sa.H = d.H;
     sa.W = d.W;
     sa.L = d.L;
     sa.D = d.D;
     sa.nsys = d.nsys;
+    sa.sstride = d.sstride;
     sa.h = d.h;
     sa.P = d.P;
     sa.ngroups = d.ngroups;
@@ -87,15 +90,6 @@ __global__ void __launch_bounds__(256) k_summary_b(const __grid_constant__ Batch
   const int by = local / ba.img[i].nbx[0];
   build_args(ba, i, sa);
   body_summary<R, CC>(sa, local - by * ba.img[i].nbx[0], by, smem);
-}
-
-template <int R, int CC, bool SMEM>
-__global__ void __launch_bounds__(256) k_reduced_b(const __grid_constant__ BatchArgs ba) {
-  extern __shared__ float smem[];
-  __shared__ PassArgs sa;
-  const int i = find_image(ba, 1, blockIdx.x);
-  build_args(ba, i, sa);
-  body_reduced<R, CC, SMEM>(sa, blockIdx.x - ba.img[i].b0[1], smem);
 }
 
 template <int R, int CC>

@@ -36,6 +36,7 @@ struct PassArgs {
   int D;               // extent across the lines (number of columns for dir 0)
   int L;               // number of lines (rows for dir 0)
   int nsys;            // number of centres: D - 2r (step 1)
+  int sstride;         // subsystem stride of the scratch arrays: nsys rounded up to 32
   int h;               // lines per chunk
   int P;               // chunks per subsystem
   int ngroups;         // chunk groups (one block of G chunks each)
@@ -50,6 +51,8 @@ struct PassArgs {
   float* xsep;         // group separators  [NG-1][r*CC][nsys]
   float* mdata;        // merge factors     [NG][G-1][MFields::N][nsys]
   int early_stage;     // k_recover may stage its tile before griddep_wait
+  int* band_cnt;       // per band of 32 subsystems: k_summary blocks finished (0 between passes)
+  int chain_smem;      // the reduced chain of a band fits in k_summary's shared memory
   // Planes 0 .. n_in1-1 come from `in`, planes n_in1 .. CC-1 from `in2`
   // (the backward solves u = A^-1 f and v = A^-1 ubar together).
   const void* in2;

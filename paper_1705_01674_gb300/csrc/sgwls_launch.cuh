@@ -1,6 +1,8 @@
 // sgwls_launch.cuh -- launch plan of one pass and the per-radius launchers.
 #pragma once
 
+#include <algorithm>
+
 #include "sgwls_batch.cuh"
 
 namespace sgwls {
@@ -67,21 +69,14 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   constexpr int OB = 32 - 2 * R;
   cudaError_t e;
   PassArgs b = a;
-  b.early_stage = pl.NG > 1 ? 1 : 0;   // k_recover follows k_reduced
+  b.early_stage = a.P > 1 ? 1 : 0;   // k_recover follows k_summary
   if (a.P > 1) {
-    if ((e = set_smem(k_summary<R, CC>, pl.smem_sum)) != cudaSuccess) return e;
-    e = launch_pdl(k_summary<R, CC>, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), pl.smem_sum, st, b);
+    const size_t chain = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
+    b.chain_smem = (pl.NG > 1 && chain <= kReducedSmemMax) ? 1 : 0;
+    const size_t smem = b.chain_smem ? std::max(pl.smem_sum, chain) : pl.smem_sum;
+    if ((e = set_smem(k_summary<R, CC>, smem)) != cudaSuccess) return e;
+    e = launch_pdl(k_summary<R, CC>, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), smem, st, b);
     if (e != cudaSuccess) return e;
-    if (pl.NG > 1) {
-      const size_t red = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
-      if (red <= kReducedSmemMax) {
-        if ((e = set_smem(k_reduced<R, CC, true>, red)) != cudaSuccess) return e;
-        e = launch_pdl(k_reduced<R, CC, true>, dim3((a.nsys + 31) / 32), dim3(32, 8), red, st, b);
-      } else {
-        e = launch_pdl(k_reduced<R, CC, false>, dim3((a.nsys + 31) / 32), dim3(32, 1), 0, st, b);
-      }
-      if (e != cudaSuccess) return e;
-    }
   }
   if ((e = set_smem(k_recover<R, CC, BWD>, pl.smem_rec)) != cudaSuccess) return e;
   e = launch_pdl(k_recover<R, CC, BWD>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), pl.smem_rec, st, b);
@@ -118,20 +113,13 @@ template <int R, int CC>
 cudaError_t launch_batch_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st) {
   cudaError_t e;
   BatchArgs b = ba;
-  b.base.early_stage = bl.any_red ? 1 : 0;
+  b.base.early_stage = bl.any_multi ? 1 : 0;   // k_recover follows k_summary
+  b.base.chain_smem = bl.red_smem ? 1 : 0;
   if (bl.any_multi) {
-    if ((e = set_smem(k_summary_b<R, CC>, bl.smem[0])) != cudaSuccess) return e;
-    if ((e = launch_pdl(k_summary_b<R, CC>, dim3(bl.nblk[0]), dim3(32, bl.G), bl.smem[0], st, b)) != cudaSuccess)
+    const size_t smem = bl.red_smem ? std::max(bl.smem[0], bl.smem[1]) : bl.smem[0];
+    if ((e = set_smem(k_summary_b<R, CC>, smem)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_summary_b<R, CC>, dim3(bl.nblk[0]), dim3(32, bl.G), smem, st, b)) != cudaSuccess)
       return e;
-    if (bl.any_red) {
-      if (bl.red_smem) {
-        if ((e = set_smem(k_reduced_b<R, CC, true>, bl.smem[1])) != cudaSuccess) return e;
-        e = launch_pdl(k_reduced_b<R, CC, true>, dim3(bl.nblk[1]), dim3(32, 8), bl.smem[1], st, b);
-      } else {
-        e = launch_pdl(k_reduced_b<R, CC, false>, dim3(bl.nblk[1]), dim3(32, 1), 0, st, b);
-      }
-      if (e != cudaSuccess) return e;
-    }
   }
   if ((e = set_smem(k_recover_b<R, CC>, bl.smem[2])) != cudaSuccess) return e;
   if ((e = launch_pdl(k_recover_b<R, CC>, dim3(bl.nblk[2]), dim3(32, bl.G), bl.smem[2], st, b)) != cudaSuccess)

@@ -16,7 +16,7 @@
 
 namespace sgwls {
 sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const void* g, int H, int W, int C,
-                      float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st);
+                      float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st, bool zero_counters);
 }
 
 namespace {
@@ -64,5 +64,5 @@ extern "C" sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, 
   const sgwls_status s = scratch_for_current_device(&ws);
   if (s != SGWLS_OK) return s;
   return sgwls::run_pass(f, q.storage, u, q.storage, g, H, W, C, lambda, &q, direction, ws,
-                         static_cast<cudaStream_t>(stream));
+                         static_cast<cudaStream_t>(stream), true);
 }

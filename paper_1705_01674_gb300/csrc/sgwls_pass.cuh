@@ -1,4 +1,4 @@
-// sgwls_pass.cuh -- one SG-WLS pass (Sec. 2.3) as three kernels.
+// sgwls_pass.cuh -- one SG-WLS pass (Sec. 2.3) as two kernels.
 //
 // Every subsystem A_s u = f (Eq. 5) of a pass is a symmetric positive
 // definite banded matrix of half-bandwidth r and length s = (2r+1) * lines.
@@ -26,10 +26,10 @@
 //               in shared memory, every thread eliminates its chunk's
 //               interior (forward sweep), then warp 0 merges the block's G
 //               chunk 2-ports into one group 2-port, keeping the merge
-//               factors for the back-fill.
-//   k_reduced   one thread per subsystem: block Cholesky of the block
-//               tridiagonal system on the group separators (r x r blocks),
-//               forward elimination and back substitution.
+//               factors for the back-fill.  The last block of each band to
+//               finish solves the band's reduced system: block Cholesky of the
+//               block tridiagonal system on the group separators (r x r
+//               blocks), forward elimination and back substitution.
 //   k_recover   block = 32 neighbouring centres x G chunks.  Warp 0 back-fills
 //               the separators inside the group from the merge factors; every
 //               thread then solves its interior with known separators
@@ -742,16 +742,18 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int
   t.p = p;
 }
 
-// Merges the block's chunk 2-ports into the group 2-port (warp 0, lane =
-// subsystem) and writes the merge factors for the back-fill.  Out of line:
-// it runs once per block and keeps the sweep's code small.
-template <int R, int CC>
-__device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lane, int sys, int grp, int c0,
-                                         int nch, int G) {
+// Folds n consecutive 2-ports (chunk-summary format; in(i) addresses element
+// i's fields) into one by eliminating the n-1 separators between them, left
+// to right.  Element 0 has a top port iff acc_top; element i has a bottom
+// port iff has_bot(i).  Merge i (1 <= i < n) keeps its factors through mf(i)
+// -- Cholesky factor Lm of the separator block, U = Lm^-1 E_YX,
+// V = Lm^-1 E_YZ, w = Lm^-1 rhs_Y -- for the back-fill; out receives the
+// folded 2-port.  Lane = subsystem.
+template <int R, int CC, typename In, typename HasBot, typename Mf, typename Out>
+__device__ __forceinline__ void fold_2ports(int n, bool acc_top, In&& in, HasBot&& has_bot, Mf&& mf, Out&& out) {
   using F = Fields<R, CC>;
   using MF = MFields<R, CC>;
-  const long long ns = a.nsys;
-  Strided cs{csum + lane, 32};
+  auto cs = in(0);
   float ETT[R][R], ETB[R][R], EBB[R][R], qT[R][CC], qB[R][CC];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -767,10 +769,9 @@ __device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lan
       qB[i][ch] = cs[F::GS + i * CC + ch];
     }
   }
-  const bool acc_top = c0 > 0;
-  for (int i = 1; i < nch; ++i) {
-    const bool b_bot = c0 + i < a.P - 1;
-    Strided bs{csum + i * F::N * 32 + lane, 32};
+  for (int i = 1; i < n; ++i) {
+    const bool b_bot = has_bot(i);
+    auto bs = in(i);
     float M[R][R], U[R][R], V[R][R], w[R][CC];
 #pragma unroll
     for (int y = 0; y < R; ++y) {
@@ -807,7 +808,7 @@ __device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lan
       add_atb<R, R>(EBB, V, V, -1.f);
       add_atb<R, CC>(qB, V, w, -1.f);
     }
-    StridedG md{a.mdata + ((long long)(grp * (G - 1) + (i - 1)) * MF::N) * ns + sys, ns};
+    auto md = mf(i);
 #pragma unroll
     for (int y = 0; y < R; ++y) {
 #pragma unroll
@@ -820,61 +821,72 @@ __device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lan
       for (int ch = 0; ch < CC; ++ch) md[MF::W + y * CC + ch] = w[y][ch];
     }
   }
-  StridedG gs{a.summ + (long long)grp * F::N * ns + sys, ns};
 #pragma unroll
   for (int i = 0; i < R; ++i) {
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      gs[F::KTT + i * R + m] = -ETT[i][m];
-      gs[F::KTB + i * R + m] = -ETB[i][m];
-      gs[F::DS + i * R + m] = EBB[i][m];
+      out[F::KTT + i * R + m] = -ETT[i][m];
+      out[F::KTB + i * R + m] = -ETB[i][m];
+      out[F::DS + i * R + m] = EBB[i][m];
     }
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) {
-      gs[F::HT + i * CC + ch] = -qT[i][ch];
-      gs[F::GS + i * CC + ch] = qB[i][ch];
+      out[F::HT + i * CC + ch] = -qT[i][ch];
+      out[F::GS + i * CC + ch] = qB[i][ch];
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_summary: chunk eliminations and the in-block merge into a group 2-port.
-// Grid (ceil(nsys / 32), NG), block (32, G).
-template <int R, int CC>
-__device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, float* smem) {
-  using F = Fields<R, CC>;
+// Back-fill of a fold: given the outer separators xX (above element 0, used
+// iff acc_top) and xZ (below element n-1, used iff has_bot(n-1)), recovers
+// the separators between the elements, bottom to top: put(i, x) receives the
+// separator between elements i-1 and i.
+template <int R, int CC, typename HasBot, typename Mf, typename Put>
+__device__ __forceinline__ void backfill_2ports(int n, bool acc_top, const float (&xX)[R][CC], float (&xZ)[R][CC],
+                                                HasBot&& has_bot, Mf&& mf, Put&& put) {
   using MF = MFields<R, CC>;
-  const int lane = threadIdx.x;
-  const int G = blockDim.y;
-  const int sys = bx * 32 + lane;
-  const int grp = by;
-  const int c0 = grp * G;
-  const int nch = min(G, a.P - c0);
-  const int c = c0 + threadIdx.y;
-
-  Tile t;
-  group_tile(a, c0, G, bx * 32, R, smem, t);
-  float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
-  griddep_wait();
-  griddep_launch();
-  stage_tile<CC, 32 + 2 * R>(a, t);
-  cp_async_wait_all();
-  __syncthreads();
-
-  const bool active = sys < a.nsys;
-  if (active && threadIdx.y < nch) {
-    chunk_summary<R, CC>(a, t, lane, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
+  for (int i = n - 1; i >= 1; --i) {
+    const bool b_bot = has_bot(i);
+    auto md = mf(i);
+    float Lm[R][R], v[R][CC];
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) Lm[y][m] = md[MF::LM + y * R + m];
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) {
+        float acc = md[MF::W + y * CC + ch];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          if (acc_top) acc -= md[MF::U + y * R + m] * xX[m][ch];
+          if (b_bot) acc -= md[MF::V + y * R + m] * xZ[m][ch];
+        }
+        v[y][ch] = acc;
+      }
+    }
+    ltsolve<R, CC>(Lm, v);
+    put(i, v);
+#pragma unroll
+    for (int y = 0; y < R; ++y)
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) xZ[y][ch] = v[y][ch];
   }
-  __syncthreads();
-  if (threadIdx.y != 0 || !active) return;
-
-  merge_block<R, CC>(a, csum, lane, sys, grp, c0, nch, G);
 }
 
+// Merges the block's chunk 2-ports into the group 2-port (warp 0, lane =
+// subsystem) and writes the merge factors for the back-fill.  Out of line:
+// it runs once per block and keeps the sweep's code small.
 template <int R, int CC>
-__global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
-  extern __shared__ float smem[];
-  body_summary<R, CC>(a, blockIdx.x, blockIdx.y, smem);
+__device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lane, int sys, int grp, int c0,
+                                         int nch, int G) {
+  using F = Fields<R, CC>;
+  using MF = MFields<R, CC>;
+  const long long ns = a.sstride;
+  fold_2ports<R, CC>(
+      nch, c0 > 0, [&](int i) { return Strided{csum + i * F::N * 32 + lane, 32}; },
+      [&](int i) { return c0 + i < a.P - 1; },
+      [&](int i) { return StridedG{a.mdata + ((long long)(grp * (G - 1) + (i - 1)) * MF::N) * ns + sys, ns}; },
+      StridedG{a.summ + (long long)grp * F::N * ns + sys, ns});
 }
 
 // Block Cholesky of the group-separator system of one subsystem (the serial
@@ -886,7 +898,7 @@ template <int R, int CC, typename Fld>
 __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& fld) {
   using F = Fields<R, CC>;
   const int NG = a.ngroups;
-  const long long ns = a.nsys;
+  const long long ns = a.sstride;
   // inputs of step g: M0 = DS_g - KTT_{g+1}, r0 = GS_g - HT_{g+1}, B = -KTB_g
   auto load_step = [&](int g, float (&M)[R][R], float (&rhs)[R][CC], float (&B)[R][R]) {
 #pragma unroll
@@ -994,38 +1006,27 @@ __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& 
   }
 }
 
-// k_reduced: one thread per subsystem, 32 subsystems per block.  With
-// SMEM the block first copies its subsystems' group 2-ports into shared
-// memory (every load in flight at once) and runs the chain there; otherwise
-// the chain reads global memory directly.
-template <int R, int CC, bool SMEM>
-__device__ __forceinline__ void body_reduced(const PassArgs& a, int bx, float* smem) {
+// Reduced system of one band (32 subsystems): copies the band's group
+// 2-ports (written by other blocks: read through L2) into shared memory when
+// they fit, then warp 0 runs the serial chains (lane = subsystem).
+template <int R, int CC>
+__device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* smem) {
   using F = Fields<R, CC>;
   const int lane = threadIdx.x;
   const int sys = bx * 32 + lane;
   const int NG = a.ngroups;
-  griddep_wait();
-  griddep_launch();
-  if (NG < 2) return;
-  const long long ns = a.nsys;
+  const long long ns = a.sstride;
   const bool ok = sys < a.nsys;
-  if (SMEM) {
-    // all warps copy the block's group 2-ports; warp 0 then runs the chains
-    const int nrow = NG * F::N;
-    constexpr int U = 8;
-    for (int r0 = threadIdx.y; r0 < nrow; r0 += U * blockDim.y) {
-      float v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int row = r0 + u * blockDim.y;
-        v[u] = (ok && row < nrow) ? a.summ[(long long)row * ns + sys] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int row = r0 + u * blockDim.y;
-        if (row < nrow) smem[row * 32 + lane] = v[u];
-      }
+  if (a.chain_smem) {
+    // rows of 32 subsystems are 128-byte lines (the stride is a multiple of
+    // 32): 16-byte asynchronous copies, all in flight at once (through L2)
+    const int nq = NG * F::N * 8;
+    const int tid = threadIdx.y * 32 + lane;
+    for (int q = tid; q < nq; q += 32 * blockDim.y) {
+      const int row = q >> 3, qq = q & 7;
+      cp_async16(smem + row * 32 + qq * 4, a.summ + (long long)row * ns + bx * 32 + qq * 4, 16);
     }
+    cp_async_wait_all();
     __syncthreads();
     if (threadIdx.y != 0 || !ok) return;
     reduced_chain<R, CC>(a, sys, [&](int g, int field) -> float& { return smem[(g * F::N + field) * 32 + lane]; });
@@ -1036,10 +1037,52 @@ __device__ __forceinline__ void body_reduced(const PassArgs& a, int bx, float* s
   }
 }
 
-template <int R, int CC, bool SMEM>
-__global__ void __launch_bounds__(256) k_reduced(const __grid_constant__ PassArgs a) {
+template <int R, int CC>
+__device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, float* smem) {
+  using F = Fields<R, CC>;
+  using MF = MFields<R, CC>;
+  const int lane = threadIdx.x;
+  const int G = blockDim.y;
+  const int sys = bx * 32 + lane;
+  const int grp = by;
+  const int c0 = grp * G;
+  const int nch = min(G, a.P - c0);
+  const int c = c0 + threadIdx.y;
+
+  Tile t;
+  group_tile(a, c0, G, bx * 32, R, smem, t);
+  float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
+  griddep_wait();
+  griddep_launch();
+  stage_tile<CC, 32 + 2 * R>(a, t);
+  cp_async_wait_all();
+  __syncthreads();
+
+  const bool active = sys < a.nsys;
+  if (active && threadIdx.y < nch) {
+    chunk_summary<R, CC>(a, t, lane, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
+  }
+  __syncthreads();
+  if (threadIdx.y == 0 && active) merge_block<R, CC>(a, csum, lane, sys, grp, c0, nch, G);
+  if (a.ngroups < 2) return;   // one group: no reduced system
+  // The last block of this band of 32 subsystems to finish (an atomic ticket
+  // taken after a memory fence; nothing waits) solves the band's reduced
+  // system on the group separators, overlapping the other bands' work.
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_last = atomicAdd(&a.band_cnt[bx], 1) == a.ngroups - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  band_chain<R, CC>(a, bx, smem);
+  if (threadIdx.x == 0 && threadIdx.y == 0) a.band_cnt[bx] = 0;   // ready for the next pass
+}
+
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
   extern __shared__ float smem[];
-  body_reduced<R, CC, SMEM>(a, blockIdx.x, smem);
+  body_summary<R, CC>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1071,27 +1114,27 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
   const bool valid = sys_raw >= 0 && sys_raw < a.nsys;
   const int sys = min(max(sys_raw, 0), a.nsys - 1);
   const int mcap = a.h * n;
-  const long long ns = a.nsys;
+  const long long ns = a.sstride;
 
   Tile t;
   group_tile(a, c0, G, bx * OB - 2 * R, R, smem, t);
   float* ports = smem + (CC + 1) * t.ntl * t.pitch;   // [G][2][XS][32]
   float* mbuf = ports + G * 2 * XS * 32;               // [G-1][MF::N][32] merge factors + [2][XS][32]
   float* store = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [G][mcap][NF][32]
-  // The input tile and the merge factors come from kernels that completed
-  // before the preceding k_reduced started; with a single chunk the
-  // preceding kernel produced the input itself, so wait first.
+  // The input tile comes from the pass before the preceding k_summary, which
+  // completed before that k_summary passed its own wait; with a single chunk
+  // (no k_summary) the preceding kernel produced the input, so wait first.
   if (!a.early_stage) griddep_wait();
   stage_tile<CC, 32 + 2 * R>(a, t);
+  if (a.early_stage) griddep_wait();
+  griddep_launch();
   // merge factors and the group's outer separators, one warp per merge
   for (int i = threadIdx.y; i < nch - 1; i += G) {
     const float* src = a.mdata + ((long long)(grp * (G - 1) + i) * MF::N) * ns + sys;
     float* dst = mbuf + i * MF::N * 32 + lane;
 #pragma unroll
-    for (int f = 0; f < MF::N; ++f) dst[f * 32] = src[f * ns];
+    for (int f = 0; f < MF::N; ++f) cp_async4(dst + f * 32, src + f * ns, true);
   }
-  if (a.early_stage) griddep_wait();
-  griddep_launch();
   if (threadIdx.y == G - 1) {
     float* dst = mbuf + (G - 1) * MF::N * 32 + lane;
 #pragma unroll
