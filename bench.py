@@ -9,9 +9,10 @@ steps.  One step = one full SG-WLS filter (2T passes) of that image.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Timing: W untimed steps, then K steps; before every timed step L2 is
-flushed by writing a 256 MiB buffer (outside the timed events); each pass
+flushed by writing a 256 MiB buffer (outside the timed events); each step
 is bracketed by CUDA events on the stream it runs on.  `value` = megapixels
-x iterations / summed device time.  `e2e` repeats the measurement through
+x iterations / summed device time.  The roofline's per-pass duration comes
+from a second run of the same K steps with an event pair around every pass.  `e2e` repeats the measurement through
 the one-call API with pinned host buffers, host->device and device->host
 copies inside the timed region.  With N > 1 (torchrun) every rank filters
 its own image (weak scaling, no collective on the data path); rank 0
@@ -257,8 +258,10 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(npass)]
-           for _ in range(args.steps)]
+    # timed region: one event pair around each step (the 2T passes run
+    # back to back, each kernel overlapping its predecessor's tail)
+    step_evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+                for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -267,15 +270,25 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.zero_()
-            step(WL["lams"][i % 2], evs[i])
+            step_evs[i][0].record(stream)
+            step(WL["lams"][i % 2])
+            step_evs[i][1].record(stream)
     torch.cuda.synchronize(dev)
     n1 = sg.launch_count()
     barrier()
     clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in step_evs)
 
+    # per-pass durations for the roofline: the same steps with an event pair
+    # around every pass (on the stream the pass kernels run on)
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(npass)]
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            step(WL["lams"][i % 2], evs[i])
+    torch.cuda.synchronize(dev)
     pass_ms = [[evs[i][t][0].elapsed_time(evs[i][t][1]) for t in range(npass)] for i in range(args.steps)]
-    step_ms = [sum(x) for x in pass_ms]
-    total_ms = sum(step_ms)
     col_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 0)
     row_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 1)
     if world > 1:

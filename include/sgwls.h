@@ -72,7 +72,16 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *   inter_storage  sgwls_dtype of the estimates between passes
  *   chunk_lines 0: automatic; otherwise the number of lines per chunk of
  *               the parallel subsystem solve (a tuning knob; the result is
- *               the same up to FP32 rounding for every value)            */
+ *               the same up to FP32 rounding for every value)
+ *   factor_cache  where the second kernel of a forward pass gets the chunk
+ *               factors (LDL^T rows and forward-substituted right-hand
+ *               sides) from: 0 automatic (kept in the workspace when one
+ *               pass's factors take at most 4 GiB, otherwise recomputed),
+ *               1 always kept, 2 always recomputed.  Keeping costs
+ *               4 (2r+1)(2r+C') bytes per pixel of workspace (C' = channels
+ *               per group, at most 4) and saves the second kernel's
+ *               weights and factorisation.  A tuning knob: the results
+ *               agree up to FP32 rounding.                                */
 typedef struct {
   int weight;
   float sigma_s, sigma_r;
@@ -85,6 +94,7 @@ typedef struct {
   int storage;
   int inter_storage;
   int chunk_lines;
+  int factor_cache;
 } sgwls_params;
 
 #define SGWLS_R_MAX 8
@@ -92,7 +102,8 @@ typedef struct {
 
 /* Defaults: exp weights, sigma_s = 1, sigma_r = 0.1, alpha_s = alpha_r = 1.2,
  * eps = 1e-4 (Sec. 1), r = 1, iters = 1, step = 1, axis_order = 0,
- * refine = 0, FP32 storage, chunk_lines = 0.  `p` must not be NULL. */
+ * refine = 0, FP32 storage, chunk_lines = 0, factor_cache = 0.  `p` must
+ * not be NULL. */
 void sgwls_params_default(sgwls_params* p);
 
 /* Human-readable name of a status code (static string, never NULL). */

@@ -50,22 +50,39 @@ constexpr size_t kSmemBlockTarget = 110 * 1024;   // two blocks per SM
 constexpr size_t kSmemBlockMax = 200 * 1024;
 constexpr int kGMax = 8;
 
-Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false) {
+// Chunk length of a pass that keeps its chunk factors, by radius (measured
+// on GB300 over 1024x768 RGB r = 1 and 1920x1080 RGB r = 2, 3, 5: long
+// enough that a thread's sweep outweighs the per-chunk staging and merge
+// work, short enough for many warps per SM); shorter when that would leave
+// fewer than kTargetWarps chunk-warps.
+inline int keep_lines(int r) { return r == 1 ? 6 : r == 2 ? 12 : r == 3 ? 8 : 16; }
+
+// keep: the pass keeps its chunk factors (k_backsub follows k_summary; no
+// k_recover tile), so only the summary's tile and 2-ports bound the block.
+Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, bool keep = false) {
   const int bands = (D + (32 - 2 * r) - 1) / (32 - 2 * r);
-  // enough chunks for ~kTargetWarps warps in flight: h <= L * bands / target
-  int h = std::max(1, (int)(((long long)L * bands) / kTargetWarps));
-  // blocks of G = 8 chunk-warps, two blocks per SM: shrink h to fit
-  while (h > 1 && smem_recover(r, CC, h, kGMax, bwd) > kSmemBlockTarget) --h;
+  auto second = [&](int hh, int G) { return keep ? smem_backsub(r, CC, hh, G) : smem_recover(r, CC, hh, G, bwd); };
+  auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G)); };
+  int h;
+  if (keep) {
+    h = keep_lines(r);
+    while (h > 1 && (long long)L * bands / h < kTargetWarps) --h;
+  } else {
+    // enough chunks for ~kTargetWarps warps in flight: h <= L * bands / target
+    h = std::max(1, (int)(((long long)L * bands) / kTargetWarps));
+    // blocks of G = 8 chunk-warps, two blocks per SM: shrink h to fit
+    while (h > 1 && block(h, kGMax) > kSmemBlockTarget) --h;
+  }
   if (chunk_lines > 0) h = std::min(chunk_lines, L);
-  while (h > 1 && smem_recover(r, CC, h, 1, bwd) > kSmemBlockMax) --h;
+  while (h > 1 && block(h, 1) > kSmemBlockMax) --h;
   h = std::min(h, L);
   Plan pl;
   pl.h = h;
   pl.P = (L + h - 1) / h;
+  // keep: as many chunk-warps per block as fit two blocks per SM
+  const size_t gcap = keep ? kSmemBlockTarget : kSmemBlockMax;
   int G = 1;
-  while (G < kGMax && G < pl.P && smem_recover(r, CC, h, 2 * G, bwd) <= kSmemBlockMax &&
-         smem_summary(r, CC, h, 2 * G) <= kSmemBlockMax)
-    G *= 2;
+  while (G < kGMax && G < pl.P && block(h, 2 * G) <= gcap) G *= 2;
   pl.G = G;
   pl.NG = (pl.P + G - 1) / G;
   pl.smem_sum = smem_summary(r, CC, h, G);
@@ -82,8 +99,30 @@ struct Layout {
   size_t xsep_off, xsep_bytes;
   size_t mdata_off, mdata_bytes;
   size_t cnt_off, cnt_bytes;   // per-band block counters of k_summary
+  size_t fac_off, fac_bytes;   // chunk factors kept between the kernels of a pass
+  size_t psi_off, psi_bytes;
   size_t total;
 };
+
+// Chunk factors of one pass over CC channels: (2r + CC) values per vector
+// entry (L * (2r+1) entries per subsystem), r * r per chunk for psi.
+constexpr size_t kFactorCacheBytes = size_t(4) << 30;
+size_t fac_bytes(int L, int r, int CC, int sstride) {
+  return (size_t)L * (2 * r + 1) * (2 * r + CC) * sstride * sizeof(float);
+}
+size_t psi_bytes(int P, int r, int sstride) { return (size_t)P * r * r * sstride * sizeof(float); }
+// Plan of one forward pass; *keep: its chunk factors are kept between the
+// two kernels (needs at least two chunks).
+Plan fwd_plan(const sgwls_params* p, int L, int D, int CC, int sstride, bool* keep) {
+  bool k = p->factor_cache == 1 || (p->factor_cache == 0 && fac_bytes(L, p->r, CC, sstride) <= kFactorCacheBytes);
+  Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k);
+  if (k && pl.P < 2) {
+    k = false;
+    pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, false);
+  }
+  *keep = k;
+  return pl;
+}
 
 size_t counter_bytes(int H, int W, int r) {
   const int bands = (std::max(H, W) - 2 * r + 31) / 32;
@@ -94,17 +133,22 @@ size_t counter_bytes(int H, int W, int r) {
 Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   Layout lo;
   const int r = p->r;
-  size_t summ = 0, xsep = 0, mdata = 0;
+  size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
     const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
     for (int c0 = 0; c0 < C; c0 += kGroupMax) {
       const int CC = std::min(kGroupMax, C - c0);
-      const Plan pl = make_plan(L, D, r, CC, p->chunk_lines);
+      bool keep = false;
+      const Plan pl = fwd_plan(p, L, D, CC, nsys, &keep);
       summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
       xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
       mdata = std::max(mdata, (size_t)pl.NG * std::max(pl.G - 1, 1) * n_mfields(r, CC) * nsys * sizeof(float));
+      if (keep) {
+        fac = std::max(fac, fac_bytes(L, r, CC, nsys));
+        psi = std::max(psi, psi_bytes(pl.P, r, nsys));
+      }
     }
   }
   // Intermediate estimates ping-pong between u and one workspace image when
@@ -122,7 +166,11 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   lo.mdata_bytes = align256(mdata);
   lo.cnt_off = lo.mdata_off + lo.mdata_bytes;
   lo.cnt_bytes = counter_bytes(H, W, r);
-  lo.total = lo.cnt_off + lo.cnt_bytes;
+  lo.fac_off = lo.cnt_off + lo.cnt_bytes;
+  lo.fac_bytes = align256(fac);
+  lo.psi_off = lo.fac_off + lo.fac_bytes;
+  lo.psi_bytes = align256(psi);
+  lo.total = lo.psi_off + lo.psi_bytes;
   return lo;
 }
 
@@ -139,6 +187,7 @@ sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
     return SGWLS_E_INVALID;
   if (p->refine != 0) return SGWLS_E_UNSUPPORTED;
   if (p->chunk_lines < 0) return SGWLS_E_INVALID;
+  if (p->factor_cache < 0 || p->factor_cache > 2) return SGWLS_E_INVALID;
   if ((p->storage != SGWLS_F32 && p->storage != SGWLS_BF16) ||
       (p->inter_storage != SGWLS_F32 && p->inter_storage != SGWLS_BF16))
     return SGWLS_E_DTYPE;
@@ -250,7 +299,8 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
   const PassLauncher launch = launcher_for(p->r);
   for (int c0 = 0; c0 < C; c0 += kGroupMax) {
     const int CC = std::min(kGroupMax, C - c0);
-    const Plan pl = make_plan(a.L, a.D, p->r, CC, p->chunk_lines);
+    bool keep = false;
+    const Plan pl = fwd_plan(p, a.L, a.D, CC, a.sstride, &keep);
     a.h = pl.h;
     a.P = pl.P;
     a.ngroups = pl.NG;
@@ -258,6 +308,8 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.in2 = a.in;
     a.n_in1 = CC;
     a.out = static_cast<char*>(out) + (size_t)c0 * plane * dt_size(out_dt);
+    a.fac = keep ? reinterpret_cast<float*>(wsb + lo.fac_off) : nullptr;
+    a.psi = keep ? reinterpret_cast<float*>(wsb + lo.psi_off) : nullptr;
     cudaError_t e = launch(a, pl, CC, st);
     if (e != cudaSuccess) return cuda_fail(e);
     __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 2 : 1), __ATOMIC_RELAXED);
@@ -681,6 +733,7 @@ void sgwls_params_default(sgwls_params* p) {
   p->storage = SGWLS_F32;
   p->inter_storage = SGWLS_F32;
   p->chunk_lines = 0;
+  p->factor_cache = 0;
 }
 
 const char* sgwls_status_string(sgwls_status s) {

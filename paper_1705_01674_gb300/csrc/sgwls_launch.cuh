@@ -30,6 +30,14 @@ inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
               otile + gacc);
 }
 
+// k_backsub: group ports and merge factors, plus the row-direction output
+// staging.
+inline size_t smem_backsub(int r, int CC, int h, int G) {
+  const size_t merge = (size_t)(G - 1) * (3 * r * r + r * CC) * 32 + 2 * (size_t)r * CC * 32;
+  const size_t otile = (size_t)CC * (32 - 2 * r) * ((G * h) | 1);
+  return 4 * ((size_t)G * 2 * r * CC * 32 + merge + otile);
+}
+
 constexpr size_t kReducedSmemMax = 96 * 1024;
 
 // Launches the kernels of one pass for a group of CC <= 4 channels.
@@ -70,6 +78,7 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   cudaError_t e;
   PassArgs b = a;
   b.early_stage = a.P > 1 ? 1 : 0;   // k_recover follows k_summary
+  if (BWD || a.P < 2) b.fac = b.psi = nullptr;   // factors are kept only by a forward k_summary
   if (a.P > 1) {
     const size_t chain = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
     b.chain_smem = (pl.NG > 1 && chain <= kReducedSmemMax) ? 1 : 0;
@@ -77,6 +86,15 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
     if ((e = set_smem(k_summary<R, CC>, smem)) != cudaSuccess) return e;
     e = launch_pdl(k_summary<R, CC>, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), smem, st, b);
     if (e != cudaSuccess) return e;
+  }
+  if constexpr (!BWD) {
+    if (b.fac) {   // the factors were kept by k_summary
+      const size_t smem = smem_backsub(R, CC, a.h, pl.G);
+      if ((e = set_smem(k_backsub<R, CC>, smem)) != cudaSuccess) return e;
+      e = launch_pdl(k_backsub<R, CC>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), smem, st, b);
+      if (e != cudaSuccess) return e;
+      return cudaGetLastError();
+    }
   }
   if ((e = set_smem(k_recover<R, CC, BWD>, pl.smem_rec)) != cudaSuccess) return e;
   e = launch_pdl(k_recover<R, CC, BWD>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), pl.smem_rec, st, b);

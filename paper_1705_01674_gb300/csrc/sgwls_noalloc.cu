@@ -54,6 +54,7 @@ extern "C" sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, 
   // a pass needs no intermediate image: size the scratch as for iters == 0
   sgwls_params q = *p;
   q.iters = 0;
+  q.factor_cache = 2;   // the chunk factors are recomputed, not kept in the scratch
   const size_t need = sgwls_workspace_bytes(H, W, C, &q);
   if (need == 0) return SGWLS_E_INVALID;
   if (need > kNoAllocScratchBytes) return SGWLS_E_WORKSPACE;

@@ -595,12 +595,18 @@ struct StridedG {
 // ---------------------------------------------------------------------------
 // Forward sweep of one chunk for the summary: eliminates the interior and
 // writes its 2-port to `out`.
+// With a.fac set it also keeps, per interior entry, the factor row, z0 and
+// Phi for k_backsub, and psi for the last r interior entries.
 template <int R, int CC>
-__device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int lane, int c, Strided out) {
+__device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int lane, int sys, int c,
+                                              Strided out) {
   constexpr int n = 2 * R + 1;
+  constexpr int NFAC = 2 * R + CC;
   using F = Fields<R, CC>;
   const Chunk q = make_chunk<R>(a, c);
   const int pstride = t.ntl * t.pitch;
+  const long long ss = a.sstride;
+  float* const fac = a.fac ? a.fac + sys : nullptr;
 
   float wh[R][R] = {};
   float Lw[R][R] = {};
@@ -663,6 +669,17 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
             for (int ch = 0; ch < CC; ++ch) HT[i][ch] += yd * y[ch];
           }
         }
+        if (fac) {
+          float* fe = fac + (long long)(line * n + j) * NFAC * ss;
+#pragma unroll
+          for (int tt = 0; tt < R; ++tt) fe[tt * ss] = Lrow[tt];
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch) fe[(R + ch) * ss] = y[ch] * dinv;
+          if (q.top) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) fe[(R + CC + i) * ss] = -YT[i] * dinv;
+          }
+        }
         float YB[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) YB[i] = 0.f;
@@ -685,6 +702,11 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
               }
 #pragma unroll
               for (int ch = 0; ch < CC; ++ch) HB[i][ch] += yd * y[ch];
+            }
+            if (fac) {
+              float* pe = a.psi + sys + (long long)(c * R + (j - (n - 2 * R))) * R * ss;
+#pragma unroll
+              for (int i = 0; i < R; ++i) pe[i * ss] = -YB[i] * dinv;
             }
           }
           push_vec<R, R>(YBw, YB);
@@ -889,15 +911,16 @@ __device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lan
       StridedG{a.summ + (long long)grp * F::N * ns + sys, ns});
 }
 
-// Block Cholesky of the group-separator system of one subsystem (the serial
-// chain).  `fld(g, field)` addresses the group 2-ports; the inputs of step
-// g+1 are read before step g is computed.  The factors L_g, Z_g =
-// L_{g-1}^{-1} (-KTB_g) and w_g are written over DS_g, KTB_g and GS_g; the
-// separator values go to xsep.
-template <int R, int CC, typename Fld>
-__device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& fld) {
+// Block Cholesky of the separator system of NG consecutive 2-ports of one
+// subsystem (the serial chain).  `fld(g, field)` addresses the 2-ports; the
+// inputs of step g+1 are read before step g is computed.  The factors L_g,
+// Z_g = L_{g-1}^{-1} (-KTB_g) and w_g are written over DS_g, KTB_g and GS_g;
+// the value of the separator between 2-ports g and g+1 goes to xsep as
+// group separator xidx(g) (skipped when !store).
+template <int R, int CC, typename Fld, typename Xidx>
+__device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, int NG, bool store, Fld&& fld,
+                                              Xidx&& xidx) {
   using F = Fields<R, CC>;
-  const int NG = a.ngroups;
   const long long ns = a.sstride;
   // inputs of step g: M0 = DS_g - KTT_{g+1}, r0 = GS_g - HT_{g+1}, B = -KTB_g
   auto load_step = [&](int g, float (&M)[R][R], float (&rhs)[R][CC], float (&B)[R][R]) {
@@ -958,10 +981,13 @@ __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& 
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) x[i][ch] = wp[i][ch];
   ltsolve<R, CC>(Lp, x);
+  if (store) {
+    const long long xb = (long long)xidx(NG - 2) * R * CC;
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int ch = 0; ch < CC; ++ch) a.xsep[((long long)(NG - 2) * R * CC + i * CC + ch) * ns + sys] = x[i][ch];
+      for (int ch = 0; ch < CC; ++ch) a.xsep[(xb + i * CC + ch) * ns + sys] = x[i][ch];
+  }
   float Lc[R][R], v[R][CC], Zc[R][R];
   auto load_back = [&](int g) {
 #pragma unroll
@@ -996,19 +1022,33 @@ __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, Fld&& 
 #pragma unroll
         for (int ch = 0; ch < CC; ++ch) vg[i][ch] -= Zg[i][m] * x[m][ch];
     ltsolve<R, CC>(Lg, vg);
+    const long long xb = (long long)xidx(g) * R * CC;
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
       for (int ch = 0; ch < CC; ++ch) {
         x[i][ch] = vg[i][ch];
-        a.xsep[((long long)g * R * CC + i * CC + ch) * ns + sys] = vg[i][ch];
+        if (store) a.xsep[(xb + i * CC + ch) * ns + sys] = vg[i][ch];
       }
   }
 }
 
-// Reduced system of one band (32 subsystems): copies the band's group
-// 2-ports (written by other blocks: read through L2) into shared memory when
-// they fit, then warp 0 runs the serial chains (lane = subsystem).
+// Segments of the reduced chain of NG group 2-ports run by nw warps: about
+// sqrt(NG) (a fold step costs about 1.5 chain steps), at most nw.
+__host__ __device__ inline int chain_segments(int NG, int nw) {
+  int S = 1;
+  while ((S + 1) * (S + 1) <= (NG * 6) / 5) ++S;
+  return S < nw ? S : nw;
+}
+
+// Reduced system of one band (32 subsystems).  When the band's group
+// 2-ports fit in shared memory (copied there through L2: other blocks wrote
+// them) the chain is split into S segments: warp s folds segment s's 2-ports
+// into one (in place: the merge factors of its i-th merge overwrite 2-port
+// i, the folded 2-port its first), warp 0 solves the chain of the S segment
+// 2-ports, then warp s back-fills the separators inside segment s.  Serial
+// depth about 2 sqrt(NG) instead of 2 NG.  Otherwise warp 0 runs the whole
+// chain from global memory.  Lane = subsystem.
 template <int R, int CC>
 __device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* smem) {
   using F = Fields<R, CC>;
@@ -1017,24 +1057,62 @@ __device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* sme
   const int NG = a.ngroups;
   const long long ns = a.sstride;
   const bool ok = sys < a.nsys;
-  if (a.chain_smem) {
-    // rows of 32 subsystems are 128-byte lines (the stride is a multiple of
-    // 32): 16-byte asynchronous copies, all in flight at once (through L2)
-    const int nq = NG * F::N * 8;
-    const int tid = threadIdx.y * 32 + lane;
-    for (int q = tid; q < nq; q += 32 * blockDim.y) {
-      const int row = q >> 3, qq = q & 7;
-      cp_async16(smem + row * 32 + qq * 4, a.summ + (long long)row * ns + bx * 32 + qq * 4, 16);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (threadIdx.y != 0 || !ok) return;
-    reduced_chain<R, CC>(a, sys, [&](int g, int field) -> float& { return smem[(g * F::N + field) * 32 + lane]; });
-  } else {
-    if (threadIdx.y != 0 || !ok) return;
+  if (!a.chain_smem) {
+    if (threadIdx.y != 0) return;
     float* const S = a.summ;
-    reduced_chain<R, CC>(a, sys, [&](int g, int field) -> float& { return S[((long long)g * F::N + field) * ns + sys]; });
+    reduced_chain<R, CC>(
+        a, sys, NG, ok, [&](int g, int field) -> float& { return S[((long long)g * F::N + field) * ns + sys]; },
+        [](int g) { return g; });
+    return;
   }
+  // rows of 32 subsystems are 128-byte lines (the stride is a multiple of
+  // 32): 16-byte asynchronous copies, all in flight at once (through L2)
+  const int nq = NG * F::N * 8;
+  const int tid = threadIdx.y * 32 + lane;
+  for (int q = tid; q < nq; q += 32 * blockDim.y) {
+    const int row = q >> 3, qq = q & 7;
+    cp_async16(smem + row * 32 + qq * 4, a.summ + (long long)row * ns + bx * 32 + qq * 4, 16);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  auto slot = [&](int g) { return Strided{smem + g * F::N * 32 + lane, 32}; };
+  const int S = chain_segments(NG, blockDim.y);
+  if (S < 2) {
+    if (threadIdx.y != 0) return;
+    reduced_chain<R, CC>(
+        a, sys, NG, ok, [&](int g, int field) -> float& { return smem[(g * F::N + field) * 32 + lane]; },
+        [](int g) { return g; });
+    return;
+  }
+  const int w = threadIdx.y;
+  auto seg0 = [&](int sg) { return (sg * NG) / S; };   // first group of segment sg
+  const int g0 = seg0(w), g1 = seg0(w + 1);
+  auto has_bot = [&](int i) { return g0 + i < NG - 1; };
+  auto mf = [&](int i) { return slot(g0 + i); };
+  if (w < S) fold_2ports<R, CC>(g1 - g0, g0 > 0, [&](int i) { return slot(g0 + i); }, has_bot, mf, slot(g0));
+  __syncthreads();
+  if (w == 0)
+    reduced_chain<R, CC>(
+        a, sys, S, ok, [&](int sg, int field) -> float& { return smem[(seg0(sg) * F::N + field) * 32 + lane]; },
+        [&](int sg) { return seg0(sg + 1) - 1; });
+  __syncthreads();   // the segment separators (global, this block's writes) are visible
+  if (w >= S || !ok) return;
+  constexpr int XS = R * CC;
+  float xX[R][CC], xZ[R][CC];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) {
+      xX[i][ch] = g0 > 0 ? a.xsep[((long long)(g0 - 1) * XS + i * CC + ch) * ns + sys] : 0.f;
+      xZ[i][ch] = g1 < NG ? a.xsep[((long long)(g1 - 1) * XS + i * CC + ch) * ns + sys] : 0.f;
+    }
+  backfill_2ports<R, CC>(g1 - g0, g0 > 0, xX, xZ, has_bot, mf, [&](int i, const float (&v)[R][CC]) {
+    const long long xb = (long long)(g0 + i - 1) * XS;
+#pragma unroll
+    for (int y = 0; y < R; ++y)
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) a.xsep[(xb + y * CC + ch) * ns + sys] = v[y][ch];
+  });
 }
 
 template <int R, int CC>
@@ -1060,7 +1138,7 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
 
   const bool active = sys < a.nsys;
   if (active && threadIdx.y < nch) {
-    chunk_summary<R, CC>(a, t, lane, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
+    chunk_summary<R, CC>(a, t, lane, sys, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
   }
   __syncthreads();
   if (threadIdx.y == 0 && active) merge_block<R, CC>(a, csum, lane, sys, grp, c0, nch, G);
@@ -1083,6 +1161,98 @@ template <int R, int CC>
 __global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
   extern __shared__ float smem[];
   body_summary<R, CC>(a, blockIdx.x, blockIdx.y, smem);
+}
+
+// Separator values of every chunk of a group (one block): loads the group's
+// merge factors (asynchronous copies, one warp per merge) and its two outer
+// separators, then warp 0 back-fills the separators between its chunks
+// (lane = subsystem).  ports[(i * 2 + side) * r*CC * 32 + lane] receives the
+// top (side 0) and bottom (side 1) separator of chunk c0 + i; mbuf holds the
+// merge factors.  Waits for all of the block's asynchronous copies.
+template <int R, int CC>
+__device__ __forceinline__ void group_ports(const PassArgs& a, int grp, int c0, int nch, int sys, int lane,
+                                            float* ports, float* mbuf) {
+  using MF = MFields<R, CC>;
+  constexpr int XS = R * CC;
+  const int G = blockDim.y;
+  const long long ns = a.sstride;
+  for (int i = threadIdx.y; i < nch - 1; i += G) {
+    const float* src = a.mdata + ((long long)(grp * (G - 1) + i) * MF::N) * ns + sys;
+    float* dst = mbuf + i * MF::N * 32 + lane;
+#pragma unroll
+    for (int f = 0; f < MF::N; ++f) cp_async4(dst + f * 32, src + f * ns, true);
+  }
+  if (threadIdx.y == G - 1) {
+    float* dst = mbuf + (G - 1) * MF::N * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < XS; ++i) {
+      dst[i * 32] = c0 > 0 ? a.xsep[((long long)(grp - 1) * XS + i) * ns + sys] : 0.f;
+      dst[(XS + i) * 32] = grp < a.ngroups - 1 ? a.xsep[((long long)grp * XS + i) * ns + sys] : 0.f;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    const float* xo = mbuf + (G - 1) * MF::N * 32 + lane;
+    float xX[R][CC], xZ[R][CC];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) {
+        xX[i][ch] = xo[(i * CC + ch) * 32];
+        xZ[i][ch] = xo[(XS + i * CC + ch) * 32];
+      }
+    backfill_2ports<R, CC>(
+        nch, c0 > 0, xX, xZ, [&](int i) { return c0 + i < a.P - 1; },
+        [&](int i) { return Strided{mbuf + (i - 1) * MF::N * 32 + lane, 32}; },
+        [&](int i, const float (&v)[R][CC]) {
+          // separator between chunks c0+i-1 and c0+i; the bottom of chunk
+          // c0+i is the value put just before (or the group's lower port)
+          float* pp = ports + (i * 2) * XS * 32 + lane;
+          float* pb = ports + (i * 2 - 1) * XS * 32 + lane;
+#pragma unroll
+          for (int y = 0; y < R; ++y)
+#pragma unroll
+            for (int ch = 0; ch < CC; ++ch) {
+              pp[(y * CC + ch) * 32] = v[y][ch];
+              pb[(y * CC + ch) * 32] = v[y][ch];
+            }
+        });
+    float* pp = ports + lane;
+    float* pl = ports + ((nch - 1) * 2 + 1) * XS * 32 + lane;
+#pragma unroll
+    for (int y = 0; y < R; ++y)
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) {
+        pp[(y * CC + ch) * 32] = xX[y][ch];
+        pl[(y * CC + ch) * 32] = xo[(XS + y * CC + ch) * 32];
+      }
+  }
+  __syncthreads();
+}
+
+// Row direction: writes the block's staged output lines ([NOUT][OB][lines],
+// pitch opitch) along the image rows.
+template <int NOUT, int OB>
+__device__ __forceinline__ void flush_otile(const PassArgs& a, int bx, int c0, const float* otile, int opitch) {
+  const int G = blockDim.y;
+  const int oline0 = c0 * a.h;
+  const int nl = min((c0 + G) * a.h, a.L) - oline0;
+  for (int row = threadIdx.y; row < NOUT * OB; row += G) {
+    const int ch = row / OB;
+    const int o = row - ch * OB;
+    const int oabs = bx * OB + o;
+    if (oabs >= a.D) continue;
+    const float* src = otile + row * opitch;
+    const long long gbase = ch * a.plane + (long long)oabs * a.W + oline0;
+    float* const outw = reinterpret_cast<float*>(a.out);
+    for (int l = threadIdx.x; l < nl; l += 32) {
+      if (a.out_dt == DT_F32)
+        outw[gbase + l] = src[l];
+      else
+        st_px(a.out, gbase + l, a.out_dt, src[l]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1128,76 +1298,7 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
   stage_tile<CC, 32 + 2 * R>(a, t);
   if (a.early_stage) griddep_wait();
   griddep_launch();
-  // merge factors and the group's outer separators, one warp per merge
-  for (int i = threadIdx.y; i < nch - 1; i += G) {
-    const float* src = a.mdata + ((long long)(grp * (G - 1) + i) * MF::N) * ns + sys;
-    float* dst = mbuf + i * MF::N * 32 + lane;
-#pragma unroll
-    for (int f = 0; f < MF::N; ++f) cp_async4(dst + f * 32, src + f * ns, true);
-  }
-  if (threadIdx.y == G - 1) {
-    float* dst = mbuf + (G - 1) * MF::N * 32 + lane;
-#pragma unroll
-    for (int i = 0; i < XS; ++i) {
-      dst[i * 32] = c0 > 0 ? a.xsep[((long long)(grp - 1) * XS + i) * ns + sys] : 0.f;
-      dst[(XS + i) * 32] = grp < a.ngroups - 1 ? a.xsep[((long long)grp * XS + i) * ns + sys] : 0.f;
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-
-  // ---- back-fill the separators inside the group (warp 0, lane = subsystem)
-  if (threadIdx.y == 0) {
-    const bool acc_top = c0 > 0;
-    const float* xo = mbuf + (G - 1) * MF::N * 32 + lane;
-    float xX[R][CC], xZ[R][CC];
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) {
-        xX[i][ch] = xo[(i * CC + ch) * 32];
-        xZ[i][ch] = xo[(XS + i * CC + ch) * 32];
-      }
-    for (int i = nch - 1; i >= 1; --i) {
-      const bool b_bot = c0 + i < a.P - 1;
-      Strided md{mbuf + (i - 1) * MF::N * 32 + lane, 32};
-      float Lm[R][R], v[R][CC];
-#pragma unroll
-      for (int y = 0; y < R; ++y) {
-#pragma unroll
-        for (int m = 0; m < R; ++m) Lm[y][m] = md[MF::LM + y * R + m];
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) {
-          float acc = md[MF::W + y * CC + ch];
-#pragma unroll
-          for (int m = 0; m < R; ++m) {
-            if (acc_top) acc -= md[MF::U + y * R + m] * xX[m][ch];
-            if (b_bot) acc -= md[MF::V + y * R + m] * xZ[m][ch];
-          }
-          v[y][ch] = acc;
-        }
-      }
-      ltsolve<R, CC>(Lm, v);
-      float* pp = ports + (i * 2) * XS * 32 + lane;
-#pragma unroll
-      for (int y = 0; y < R; ++y)
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) {
-          pp[(y * CC + ch) * 32] = v[y][ch];            // top of chunk c0+i
-          pp[(XS + y * CC + ch) * 32] = xZ[y][ch];      // bottom of chunk c0+i
-          xZ[y][ch] = v[y][ch];
-        }
-    }
-    float* pp = ports + lane;
-#pragma unroll
-    for (int y = 0; y < R; ++y)
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) {
-        pp[(y * CC + ch) * 32] = xX[y][ch];
-        pp[(XS + y * CC + ch) * 32] = xZ[y][ch];
-      }
-  }
-  __syncthreads();
+  group_ports<R, CC>(a, grp, c0, nch, sys, lane, ports, mbuf);
   // Row direction: the block's output lines are staged as [CC][OB][lines]
   // (odd pitch) and written out along the lines at the end.
   const int oline0 = c0 * a.h;
@@ -1440,24 +1541,7 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
   }  // this warp's chunk
 
   if (a.dir != 0 || BWD) __syncthreads();
-  if (a.dir != 0) {
-    const int nl = min((c0 + G) * a.h, a.L) - oline0;
-    for (int row = threadIdx.y; row < NOUT * OB; row += G) {
-      const int ch = row / OB;
-      const int o = row - ch * OB;
-      const int oabs = bx * OB + o;
-      if (oabs >= a.D) continue;
-      const float* src = otile + row * opitch;
-      const long long gbase = ch * a.plane + (long long)oabs * a.W + oline0;
-      float* const outw = reinterpret_cast<float*>(a.out);
-      for (int l = lane; l < nl; l += 32) {
-        if (a.out_dt == DT_F32)
-          outw[gbase + l] = src[l];
-        else
-          st_px(a.out, gbase + l, a.out_dt, src[l]);
-      }
-    }
-  }
+  if (a.dir != 0) flush_otile<NOUT, OB>(a, bx, c0, otile, opitch);
   if constexpr (BWD) {
     // dLoss/dlambda: warp sum, one atomic per warp
 #pragma unroll
@@ -1479,6 +1563,159 @@ template <int R, int CC, bool BWD>
 __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArgs a) {
   extern __shared__ float smem[];
   body_recover<R, CC, BWD>(a, blockIdx.x, blockIdx.y, smem);
+}
+
+// ---------------------------------------------------------------------------
+// k_backsub: the second kernel of a pass when k_summary kept the chunk
+// factors (a.fac).  Back-fills the group's separators, then every thread
+// runs the backward substitution of its chunk from the kept rows,
+//   x_e = z0_e + Phi_e xT + Psi_e xB - sum_t L[e+t, e] x_{e+t},
+// and averages each pixel's 2r+1 values across the neighbouring centres'
+// lanes.  No tile, no weights: the factors come from L2.  Grid (ceil(D / OB),
+// NG), block (32, G); lane = centre, warp = chunk.
+template <int R, int CC>
+__device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, float* smem) {
+  constexpr int n = 2 * R + 1;
+  constexpr int NFAC = 2 * R + CC;
+  constexpr int OB = 32 - 2 * R;
+  constexpr int XS = R * CC;
+  using MF = MFields<R, CC>;
+  const int lane = threadIdx.x;
+  const int G = blockDim.y;
+  const int grp = by;
+  const int c0 = grp * G;
+  const int nch = min(G, a.P - c0);
+  const int c = c0 + threadIdx.y;
+  const int kc = bx * OB - R + lane;  // this lane's centre
+  const int sys_raw = kc - R;
+  const bool valid = sys_raw >= 0 && sys_raw < a.nsys;
+  const int sys = min(max(sys_raw, 0), a.nsys - 1);
+  const long long ss = a.sstride;
+
+  float* ports = smem;                                  // [G][2][XS][32]
+  float* mbuf = ports + G * 2 * XS * 32;                // [G-1][MF::N][32] + [2][XS][32]
+  float* otile = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [CC][OB][opitch]
+  griddep_wait();
+  griddep_launch();
+  group_ports<R, CC>(a, grp, c0, nch, sys, lane, ports, mbuf);
+  const int oline0 = c0 * a.h;
+  const int opitch = (G * a.h) | 1;
+
+  if (threadIdx.y < nch) {  // warp-uniform
+    const Chunk q = make_chunk<R>(a, c);
+    float xT[R][CC], xB[R][CC];
+    {
+      const float* pp = ports + (threadIdx.y * 2) * XS * 32 + lane;
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) {
+          xT[i][ch] = pp[(i * CC + ch) * 32];
+          xB[i][ch] = pp[(XS + i * CC + ch) * 32];
+        }
+    }
+    const int o = kc;
+    const bool writer = lane >= R && lane < 32 - R && o >= 0 && o < a.D;
+    float inv_cnt = 0.f;
+    if (writer) {
+      const int lo = max(R, o - R), hi = min(a.D - 1 - R, o + R);
+      inv_cnt = 1.0f / (float)(hi - lo + 1);
+    }
+    const float* const fac = a.fac + sys;
+    float Lb[R][R] = {};   // Lb[u-1][t-1] = L[p+u, p+u-t]
+    float xw[R][CC] = {};  // x of entries p+1 .. p+R (interior only)
+    const long long ostride = a.dir == 0 ? 1 : a.W;
+    const long long lstride = a.dir == 0 ? a.W : 1;
+    float* const outp = reinterpret_cast<float*>(a.out);
+    for_lines_rev(q.line0, q.line1, [&](auto odd, auto last, int line) {
+      constexpr bool ODD = decltype(odd)::value;
+      constexpr bool LAST = decltype(last)::value;
+      float xl[n][CC];
+      const float* fl = fac + (long long)line * n * NFAC * ss;
+#pragma unroll LineUnroll<R>::value
+      for (int j = n - 1; j >= 0; --j) {
+        float x[CC];
+        if (LAST && q.bot && j >= n - R) {
+#pragma unroll
+          for (int i = 0; i < R; ++i)
+            if (i == j - (n - R))
+#pragma unroll
+              for (int ch = 0; ch < CC; ++ch) x[ch] = xB[i][ch];
+        } else {
+          const float* fe = fl + (long long)j * NFAC * ss;
+          float Lrow[R];
+#pragma unroll
+          for (int tt = 0; tt < R; ++tt) Lrow[tt] = __ldcg(fe + tt * ss);
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch) x[ch] = __ldcg(fe + (R + ch) * ss);
+          if (q.top) {
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              const float ph = __ldcg(fe + (R + CC + i) * ss);
+#pragma unroll
+              for (int ch = 0; ch < CC; ++ch) x[ch] += ph * xT[i][ch];
+            }
+          }
+          if (LAST && q.bot && j >= n - 2 * R) {
+            const float* pe = a.psi + sys + (long long)(c * R + (j - (n - 2 * R))) * R * ss;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              const float ps = __ldcg(pe + i * ss);
+#pragma unroll
+              for (int ch = 0; ch < CC; ++ch) x[ch] += ps * xB[i][ch];
+            }
+          }
+#pragma unroll
+          for (int tt = 1; tt <= R; ++tt)
+#pragma unroll
+            for (int ch = 0; ch < CC; ++ch) x[ch] -= Lb[tt - 1][tt - 1] * xw[tt - 1][ch];
+#pragma unroll
+          for (int u = R - 1; u > 0; --u)
+#pragma unroll
+            for (int tt = 0; tt < R; ++tt) Lb[u][tt] = Lb[u - 1][tt];
+#pragma unroll
+          for (int tt = 0; tt < R; ++tt) Lb[0][tt] = Lrow[tt];
+          push_vec<R, CC>(xw, x);
+        }
+        // (registers for r <= 3; the rolled loop of larger r indexes xl
+        // dynamically, which places it in local memory)
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) xl[j][ch] = x[ch];
+      }
+      // inverse construction + averaging: value at across-offset kc - R + e
+      const long long pix = (long long)line * lstride + (long long)o * ostride;
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) {
+        float voff[n];
+#pragma unroll
+        for (int e2 = 0; e2 < n; ++e2) voff[e2] = valid ? xl[ecol<R, ODD>(e2)][ch] : 0.f;
+        float sum = voff[R];
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+          sum += __shfl_down_sync(0xffffffffu, voff[R - d], d);  // from centre kc + d
+          sum += __shfl_up_sync(0xffffffffu, voff[R + d], d);    // from centre kc - d
+        }
+        if (writer) {
+          if (a.dir != 0)
+            otile[(ch * OB + (lane - R)) * opitch + (line - oline0)] = sum * inv_cnt;
+          else if (a.out_dt == DT_F32)
+            outp[pix + ch * a.plane] = sum * inv_cnt;
+          else
+            st_px(a.out, pix + ch * a.plane, a.out_dt, sum * inv_cnt);
+        }
+      }
+    });
+  }
+  if (a.dir != 0) {
+    __syncthreads();
+    flush_otile<CC, OB>(a, bx, c0, otile, opitch);
+  }
+}
+
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArgs a) {
+  extern __shared__ float smem[];
+  body_backsub<R, CC>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 }  // namespace sgwls

@@ -76,6 +76,38 @@ def test_parity_small_ragged(api, r, C, axis_order, chunk_lines):
     assert err <= TOL, err
 
 
+@pytest.mark.parametrize("r", [1, 2, 3, 5])
+@pytest.mark.parametrize("C", [1, 3, 4])
+@pytest.mark.parametrize("factor_cache", [1, 2])
+def test_parity_factor_cache_modes(api, r, C, factor_cache):
+    """Both sources of the chunk factors in the second kernel of a pass:
+    kept by the first kernel (1) or recomputed from the staged tile (2),
+    with 1- and 3-line chunks (many chunks, ragged last chunk and group)."""
+    F = synth.rgb_scene(61, 75, seed=30 + r, n_rect=15, n_disk=4)
+    F = np.concatenate([F, F[:1]])[:C]
+    G = synth.luminance(synth.rgb_scene(61, 75, seed=30 + r, n_rect=15, n_disk=4))
+    kw = dict(r=r, iters=2, sigma_r=0.1)
+    ref = _oracle(F, G, 1.5, **kw)
+    for chunk_lines in (1, 3):
+        got = _gpu(api, F, G, 1.5, chunk_lines=chunk_lines, factor_cache=factor_cache, **kw)
+        err = _maxerr(got, ref)
+        assert err <= TOL, (chunk_lines, err)
+
+
+@pytest.mark.parametrize("chunk_lines", [1, 2, 5])
+def test_parity_long_reduced_chain(api, chunk_lines):
+    """A tall strip cut into many chunks: 900 x 40 with 1-, 2- and 5-line
+    chunks gives 113, 57 and 23 chunk groups per column subsystem (the
+    band's reduced chain in global memory, and split into segments in
+    shared memory)."""
+    F = synth.rgb_scene(900, 40, seed=77, n_rect=30, n_disk=5)
+    G = synth.luminance(F)
+    for r in (1, 2):
+        kw = dict(r=r, iters=1, sigma_r=0.1)
+        err = _maxerr(_gpu(api, F, G, 3.0, chunk_lines=chunk_lines, **kw), _oracle(F, G, 3.0, **kw))
+        assert err <= TOL, (r, err)
+
+
 @pytest.mark.parametrize("shape", [(3, 3), (3, 40), (40, 3), (5, 130), (130, 5), (33, 31)])
 def test_edge_shapes(api, shape):
     """Minimum sizes (a single centre), very thin images, sizes one past a
@@ -165,13 +197,20 @@ def test_bf16_storage(api, inter):
     assert err <= bound, (err, bound)
 
 
+_FULL_REF = {}
+
+
+@pytest.mark.parametrize("factor_cache", [0, 2])
 @pytest.mark.parametrize("lam", [0.5, 2.0])
-def test_config_rgb_1024x768_full(api, lam):
+def test_config_rgb_1024x768_full(api, lam, factor_cache):
     """Full size: 1024 x 768 RGB scene (200 rectangles, 50 disks, texture,
     noise), guidance = luminance, r = 1, T = 3, range parameter 0.1; every
-    output pixel compared with the FP64 oracle."""
+    output pixel compared with the FP64 oracle, with the chunk factors kept
+    between the kernels (the automatic choice at this size) and recomputed."""
     F = synth.rgb_scene(768, 1024, seed=2)
     G = synth.luminance(F)
     kw = dict(r=1, iters=3, sigma_r=0.1)
-    err = _maxerr(_gpu(api, F, G, lam, **kw), _oracle(F, G, lam, **kw))
+    if lam not in _FULL_REF:
+        _FULL_REF[lam] = _oracle(F, G, lam, **kw)
+    err = _maxerr(_gpu(api, F, G, lam, factor_cache=factor_cache, **kw), _FULL_REF[lam])
     assert err <= TOL, err
