@@ -379,11 +379,31 @@ BatchLauncher batch_launcher_for(int r) {
   }
 }
 
+// Whether the passes of a batched call keep their chunk factors: every
+// image's factors within the single-image budget (or factor_cache = 1).
+bool batch_keep(int B, const sgwls_image* imgs, const sgwls_params* p) {
+  if (p->factor_cache == 2) return false;
+  if (p->factor_cache == 1) return true;
+  for (int i = 0; i < B; ++i) {
+    for (int dir = 0; dir < 2; ++dir) {
+      const int L = dir == 0 ? imgs[i].H : imgs[i].W;
+      const int D = dir == 0 ? imgs[i].W : imgs[i].H;
+      const int nsys = ((D - 2 * p->r) + 31) / 32 * 32;
+      if (fac_bytes(L, p->r, imgs[i].C, nsys) > kFactorCacheBytes) return false;
+    }
+  }
+  return true;
+}
+
 // Lines per chunk shared by every image of a batch (blocks of kGMax chunks,
 // two blocks per SM).
-int batch_h(int r, int CC) {
-  int h = 64;
-  while (h > 1 && smem_recover(r, CC, h, kGMax) > kSmemBlockTarget) --h;
+int batch_h(int r, int CC, bool keep) {
+  int h = keep ? keep_lines(r) : 64;
+  auto block = [&](int hh) {
+    return keep ? std::max(smem_summary(r, CC, hh, kGMax), smem_backsub(r, CC, hh, kGMax))
+                : smem_recover(r, CC, hh, kGMax);
+  };
+  while (h > 1 && block(h) > kSmemBlockTarget) --h;
   return h;
 }
 
@@ -399,14 +419,14 @@ Plan batch_plan(int L, int r, int CC, int h0) {
 }
 
 struct BatchImgLayout {
-  size_t img, summ, xsep, mdata, cnt, end;
+  size_t img, summ, xsep, mdata, cnt, fac, psi, end;
 };
 
 // Workspace of image i starts at `base`; returns its layout.
-BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_params* p) {
+BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_params* p, bool keep) {
   const int r = p->r;
-  const int h0 = batch_h(r, C);
-  size_t summ = 0, xsep = 0, mdata = 0;
+  const int h0 = batch_h(r, C, keep);
+  size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
@@ -415,6 +435,10 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
     summ = std::max(summ, (size_t)pl.NG * n_fields(r, C) * nsys * sizeof(float));
     xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * C * nsys * sizeof(float));
     mdata = std::max(mdata, (size_t)pl.NG * (kGMax - 1) * n_mfields(r, C) * nsys * sizeof(float));
+    if (keep) {
+      fac = std::max(fac, fac_bytes(L, r, C, nsys));
+      psi = std::max(psi, psi_bytes(pl.P, r, nsys));
+    }
   }
   const int n_img = (p->iters > 0) ? (p->inter_storage == p->storage ? 1 : 2) : 0;
   BatchImgLayout lo;
@@ -423,7 +447,9 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
   lo.xsep = lo.summ + align256(summ);
   lo.mdata = lo.xsep + align256(xsep);
   lo.cnt = 0;   // (counters live in the batch's shared counter region)
-  lo.end = lo.mdata + align256(mdata);
+  lo.fac = lo.mdata + align256(mdata);
+  lo.psi = lo.fac + align256(fac);
+  lo.end = lo.psi + align256(psi);
   return lo;
 }
 
@@ -452,8 +478,9 @@ size_t batch_counters(int B, const sgwls_image* imgs, const sgwls_params* p) {
 }
 
 size_t batch_workspace(int B, const sgwls_image* imgs, const sgwls_params* p) {
+  const bool keep = batch_keep(B, imgs, p);
   size_t off = batch_counters(B, imgs, p);
-  for (int i = 0; i < B; ++i) off = batch_img_layout(off, imgs[i].H, imgs[i].W, imgs[i].C, p).end;
+  for (int i = 0; i < B; ++i) off = batch_img_layout(off, imgs[i].H, imgs[i].W, imgs[i].C, p, keep).end;
   return off;
 }
 
@@ -471,7 +498,8 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
     }
     return SGWLS_OK;
   }
-  const int h0 = batch_h(r, C);
+  const bool keep = batch_keep(B, imgs, p);
+  const int h0 = batch_h(r, C, keep);
   const BatchLauncher launch = batch_launcher_for(r);
   const int OB = 32 - 2 * r;
   const int npass = 2 * p->iters;
@@ -481,7 +509,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
     const size_t ncnt = batch_counters(B, imgs, p);
     size_t off = ncnt, coff = 0;
     for (int i = 0; i < B; ++i) {
-      lay[i] = batch_img_layout(off, imgs[i].H, imgs[i].W, C, p);
+      lay[i] = batch_img_layout(off, imgs[i].H, imgs[i].W, C, p, keep);
       off = lay[i].end;
       cnt_off[i] = coff;
       coff += counter_bytes(imgs[i].H, imgs[i].W, r);
@@ -506,6 +534,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
       ba->nimg = nb;
       BatchLaunch bl = {};
       bl.G = kGMax;
+      bl.keep = keep;
       size_t red_max = 0;
       int b[3] = {0, 0, 0};
       for (int k = 0; k < nb; ++k) {
@@ -543,6 +572,8 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
         d.xsep = reinterpret_cast<float*>(wsb + lo.xsep);
         d.mdata = reinterpret_cast<float*>(wsb + lo.mdata);
         d.band_cnt = reinterpret_cast<int*>(wsb + cnt_off[i0 + k]);
+        d.fac = keep ? reinterpret_cast<float*>(wsb + lo.fac) : nullptr;
+        d.psi = keep ? reinterpret_cast<float*>(wsb + lo.psi) : nullptr;
         d.plane = (long long)im.H * im.W;
         d.H = im.H;
         d.W = im.W;
@@ -568,7 +599,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
         bl.any_red |= pl.NG > 1;
         red_max = std::max(red_max, (size_t)pl.NG * n_fields(r, C) * 32 * sizeof(float));
         bl.smem[0] = pl.smem_sum;
-        bl.smem[2] = pl.smem_rec;
+        bl.smem[2] = keep ? smem_backsub(r, C, h0, kGMax) : pl.smem_rec;
       }
       // the output type of intermediate passes is the intermediate type
       a.out_dt = (t == npass - 1) ? sdt : (idt == sdt ? sdt : idt);

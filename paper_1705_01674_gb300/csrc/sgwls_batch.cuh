@@ -22,10 +22,12 @@ struct ImgDesc {
   float* xsep;
   float* mdata;
   int* band_cnt;
+  float* fac;   // kept chunk factors (batches whose passes keep them)
+  float* psi;
   long long plane;
   int H, W, L, D, nsys, sstride, h, P, ngroups;
   float lam;
-  int b0[3];    // first block of this image in the summary / (unused) / recover launch
+  int b0[3];    // first block of this image in the summary / (unused) / recover or backsub launch
   int nbx[3];   // blocks along the across direction in each launch
 };
 
@@ -66,6 +68,8 @@ __device__ __forceinline__ void build_args(const BatchArgs& ba, int i, PassArgs&
     sa.xsep = d.xsep;
     sa.mdata = d.mdata;
     sa.band_cnt = d.band_cnt;
+    sa.fac = d.fac;
+    sa.psi = d.psi;
     sa.plane = d.plane;
     sa.H = d.H;
     sa.W = d.W;
@@ -101,6 +105,17 @@ __global__ void __launch_bounds__(256) k_recover_b(const __grid_constant__ Batch
   const int by = local / ba.img[i].nbx[2];
   build_args(ba, i, sa);
   body_recover<R, CC, false>(sa, local - by * ba.img[i].nbx[2], by, smem);
+}
+
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_backsub_b(const __grid_constant__ BatchArgs ba) {
+  extern __shared__ float smem[];
+  __shared__ PassArgs sa;
+  const int i = find_image(ba, 2, blockIdx.x);
+  const int local = blockIdx.x - ba.img[i].b0[2];
+  const int by = local / ba.img[i].nbx[2];
+  build_args(ba, i, sa);
+  body_backsub<R, CC>(sa, local - by * ba.img[i].nbx[2], by, smem);
 }
 
 }  // namespace sgwls

@@ -125,6 +125,7 @@ struct BatchLaunch {
   bool red_smem;     // reduced chain in shared memory
   bool any_multi;    // some image has more than one chunk
   bool any_red;      // some image has more than one chunk group
+  bool keep;         // k_summary keeps the chunk factors, k_backsub follows
 };
 
 template <int R, int CC>
@@ -138,6 +139,12 @@ cudaError_t launch_batch_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStre
     if ((e = set_smem(k_summary_b<R, CC>, smem)) != cudaSuccess) return e;
     if ((e = launch_pdl(k_summary_b<R, CC>, dim3(bl.nblk[0]), dim3(32, bl.G), smem, st, b)) != cudaSuccess)
       return e;
+  }
+  if (bl.keep && bl.any_multi) {
+    if ((e = set_smem(k_backsub_b<R, CC>, bl.smem[2])) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_backsub_b<R, CC>, dim3(bl.nblk[2]), dim3(32, bl.G), bl.smem[2], st, b)) != cudaSuccess)
+      return e;
+    return cudaGetLastError();
   }
   if ((e = set_smem(k_recover_b<R, CC>, bl.smem[2])) != cudaSuccess) return e;
   if ((e = launch_pdl(k_recover_b<R, CC>, dim3(bl.nblk[2]), dim3(32, bl.G), bl.smem[2], st, b)) != cudaSuccess)

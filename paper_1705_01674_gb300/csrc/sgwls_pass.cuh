@@ -251,25 +251,37 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src, int src
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
 }
 
-// FP32 tiles with 16-byte transfers (image rows 16-byte aligned).
-// Column direction: asynchronous 16-byte copies along the offsets into quads
-// of the tile (its column origin is the quad boundary, cs = off0 mod 4); only
-// quads that start left of the image use scalar loads.  Row direction: each
-// warp instruction loads 8 quads (32 consecutive lines) of 4 image rows, U
-// loads in flight per thread, scattered into the transposed tile.
-template <int CC, int NCOL>
-__device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t) {
+// Four consecutive BF16 values (8-byte aligned) widened to FP32.
+__device__ __forceinline__ float4 ld_bf16x4(const unsigned short* p) {
+  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+  return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
+                     __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
+}
+__device__ __forceinline__ float ld_bf16(const unsigned short* p) {
+  return __uint_as_float(static_cast<unsigned>(__ldg(p)) << 16);
+}
+
+// One tile plane with 4-element transfers (image rows 16-byte aligned for
+// FP32, 8-byte aligned for BF16).  Column direction: quads along the
+// offsets into quads of the tile (its column origin is the quad boundary,
+// cs = off0 mod 4): FP32 as asynchronous 16-byte copies, BF16 as 8-byte
+// loads widened in registers (U in flight per thread); only quads that
+// start left of the image use scalar loads.  Row direction: each warp
+// instruction loads 8 quads (32 consecutive lines) of 4 image rows, U loads
+// in flight per thread, scattered into the transposed tile.
+template <bool F32, int NCOL>
+__device__ __forceinline__ void stage_plane_vec(const PassArgs& a, const Tile& t, const void* vbase, float* dplane) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nthreads = blockDim.x * blockDim.y;
   const long long W = a.W;
-#pragma unroll 1
-  for (int pl = 0; pl <= CC; ++pl) {
-    const float* base = reinterpret_cast<const float*>(plane_base<CC>(a, pl, 4));
-    float* dplane = t.p + pl * t.ntl * t.pitch;
-    if (a.dir == 0) {
-      constexpr int PQ = (NCOL + 3 + 3) / 4;
-      const int x0 = t.off0 - t.cs;
-      const int nq = t.ntl * PQ;
+  const float* fb = reinterpret_cast<const float*>(vbase);
+  const unsigned short* hb = reinterpret_cast<const unsigned short*>(vbase);
+  constexpr int U = 4;
+  if (a.dir == 0) {
+    constexpr int PQ = (NCOL + 3 + 3) / 4;
+    const int x0 = t.off0 - t.cs;
+    const int nq = t.ntl * PQ;
+    if constexpr (F32) {
       for (int idx = tid; idx < nq; idx += nthreads) {
         const int tl = idx / PQ;
         const int q = idx - tl * PQ;
@@ -279,34 +291,67 @@ __device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t)
         const bool lok = line >= 0 && line < a.L;
         if (x >= 0) {
           const int valid = lok ? max(0, min(4, a.D - x)) : 0;
-          cp_async16(dst, valid > 0 ? base + (line * W + x) : base, 4 * valid);
+          cp_async16(dst, valid > 0 ? fb + (line * W + x) : fb, 4 * valid);
         } else {
-          const float* rp = base + (lok ? line : 0) * W;
+          const float* rp = fb + (lok ? line : 0) * W;
 #pragma unroll
           for (int i = 0; i < 4; ++i) dst[i] = (lok && x + i >= 0 && x + i < a.D) ? __ldg(rp + x + i) : 0.f;
         }
       }
     } else {
-      constexpr int NCB = (NCOL + 3) / 4;
-      constexpr int U = 4;
-      const int x0 = t.tl0 & ~3;                 // first quad's line
-      const int nql = (t.tl0 + t.ntl - x0 + 3) / 4;
-      const int nqb = (nql + 7) / 8;
-      const int qs = threadIdx.x & 7, csub = threadIdx.x >> 3;
-      const int ntile = nqb * NCB;
-      for (int tb = threadIdx.y; tb < ntile; tb += U * blockDim.y) {
+      for (int i0 = tid; i0 < nq; i0 += U * nthreads) {
         float4 v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int tile = tb + u * blockDim.y;
-          const int qb = tile / NCB;
-          const int cb = tile - qb * NCB;
-          const int q = qb * 8 + qs, col = cb * 4 + csub;
-          const int off = t.off0 + col;
+          const int idx = i0 + u * nthreads;
+          const int tl = idx / PQ;
+          const int q = idx - tl * PQ;
+          const int line = t.tl0 + tl;
           const int x = x0 + 4 * q;
           v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (tile < ntile && q < nql && col < NCOL && off >= 0 && off < a.D) {
-            const float* rp = base + off * W;
+          if (idx < nq && line >= 0 && line < a.L) {
+            const unsigned short* rp = hb + line * W;
+            if (x >= 0 && x + 3 < a.D) {
+              v[u] = ld_bf16x4(rp + x);
+            } else {
+              if (x >= 0 && x < a.D) v[u].x = ld_bf16(rp + x);
+              if (x + 1 >= 0 && x + 1 < a.D) v[u].y = ld_bf16(rp + x + 1);
+              if (x + 2 >= 0 && x + 2 < a.D) v[u].z = ld_bf16(rp + x + 2);
+              if (x + 3 >= 0 && x + 3 < a.D) v[u].w = ld_bf16(rp + x + 3);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = i0 + u * nthreads;
+          if (idx >= nq) continue;
+          const int tl = idx / PQ;
+          const int q = idx - tl * PQ;
+          *reinterpret_cast<float4*>(dplane + tl * t.pitch + 4 * q) = v[u];
+        }
+      }
+    }
+  } else {
+    constexpr int NCB = (NCOL + 3) / 4;
+    const int x0 = t.tl0 & ~3;                 // first quad's line
+    const int nql = (t.tl0 + t.ntl - x0 + 3) / 4;
+    const int nqb = (nql + 7) / 8;
+    const int qs = threadIdx.x & 7, csub = threadIdx.x >> 3;
+    const int ntile = nqb * NCB;
+    for (int tb = threadIdx.y; tb < ntile; tb += U * blockDim.y) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int tile = tb + u * blockDim.y;
+        const int qb = tile / NCB;
+        const int cb = tile - qb * NCB;
+        const int q = qb * 8 + qs, col = cb * 4 + csub;
+        const int off = t.off0 + col;
+        const int x = x0 + 4 * q;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tile < ntile && q < nql && col < NCOL && off >= 0 && off < a.D) {
+          if constexpr (F32) {
+            const float* rp = fb + off * W;
             if (x >= 0 && x + 3 < a.L) {
               v[u] = __ldg(reinterpret_cast<const float4*>(rp + x));
             } else {
@@ -315,34 +360,67 @@ __device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t)
               if (x + 2 >= 0 && x + 2 < a.L) v[u].z = __ldg(rp + x + 2);
               if (x + 3 >= 0 && x + 3 < a.L) v[u].w = __ldg(rp + x + 3);
             }
+          } else {
+            const unsigned short* rp = hb + off * W;
+            if (x >= 0 && x + 3 < a.L) {
+              v[u] = ld_bf16x4(rp + x);
+            } else {
+              if (x >= 0 && x < a.L) v[u].x = ld_bf16(rp + x);
+              if (x + 1 >= 0 && x + 1 < a.L) v[u].y = ld_bf16(rp + x + 1);
+              if (x + 2 >= 0 && x + 2 < a.L) v[u].z = ld_bf16(rp + x + 2);
+              if (x + 3 >= 0 && x + 3 < a.L) v[u].w = ld_bf16(rp + x + 3);
+            }
           }
         }
+      }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int tile = tb + u * blockDim.y;
-          const int qb = tile / NCB;
-          const int cb = tile - qb * NCB;
-          const int q = qb * 8 + qs, col = cb * 4 + csub;
-          if (tile >= ntile || q >= nql || col >= NCOL) continue;
-          const int tlq = x0 + 4 * q - t.tl0;   // tile line of v.x
-          const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+      for (int u = 0; u < U; ++u) {
+        const int tile = tb + u * blockDim.y;
+        const int qb = tile / NCB;
+        const int cb = tile - qb * NCB;
+        const int q = qb * 8 + qs, col = cb * 4 + csub;
+        if (tile >= ntile || q >= nql || col >= NCOL) continue;
+        const int tlq = x0 + 4 * q - t.tl0;   // tile line of v.x
+        const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (tlq + i >= 0 && tlq + i < t.ntl) dplane[(tlq + i) * t.pitch + col] = e[i];
-        }
+        for (int i = 0; i < 4; ++i)
+          if (tlq + i >= 0 && tlq + i < t.ntl) dplane[(tlq + i) * t.pitch + col] = e[i];
       }
     }
   }
 }
 
-// The tile planes share one storage type when the estimate and the guidance
-// do (always, except for a BF16 guidance with FP32 intermediates).
+// Every plane with 4-element transfers, each in its own storage type.
+template <int CC, int NCOL>
+__device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t) {
+#pragma unroll 1
+  for (int pl = 0; pl <= CC; ++pl) {
+    const int dt = pl < CC ? a.in_dt : a.g_dt;
+    const void* base = plane_base<CC>(a, pl, dt == DT_F32 ? 4 : 2);
+    float* dplane = t.p + pl * t.ntl * t.pitch;
+    if (dt == DT_F32)
+      stage_plane_vec<true, NCOL>(a, t, base, dplane);
+    else
+      stage_plane_vec<false, NCOL>(a, t, base, dplane);
+  }
+}
+
+// The 4-element staging applies when every plane's rows start on a 4-element
+// boundary of its type (16 bytes for FP32, 8 for BF16).
+__device__ __forceinline__ bool vec_staging(const PassArgs& a) {
+  if (a.W & 3) return false;
+  const uintptr_t m_in = a.in_dt == DT_F32 ? 15 : 7;
+  const uintptr_t m_g = a.g_dt == DT_F32 ? 15 : 7;
+  return ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.in2)) & m_in) == 0 &&
+         (reinterpret_cast<uintptr_t>(a.g) & m_g) == 0;
+}
+
+// Dispatch: 4-element transfers when aligned; otherwise per-element copies
+// (asynchronous for FP32, plain loads for BF16 or mixed types).
 template <int CC, int NCOL>
 __device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t) {
   const int ncol = NCOL;
-  const bool aligned = ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.in2) |
-                         reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 && (a.W & 3) == 0;
-  if (a.in_dt == DT_F32 && a.g_dt == DT_F32 && aligned)
+  if (vec_staging(a))
     stage_tile_vec<CC, NCOL>(a, t);
   else if (a.in_dt == DT_F32 && a.g_dt == DT_F32)
     stage_tile_async<CC, NCOL>(a, t);
@@ -756,10 +834,7 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int
   t.tl0 = c0 * a.h - 1;
   t.ntl = min((c0 + G) * a.h, a.L) + 1 - t.tl0;
   t.off0 = off0;
-  const bool vec = a.dir == 0 && a.in_dt == DT_F32 && a.g_dt == DT_F32 &&
-                   ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.in2) |
-                     reinterpret_cast<uintptr_t>(a.g)) & 15) == 0 && (a.W & 3) == 0;
-  t.cs = vec ? (off0 & 3) : 0;
+  t.cs = (a.dir == 0 && vec_staging(a)) ? (off0 & 3) : 0;
   t.pitch = tile_pitch(r, a.dir);
   t.p = p;
 }
@@ -1627,10 +1702,30 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
     const long long ostride = a.dir == 0 ? 1 : a.W;
     const long long lstride = a.dir == 0 ? a.W : 1;
     float* const outp = reinterpret_cast<float*>(a.out);
+    // r = 1: a line's factor rows (3 x (2 + CC) values) live in registers and
+    // the next line's are fetched while this one is solved
+    constexpr bool PF = false;
+    constexpr int PN = PF ? n : 1, PNF = PF ? NFAC : 1;
+    float cur[PN][PNF];
+    auto fetch = [&](int line, float (&dst)[PN][PNF], bool last_line) {
+      const float* fl = fac + (long long)line * n * NFAC * ss;
+#pragma unroll
+      for (int j = 0; j < PN; ++j) {
+        if (last_line && q.bot && j >= n - R) continue;
+#pragma unroll
+        for (int f = 0; f < PNF; ++f)
+          if (f < R + CC || q.top) dst[j][f] = __ldcg(fl + (j * NFAC + f) * ss);
+      }
+    };
+    if constexpr (PF) fetch(q.line1 - 1, cur, true);
     for_lines_rev(q.line0, q.line1, [&](auto odd, auto last, int line) {
       constexpr bool ODD = decltype(odd)::value;
       constexpr bool LAST = decltype(last)::value;
       float xl[n][CC];
+      float nxt[PN][PNF];
+      if constexpr (PF) {
+        if (line > q.line0) fetch(line - 1, nxt, false);
+      }
       const float* fl = fac + (long long)line * n * NFAC * ss;
 #pragma unroll LineUnroll<R>::value
       for (int j = n - 1; j >= 0; --j) {
@@ -1643,15 +1738,19 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
               for (int ch = 0; ch < CC; ++ch) x[ch] = xB[i][ch];
         } else {
           const float* fe = fl + (long long)j * NFAC * ss;
+          auto fv = [&](int f) -> float {
+            if constexpr (PF) return cur[j < PN ? j : 0][f < PNF ? f : 0];
+            else return __ldcg(fe + f * ss);
+          };
           float Lrow[R];
 #pragma unroll
-          for (int tt = 0; tt < R; ++tt) Lrow[tt] = __ldcg(fe + tt * ss);
+          for (int tt = 0; tt < R; ++tt) Lrow[tt] = fv(tt);
 #pragma unroll
-          for (int ch = 0; ch < CC; ++ch) x[ch] = __ldcg(fe + (R + ch) * ss);
+          for (int ch = 0; ch < CC; ++ch) x[ch] = fv(R + ch);
           if (q.top) {
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-              const float ph = __ldcg(fe + (R + CC + i) * ss);
+              const float ph = fv(R + CC + i);
 #pragma unroll
               for (int ch = 0; ch < CC; ++ch) x[ch] += ph * xT[i][ch];
             }
@@ -1681,6 +1780,14 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
         // dynamically, which places it in local memory)
 #pragma unroll
         for (int ch = 0; ch < CC; ++ch) xl[j][ch] = x[ch];
+      }
+      if constexpr (PF) {
+        if (line > q.line0) {
+#pragma unroll
+          for (int j = 0; j < PN; ++j)
+#pragma unroll
+            for (int f = 0; f < PNF; ++f) cur[j][f] = nxt[j][f];
+        }
       }
       // inverse construction + averaging: value at across-offset kc - R + e
       const long long pix = (long long)line * lstride + (long long)o * ostride;

@@ -37,11 +37,14 @@ def _batch(n, seed, lo, hi, C=1):
     return imgs, guides, [float(x) for x in lams]
 
 
+@pytest.mark.parametrize("factor_cache", [0, 2])
 @pytest.mark.parametrize("r,C", [(2, 1), (1, 3), (3, 1)])
-def test_batched_uneven_matches_oracle(api, r, C):
+def test_batched_uneven_matches_oracle(api, r, C, factor_cache):
+    """7 images, sides 2r+1 .. 90 (single-chunk images beside multi-group
+    ones), chunk factors kept (automatic at these sizes) and recomputed."""
     import torch
     imgs, guides, lams = _batch(7, seed=40 + r, lo=2 * r + 1, hi=90, C=C)
-    kw = dict(r=r, iters=2, sigma_r=0.1)
+    kw = dict(r=r, iters=2, sigma_r=0.1, factor_cache=factor_cache)
     fs = [torch.from_numpy(x).cuda() for x in imgs]
     gs = [torch.from_numpy(x).cuda() for x in guides]
     outs = api.sgwls_filter_batched(fs, gs, lams, **kw)
