@@ -54,12 +54,13 @@ struct PassArgs {
   int* band_cnt;       // per band of 32 subsystems: k_summary blocks finished (0 between passes)
   int chain_smem;      // the reduced chain of a band fits in k_summary's shared memory
   // Chunk factors kept between the two kernels of a pass (null: k_recover
-  // recomputes them).  fac[(e * (2r + CC) + f) * sstride + sys] for vector
-  // entry e of an interior: f < r: L[e, e-1..e-r]; then z0 = D^-1 L^-1 f
-  // (CC values); then Phi = -D^-1 L^-1 A(I, S_top) (r values, chunks with a
-  // top separator).  psi[((c * r + k) * r + i) * sstride + sys]: the
-  // bottom-separator column i of -D^-1 L^-1 A(I, S_bot) at the chunk's k-th
-  // of its last r interior entries (the only rows where it is not zero).
+  // recomputes them), per band of 32 subsystems (sys = 32 band + lane):
+  // fac[band][e][f][lane] for vector entry e of an interior: f < r:
+  // L[e, e-1..e-r]; then z0 = D^-1 L^-1 f (CC values); then Phi =
+  // -D^-1 L^-1 A(I, S_top) (r values, chunks with a top separator).
+  // psi[band][c][k][i][lane]: the bottom-separator column i of
+  // -D^-1 L^-1 A(I, S_bot) at chunk c's k-th of its last r interior entries
+  // (the only rows where it is not zero).
   float* fac;
   float* psi;
   // Planes 0 .. n_in1-1 come from `in`, planes n_in1 .. CC-1 from `in2`

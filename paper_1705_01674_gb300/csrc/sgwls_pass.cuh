@@ -104,13 +104,13 @@ __device__ __forceinline__ const char* plane_base(const PassArgs& a, int pl, int
 
 // Mixed storage types (BF16 guidance with FP32 estimates): plain loop.
 template <int CC>
-__device__ __noinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, int ncol) {
+__device__ __noinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, int ncol, int p0, int p1) {
   const int nthreads = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int per_plane = t.ntl * ncol;
-  for (int idx = tid; idx < (CC + 1) * per_plane; idx += nthreads) {
-    const int pl = idx / per_plane;
-    const int rest = idx - pl * per_plane;
+  for (int idx = tid; idx < (p1 - p0) * per_plane; idx += nthreads) {
+    const int pl = p0 + idx / per_plane;
+    const int rest = idx - (pl - p0) * per_plane;
     const int tl = rest / ncol, col = rest - tl * ncol;
     const int line = t.tl0 + tl, off = t.off0 + col;
     float v = 0.f;
@@ -135,11 +135,11 @@ __device__ __forceinline__ float ld_plane(const void* base, long long idx) {
 // lines.  Row direction: lanes along the lines (contiguous in memory), warps
 // over the offsets.  Each thread issues U loads before its stores.
 template <int CC, bool F32>
-__device__ __noinline__ void stage_tile_t(const PassArgs& a, const Tile& t, int ncol) {
+__device__ __noinline__ void stage_tile_t(const PassArgs& a, const Tile& t, int ncol, int p0, int p1) {
   const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
   constexpr int U = 4;
 #pragma unroll 1
-  for (int pl = 0; pl <= CC; ++pl) {
+  for (int pl = p0; pl < p1; ++pl) {
     const char* base = plane_base<CC>(a, pl, F32 ? 4 : 2);
     float* dplane = t.p + pl * t.ntl * t.pitch;
     if (a.dir == 0) {
@@ -206,12 +206,12 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <int CC, int NCOL>
-__device__ __noinline__ void stage_tile_async(const PassArgs& a, const Tile& t) {
+__device__ __noinline__ void stage_tile_async(const PassArgs& a, const Tile& t, int p0, int p1) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nthreads = blockDim.x * blockDim.y;
   const long long W = a.W;
 #pragma unroll 1
-  for (int pl = 0; pl <= CC; ++pl) {
+  for (int pl = p0; pl < p1; ++pl) {
     const float* base = reinterpret_cast<const float*>(plane_base<CC>(a, pl, 4));
     float* dplane = t.p + pl * t.ntl * t.pitch;
     if (a.dir == 0) {
@@ -392,9 +392,9 @@ __device__ __forceinline__ void stage_plane_vec(const PassArgs& a, const Tile& t
 
 // Every plane with 4-element transfers, each in its own storage type.
 template <int CC, int NCOL>
-__device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t) {
+__device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t, int p0, int p1) {
 #pragma unroll 1
-  for (int pl = 0; pl <= CC; ++pl) {
+  for (int pl = p0; pl < p1; ++pl) {
     const int dt = pl < CC ? a.in_dt : a.g_dt;
     const void* base = plane_base<CC>(a, pl, dt == DT_F32 ? 4 : 2);
     float* dplane = t.p + pl * t.ntl * t.pitch;
@@ -416,18 +416,19 @@ __device__ __forceinline__ bool vec_staging(const PassArgs& a) {
 }
 
 // Dispatch: 4-element transfers when aligned; otherwise per-element copies
-// (asynchronous for FP32, plain loads for BF16 or mixed types).
+// (asynchronous for FP32, plain loads for BF16 or mixed types).  Planes
+// [p0, p1): the estimate planes are 0 .. CC-1, the guidance plane CC.
 template <int CC, int NCOL>
-__device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t) {
+__device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t, int p0 = 0, int p1 = CC + 1) {
   const int ncol = NCOL;
   if (vec_staging(a))
-    stage_tile_vec<CC, NCOL>(a, t);
+    stage_tile_vec<CC, NCOL>(a, t, p0, p1);
   else if (a.in_dt == DT_F32 && a.g_dt == DT_F32)
-    stage_tile_async<CC, NCOL>(a, t);
+    stage_tile_async<CC, NCOL>(a, t, p0, p1);
   else if (a.in_dt == DT_BF16 && a.g_dt == DT_BF16)
-    stage_tile_t<CC, false>(a, t, ncol);
+    stage_tile_t<CC, false>(a, t, ncol, p0, p1);
   else
-    stage_tile_mixed<CC>(a, t, ncol);
+    stage_tile_mixed<CC>(a, t, ncol, p0, p1);
 }
 
 // Column (relative to the lane's strip start) of entry j of a line.
@@ -455,6 +456,41 @@ __device__ __forceinline__ void forward_weights(const PassArgs& a, const float* 
     const float gq = jt < n ? gr[ecol<R, ODD>(jt)] : gnr[ecol<R, !ODD>(jt - n)];
     const float w = a.sp[j * R + t - 1] * range_factor(a, g0 - gq);
     wf[t - 1] = (jt < n || end_ok) ? w : 0.f;
+  }
+}
+
+// lambda * w(p, p+t) of every entry of a line (j = 0..2r, t = 1..r), one
+// branch on the weight form per line instead of one per pair.
+template <int R, bool ODD>
+__device__ __forceinline__ void line_weights(const PassArgs& a, const float* gr, const float* gnr, bool end_ok,
+                                             float (&wl)[2 * R + 1][R]) {
+  constexpr int n = 2 * R + 1;
+  float g[n + R];   // guidance of the line's entries, then of the next line's first r
+#pragma unroll
+  for (int j = 0; j < n; ++j) g[j] = gr[ecol<R, ODD>(j)];
+#pragma unroll
+  for (int k = 0; k < R; ++k) g[n + k] = gnr[ecol<R, !ODD>(k)];
+  if (a.weight == 0) {
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int t = 1; t <= R; ++t) {
+        const float d = g[j] - g[j + t];
+        wl[j][t - 1] = a.sp[j * R + t - 1] * fast_ex2(d * d * a.range_k);
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int t = 1; t <= R; ++t)
+        wl[j][t - 1] = a.sp[j * R + t - 1] / (powf(fabsf(g[j] - g[j + t]), a.range_k) + a.eps);
+  }
+  if (!end_ok) {
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int t = 1; t <= R; ++t)
+        if (j + t >= n) wl[j][t - 1] = 0.f;
   }
 }
 
@@ -673,18 +709,32 @@ struct StridedG {
 // ---------------------------------------------------------------------------
 // Forward sweep of one chunk for the summary: eliminates the interior and
 // writes its 2-port to `out`.
+// Factor store of one subsystem (band of 32 subsystems, lane in the band):
+// fac[band][e][field][32] with e = line * (2r+1) + j over the L lines and
+// field < 2r + CC; psi[band][c][k][i][32].  Inside a band every offset is a
+// compile-time multiple of 32 floats from the line's base.
+template <int R, int CC>
+__device__ __forceinline__ float* fac_lane(const PassArgs& a, int sys) {
+  const size_t band = (size_t)a.L * (2 * R + 1) * (2 * R + CC) * 32;
+  return a.fac + (size_t)(sys >> 5) * band + (sys & 31);
+}
+template <int R>
+__device__ __forceinline__ float* psi_lane(const PassArgs& a, int sys) {
+  const size_t band = (size_t)a.P * R * R * 32;
+  return a.psi + (size_t)(sys >> 5) * band + (sys & 31);
+}
 // With a.fac set it also keeps, per interior entry, the factor row, z0 and
 // Phi for k_backsub, and psi for the last r interior entries.
-template <int R, int CC>
+template <int R, int CC, bool KEEP>
 __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int lane, int sys, int c,
                                               Strided out) {
   constexpr int n = 2 * R + 1;
   constexpr int NFAC = 2 * R + CC;
+  constexpr bool LW = LineUnroll<R>::value > 1;   // a line's weights computed together
   using F = Fields<R, CC>;
   const Chunk q = make_chunk<R>(a, c);
   const int pstride = t.ntl * t.pitch;
-  const long long ss = a.sstride;
-  float* const fac = a.fac ? a.fac + sys : nullptr;
+  float* const fac = KEEP ? fac_lane<R, CC>(a, sys) : nullptr;
 
   float wh[R][R] = {};
   float Lw[R][R] = {};
@@ -706,10 +756,17 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
     const float* gnr = t.row(CC, line + 1) + lane;
     const float* fr = t.row(0, line) + lane;
     const bool end_ok = line + 1 < a.L;
+    float wl[LW ? n : 1][R];
+    if constexpr (LW) line_weights<R, ODD>(a, gr, gnr, end_ok, wl);
 #pragma unroll LineUnroll<R>::value
     for (int j = 0; j < n; ++j) {
       float wf[R];
-      forward_weights<R, ODD>(a, gr, gnr, j, end_ok, wf);
+      if constexpr (LW) {
+#pragma unroll
+        for (int tt = 0; tt < R; ++tt) wf[tt] = wl[LW ? j : 0][tt];
+      } else {
+        forward_weights<R, ODD>(a, gr, gnr, j, end_ok, wf);
+      }
       float diag = 1.f;
 #pragma unroll
       for (int tt = 0; tt < R; ++tt) diag += wf[tt] + wh[tt][tt];
@@ -728,35 +785,32 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
         float YT[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) YT[i] = 0.f;
-        if (q.top) {
-          if (FIRST) {
-            // E_T[p][i] = A[p, b-R+i] = -lambda w(p-tt, p), tt = j + R - i
+        // Top-separator terms, tracked in every chunk: without a separator
+        // above (chunk 0) the prologue weights wh are zero, so YT, KTT and
+        // HT stay zero and no branch is needed.
+        // E_T[p][i] = A[p, b-R+i] = -lambda w(p-tt, p), tt = j + R - i
 #pragma unroll
-            for (int i = 0; i < R; ++i)
+        for (int i = 0; i < R; ++i)
 #pragma unroll
-              for (int tt = 1; tt <= R; ++tt)
-                if (tt == j + R - i) YT[i] = -wh[tt - 1][tt - 1];
-          }
-          fwd_subst<R, R>(Lrow, YTw, YT);
+          for (int tt = 1; tt <= R; ++tt)
+            if (tt == j + R - i) YT[i] = FIRST ? -wh[tt - 1][tt - 1] : 0.f;
+        fwd_subst<R, R>(Lrow, YTw, YT);
 #pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float yd = YT[i] * dinv;
+        for (int i = 0; i < R; ++i) {
+          const float yd = YT[i] * dinv;
 #pragma unroll
-            for (int m = 0; m < R; ++m) KTT[i][m] += yd * YT[m];
+          for (int m = 0; m < R; ++m) KTT[i][m] += yd * YT[m];
 #pragma unroll
-            for (int ch = 0; ch < CC; ++ch) HT[i][ch] += yd * y[ch];
-          }
+          for (int ch = 0; ch < CC; ++ch) HT[i][ch] += yd * y[ch];
         }
-        if (fac) {
-          float* fe = fac + (long long)(line * n + j) * NFAC * ss;
+        if constexpr (KEEP) {
+          float* fe = fac + ((line * n + j) * NFAC) * 32;
 #pragma unroll
-          for (int tt = 0; tt < R; ++tt) fe[tt * ss] = Lrow[tt];
+          for (int tt = 0; tt < R; ++tt) fe[tt * 32] = Lrow[tt];
 #pragma unroll
-          for (int ch = 0; ch < CC; ++ch) fe[(R + ch) * ss] = y[ch] * dinv;
-          if (q.top) {
+          for (int ch = 0; ch < CC; ++ch) fe[(R + ch) * 32] = y[ch] * dinv;
 #pragma unroll
-            for (int i = 0; i < R; ++i) fe[(R + CC + i) * ss] = -YT[i] * dinv;
-          }
+          for (int i = 0; i < R; ++i) fe[(R + CC + i) * 32] = -YT[i] * dinv;
         }
         float YB[R];
 #pragma unroll
@@ -781,10 +835,10 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
 #pragma unroll
               for (int ch = 0; ch < CC; ++ch) HB[i][ch] += yd * y[ch];
             }
-            if (fac) {
-              float* pe = a.psi + sys + (long long)(c * R + (j - (n - 2 * R))) * R * ss;
+            if constexpr (KEEP) {
+              float* pe = psi_lane<R>(a, sys) + ((c * R + (j - (n - 2 * R))) * R) * 32;
 #pragma unroll
-              for (int i = 0; i < R; ++i) pe[i * ss] = -YB[i] * dinv;
+              for (int i = 0; i < R; ++i) pe[i * 32] = -YB[i] * dinv;
             }
           }
           push_vec<R, R>(YBw, YB);
@@ -866,20 +920,38 @@ __device__ __forceinline__ void fold_2ports(int n, bool acc_top, In&& in, HasBot
       qB[i][ch] = cs[F::GS + i * CC + ch];
     }
   }
+  // Small 2-ports: element i's fields are read one merge ahead (before merge
+  // i-1 writes its factors, which may overwrite element i-1 in place), so
+  // the loads leave the serial path.
+  constexpr bool PREF = F::N <= 40;
+  constexpr int NB = PREF ? F::N : 1;
+  float nb[NB], cb[NB];
+  auto load = [&](int i) {
+    auto src = in(i);
+#pragma unroll
+    for (int f = 0; f < NB; ++f) nb[f] = src[f];
+  };
+  if (PREF && n > 1) load(1);
   for (int i = 1; i < n; ++i) {
     const bool b_bot = has_bot(i);
-    auto bs = in(i);
+    auto direct = in(i);
+    if constexpr (PREF) {
+#pragma unroll
+      for (int f = 0; f < NB; ++f) cb[f] = nb[f];
+      if (i + 1 < n) load(i + 1);
+    }
+    auto bs = [&](int f) -> float { if constexpr (PREF) return cb[f < NB ? f : 0]; else return direct[f]; };
     float M[R][R], U[R][R], V[R][R], w[R][CC];
 #pragma unroll
     for (int y = 0; y < R; ++y) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        M[y][m] = EBB[y][m] - bs[F::KTT + y * R + m];
+        M[y][m] = EBB[y][m] - bs(F::KTT + y * R + m);
         U[y][m] = ETB[m][y];                       // E_YX = E_XY^T
-        V[y][m] = -bs[F::KTB + y * R + m];         // E_YZ
+        V[y][m] = -bs(F::KTB + y * R + m);         // E_YZ
       }
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) w[y][ch] = qB[y][ch] - bs[F::HT + y * CC + ch];
+      for (int ch = 0; ch < CC; ++ch) w[y][ch] = qB[y][ch] - bs(F::HT + y * CC + ch);
     }
     chol_inplace<R>(M);
     lsolve<R, R>(M, U);
@@ -897,9 +969,9 @@ __device__ __forceinline__ void fold_2ports(int n, bool acc_top, In&& in, HasBot
 #pragma unroll
     for (int y = 0; y < R; ++y) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) EBB[y][m] = b_bot ? bs[F::DS + y * R + m] : 0.f;
+      for (int m = 0; m < R; ++m) EBB[y][m] = b_bot ? bs(F::DS + y * R + m) : 0.f;
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) qB[y][ch] = b_bot ? bs[F::GS + y * CC + ch] : 0.f;
+      for (int ch = 0; ch < CC; ++ch) qB[y][ch] = b_bot ? bs(F::GS + y * CC + ch) : 0.f;
     }
     if (b_bot) {
       add_atb<R, R>(EBB, V, V, -1.f);
@@ -970,20 +1042,38 @@ __device__ __forceinline__ void backfill_2ports(int n, bool acc_top, const float
   }
 }
 
-// Merges the block's chunk 2-ports into the group 2-port (warp 0, lane =
-// subsystem) and writes the merge factors for the back-fill.  Out of line:
-// it runs once per block and keeps the sweep's code small.
+// Merges the block's chunk 2-ports into the group 2-port as a binary tree:
+// at level l warp w merges the node of chunks [2w 2^l, (2w+1) 2^l) with its
+// right neighbour (in place, slot of the left node), so the serial depth is
+// log2(G) merges instead of G-1.  Merge (l, w) keeps its factors in mdata
+// slot G - (G >> l) + w of the group (lane = subsystem).  The group 2-port
+// goes to summ.  Every thread of the block calls this (barriers).
 template <int R, int CC>
-__device__ __noinline__ void merge_block(const PassArgs& a, float* csum, int lane, int sys, int grp, int c0,
-                                         int nch, int G) {
+__device__ __forceinline__ void merge_tree(const PassArgs& a, float* csum, int lane, int sys, int grp, int c0,
+                                           int nch, int G, bool active) {
   using F = Fields<R, CC>;
   using MF = MFields<R, CC>;
   const long long ns = a.sstride;
-  fold_2ports<R, CC>(
-      nch, c0 > 0, [&](int i) { return Strided{csum + i * F::N * 32 + lane, 32}; },
-      [&](int i) { return c0 + i < a.P - 1; },
-      [&](int i) { return StridedG{a.mdata + ((long long)(grp * (G - 1) + (i - 1)) * MF::N) * ns + sys, ns}; },
-      StridedG{a.summ + (long long)grp * F::N * ns + sys, ns});
+  auto slot = [&](int i) { return Strided{csum + i * F::N * 32 + lane, 32}; };
+  for (int span = 1; span < nch; span *= 2) {
+    const int left = threadIdx.y * 2 * span;
+    if (active && left + span < nch) {
+      const int id = G - G / span + threadIdx.y;   // G - (G >> l) + w
+      const int last = min(left + 2 * span, nch) - 1;
+      fold_2ports<R, CC>(
+          2, c0 + left > 0, [&](int i) { return slot(left + i * span); },
+          [&](int) { return c0 + last < a.P - 1; },
+          [&](int) { return StridedG{a.mdata + ((long long)(grp * (G - 1) + id) * MF::N) * ns + sys, ns}; },
+          slot(left));
+    }
+    __syncthreads();
+  }
+  if (threadIdx.y == 0 && active) {
+    const Strided g0 = slot(0);
+    StridedG gs{a.summ + (long long)grp * F::N * ns + sys, ns};
+#pragma unroll
+    for (int f = 0; f < F::N; ++f) gs[f] = g0[f];
+  }
 }
 
 // Block Cholesky of the separator system of NG consecutive 2-ports of one
@@ -1108,12 +1198,15 @@ __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, int NG
   }
 }
 
-// Segments of the reduced chain of NG group 2-ports run by nw warps: about
-// sqrt(NG) (a fold step costs about 1.5 chain steps), at most nw.
-__host__ __device__ inline int chain_segments(int NG, int nw) {
+// Segment length of the reduced chain of NG group 2-ports run by nw warps:
+// about sqrt(NG) segments of m 2-ports (a fold step costs about 1.5 chain
+// steps), at most nw of them; the last segment may be shorter.
+__host__ __device__ inline int chain_segment_len(int NG, int nw) {
   int S = 1;
   while ((S + 1) * (S + 1) <= (NG * 6) / 5) ++S;
-  return S < nw ? S : nw;
+  int m = (NG + S - 1) / S;
+  while ((NG + m - 1) / m > nw) ++m;
+  return m;
 }
 
 // Reduced system of one band (32 subsystems).  When the band's group
@@ -1151,7 +1244,8 @@ __device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* sme
   cp_async_wait_all();
   __syncthreads();
   auto slot = [&](int g) { return Strided{smem + g * F::N * 32 + lane, 32}; };
-  const int S = chain_segments(NG, blockDim.y);
+  const int m = chain_segment_len(NG, blockDim.y);
+  const int S = (NG + m - 1) / m;
   if (S < 2) {
     if (threadIdx.y != 0) return;
     reduced_chain<R, CC>(
@@ -1160,7 +1254,7 @@ __device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* sme
     return;
   }
   const int w = threadIdx.y;
-  auto seg0 = [&](int sg) { return (sg * NG) / S; };   // first group of segment sg
+  auto seg0 = [&](int sg) { return min(sg * m, NG); };   // first group of segment sg
   const int g0 = seg0(w), g1 = seg0(w + 1);
   auto has_bot = [&](int i) { return g0 + i < NG - 1; };
   auto mf = [&](int i) { return slot(g0 + i); };
@@ -1205,18 +1299,26 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   Tile t;
   group_tile(a, c0, G, bx * 32, R, smem, t);
   float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
+  // The guidance is an input of the whole filter (no kernel of the filter
+  // writes it): its plane is staged before the wait, overlapping the
+  // preceding kernel's tail; the estimate planes after it.
+  stage_tile<CC, 32 + 2 * R>(a, t, CC, CC + 1);
   griddep_wait();
   griddep_launch();
-  stage_tile<CC, 32 + 2 * R>(a, t);
+  stage_tile<CC, 32 + 2 * R>(a, t, 0, CC);
   cp_async_wait_all();
   __syncthreads();
 
   const bool active = sys < a.nsys;
   if (active && threadIdx.y < nch) {
-    chunk_summary<R, CC>(a, t, lane, sys, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
+    const Strided out{csum + threadIdx.y * F::N * 32 + lane, 32};
+    if (a.fac)
+      chunk_summary<R, CC, true>(a, t, lane, sys, c, out);
+    else
+      chunk_summary<R, CC, false>(a, t, lane, sys, c, out);
   }
   __syncthreads();
-  if (threadIdx.y == 0 && active) merge_block<R, CC>(a, csum, lane, sys, grp, c0, nch, G);
+  merge_tree<R, CC>(a, csum, lane, sys, grp, c0, nch, G, active);
   if (a.ngroups < 2) return;   // one group: no reduced system
   // The last block of this band of 32 subsystems to finish (an atomic ticket
   // taken after a memory fence; nothing waits) solves the band's reduced
@@ -1239,11 +1341,12 @@ __global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArg
 }
 
 // Separator values of every chunk of a group (one block): loads the group's
-// merge factors (asynchronous copies, one warp per merge) and its two outer
-// separators, then warp 0 back-fills the separators between its chunks
-// (lane = subsystem).  ports[(i * 2 + side) * r*CC * 32 + lane] receives the
-// top (side 0) and bottom (side 1) separator of chunk c0 + i; mbuf holds the
-// merge factors.  Waits for all of the block's asynchronous copies.
+// merge factors (asynchronous copies) and its two outer separators, then
+// back-fills the separators between its chunks down the merge tree of
+// merge_tree, one warp per merge of a level (lane = subsystem).
+// ports[(i * 2 + side) * r*CC * 32 + lane] receives the top (side 0) and
+// bottom (side 1) separator of chunk c0 + i; mbuf holds the merge factors.
+// Waits for all of the block's asynchronous copies.
 template <int R, int CC>
 __device__ __forceinline__ void group_ports(const PassArgs& a, int grp, int c0, int nch, int sys, int lane,
                                             float* ports, float* mbuf) {
@@ -1251,7 +1354,8 @@ __device__ __forceinline__ void group_ports(const PassArgs& a, int grp, int c0, 
   constexpr int XS = R * CC;
   const int G = blockDim.y;
   const long long ns = a.sstride;
-  for (int i = threadIdx.y; i < nch - 1; i += G) {
+  // (the tree's merge slots are not contiguous when nch < G: copy all G-1)
+  for (int i = threadIdx.y; i < (nch > 1 ? G - 1 : 0); i += G) {
     const float* src = a.mdata + ((long long)(grp * (G - 1) + i) * MF::N) * ns + sys;
     float* dst = mbuf + i * MF::N * 32 + lane;
 #pragma unroll
@@ -1267,43 +1371,54 @@ __device__ __forceinline__ void group_ports(const PassArgs& a, int grp, int c0, 
   }
   cp_async_wait_all();
   __syncthreads();
+  // the group's outer separators: top of its first chunk, bottom of its last
   if (threadIdx.y == 0) {
     const float* xo = mbuf + (G - 1) * MF::N * 32 + lane;
-    float xX[R][CC], xZ[R][CC];
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) {
-        xX[i][ch] = xo[(i * CC + ch) * 32];
-        xZ[i][ch] = xo[(XS + i * CC + ch) * 32];
-      }
-    backfill_2ports<R, CC>(
-        nch, c0 > 0, xX, xZ, [&](int i) { return c0 + i < a.P - 1; },
-        [&](int i) { return Strided{mbuf + (i - 1) * MF::N * 32 + lane, 32}; },
-        [&](int i, const float (&v)[R][CC]) {
-          // separator between chunks c0+i-1 and c0+i; the bottom of chunk
-          // c0+i is the value put just before (or the group's lower port)
-          float* pp = ports + (i * 2) * XS * 32 + lane;
-          float* pb = ports + (i * 2 - 1) * XS * 32 + lane;
-#pragma unroll
-          for (int y = 0; y < R; ++y)
-#pragma unroll
-            for (int ch = 0; ch < CC; ++ch) {
-              pp[(y * CC + ch) * 32] = v[y][ch];
-              pb[(y * CC + ch) * 32] = v[y][ch];
-            }
-        });
     float* pp = ports + lane;
     float* pl = ports + ((nch - 1) * 2 + 1) * XS * 32 + lane;
 #pragma unroll
-    for (int y = 0; y < R; ++y)
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) {
-        pp[(y * CC + ch) * 32] = xX[y][ch];
-        pl[(y * CC + ch) * 32] = xo[(XS + y * CC + ch) * 32];
-      }
+    for (int i = 0; i < XS; ++i) {
+      pp[i * 32] = xo[i * 32];
+      pl[i * 32] = xo[(XS + i) * 32];
+    }
   }
   __syncthreads();
+  // back-fill down the merge tree (the merges of merge_tree in reverse): the
+  // separator of merge (l, w) lies between chunks left+span-1 and left+span
+  int top = 1;
+  while (top < nch) top *= 2;
+  for (int span = top / 2; span >= 1; span /= 2) {
+    const int left = threadIdx.y * 2 * span;
+    if (left + span < nch) {
+      const int id = G - G / span + threadIdx.y;
+      const int last = min(left + 2 * span, nch) - 1;
+      float xX[R][CC], xZ[R][CC];
+      const float* pt = ports + (left * 2) * XS * 32 + lane;        // top of chunk left
+      const float* pb = ports + (last * 2 + 1) * XS * 32 + lane;    // bottom of chunk last
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) {
+          xX[i][ch] = pt[(i * CC + ch) * 32];
+          xZ[i][ch] = pb[(i * CC + ch) * 32];
+        }
+      backfill_2ports<R, CC>(
+          2, c0 + left > 0, xX, xZ, [&](int) { return c0 + last < a.P - 1; },
+          [&](int) { return Strided{mbuf + id * MF::N * 32 + lane, 32}; },
+          [&](int, const float (&v)[R][CC]) {
+            float* p0 = ports + ((left + span - 1) * 2 + 1) * XS * 32 + lane;   // bottom of chunk left+span-1
+            float* p1 = ports + ((left + span) * 2) * XS * 32 + lane;           // top of chunk left+span
+#pragma unroll
+            for (int y = 0; y < R; ++y)
+#pragma unroll
+              for (int ch = 0; ch < CC; ++ch) {
+                p0[(y * CC + ch) * 32] = v[y][ch];
+                p1[(y * CC + ch) * 32] = v[y][ch];
+              }
+          });
+    }
+    __syncthreads();
+  }
 }
 
 // Row direction: writes the block's staged output lines ([NOUT][OB][lines],
@@ -1696,7 +1811,8 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
       const int lo = max(R, o - R), hi = min(a.D - 1 - R, o + R);
       inv_cnt = 1.0f / (float)(hi - lo + 1);
     }
-    const float* const fac = a.fac + sys;
+    const float* const fac = fac_lane<R, CC>(a, sys);
+    const float* const psi = psi_lane<R>(a, sys);
     float Lb[R][R] = {};   // Lb[u-1][t-1] = L[p+u, p+u-t]
     float xw[R][CC] = {};  // x of entries p+1 .. p+R (interior only)
     const long long ostride = a.dir == 0 ? 1 : a.W;
@@ -1708,13 +1824,13 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
     constexpr int PN = PF ? n : 1, PNF = PF ? NFAC : 1;
     float cur[PN][PNF];
     auto fetch = [&](int line, float (&dst)[PN][PNF], bool last_line) {
-      const float* fl = fac + (long long)line * n * NFAC * ss;
+      const float* fl = fac + line * n * NFAC * 32;
 #pragma unroll
       for (int j = 0; j < PN; ++j) {
         if (last_line && q.bot && j >= n - R) continue;
 #pragma unroll
         for (int f = 0; f < PNF; ++f)
-          if (f < R + CC || q.top) dst[j][f] = __ldcg(fl + (j * NFAC + f) * ss);
+          if (f < R + CC || q.top) dst[j][f] = __ldcg(fl + (j * NFAC + f) * 32);
       }
     };
     if constexpr (PF) fetch(q.line1 - 1, cur, true);
@@ -1726,7 +1842,7 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
       if constexpr (PF) {
         if (line > q.line0) fetch(line - 1, nxt, false);
       }
-      const float* fl = fac + (long long)line * n * NFAC * ss;
+      const float* fl = fac + line * n * NFAC * 32;
 #pragma unroll LineUnroll<R>::value
       for (int j = n - 1; j >= 0; --j) {
         float x[CC];
@@ -1737,10 +1853,10 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
 #pragma unroll
               for (int ch = 0; ch < CC; ++ch) x[ch] = xB[i][ch];
         } else {
-          const float* fe = fl + (long long)j * NFAC * ss;
+          const float* fe = fl + j * NFAC * 32;
           auto fv = [&](int f) -> float {
             if constexpr (PF) return cur[j < PN ? j : 0][f < PNF ? f : 0];
-            else return __ldcg(fe + f * ss);
+            else return __ldcg(fe + f * 32);
           };
           float Lrow[R];
 #pragma unroll
@@ -1756,10 +1872,10 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
             }
           }
           if (LAST && q.bot && j >= n - 2 * R) {
-            const float* pe = a.psi + sys + (long long)(c * R + (j - (n - 2 * R))) * R * ss;
+            const float* pe = psi + ((c * R + (j - (n - 2 * R))) * R) * 32;
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-              const float ps = __ldcg(pe + i * ss);
+              const float ps = __ldcg(pe + i * 32);
 #pragma unroll
               for (int ch = 0; ch < CC; ++ch) x[ch] += ps * xB[i][ch];
             }

@@ -351,3 +351,19 @@ def test_close_to_full_wls_2d():
         ref = wls2d(F, F, lam, prm)[0]
         U = sgwls(F, F, lam, prm)[0]
         assert rms(U - ref) < 0.6 * rms(F - ref)
+
+
+def test_sampled_pass_offsets_match_whole_pass():
+    """The per-offset pass oracle used by the full-size GPU tests equals the
+    whole-image pass at every offset of a small image, both directions."""
+    from sampled_pass import oracle_pass_offsets
+    F = synth.rgb_scene(23, 29, seed=12, n_rect=6, n_disk=2)
+    G = synth.luminance(F)
+    for r in (1, 2):
+        prm = Params(r=r, iters=1, sigma_s=float(r), sigma_r=0.1)
+        for d, dim in ((COLUMN, 29), (ROW, 23)):
+            whole = sgwls_pass(F.astype(np.float64), G.astype(np.float64), 1.3, prm, d)
+            offs = list(range(dim))
+            got = oracle_pass_offsets(F, G, 1.3, prm, d, offs)
+            ref = whole if d == ROW else whole.transpose(0, 2, 1)
+            assert np.abs(got - ref).max() < 1e-12
