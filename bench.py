@@ -61,6 +61,28 @@ def _dist():
     return rank, world, local
 
 
+def _rank_seed(rank: int) -> int:
+    """Every rank filters its own synthetic image (weak scaling)."""
+    return WL["seed"] + rank
+
+
+def _max_over_ranks(x: float, world: int, device) -> float:
+    """Max of a per-rank duration over all ranks (the job ends with the
+    slowest rank); identity for one rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(world: int, mp_per_step: float, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the work of all ranks over the slowest rank's time."""
+    return world * mp_per_step * steps / (total_ms / 1e3)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -225,7 +247,7 @@ def run_ours(args):
     import paper_1705_01674_gb300 as sg
 
     H, W, C, T = WL["H"], WL["W"], WL["C"], WL["iters"]
-    F, G = _inputs(WL["seed"] + rank)
+    F, G = _inputs(_rank_seed(rank))
     f = torch.from_numpy(F).to(dev)
     g = torch.from_numpy(G).to(dev)
     bufs = [torch.empty_like(f), torch.empty_like(f)]
@@ -291,13 +313,9 @@ def run_ours(args):
     pass_ms = [[evs[i][t][0].elapsed_time(evs[i][t][1]) for t in range(npass)] for i in range(args.steps)]
     col_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 0)
     row_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = _max_over_ranks(total_ms, world, dev)
     mp_per_step = H * W / 1e6 * T
-    value = world * mp_per_step * args.steps / (total_ms / 1e3)
+    value = _job_value(world, mp_per_step, args.steps, total_ms)
 
     # accuracy of the last lambda-2.0 output against the oracle (rank 0)
     # and the CPU baseline: the oracle, single-threaded, same image.
@@ -341,13 +359,8 @@ def run_ours(args):
             if i >= args.warmup:
                 e2e_ms.append((e0, e1))
     torch.cuda.synchronize(dev)
-    e2e_total = sum(a.elapsed_time(b) for a, b in e2e_ms)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
-    e2e_value = world * mp_per_step * args.steps / (e2e_total / 1e3)
+    e2e_total = _max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ms), world, dev)
+    e2e_value = _job_value(world, mp_per_step, args.steps, e2e_total)
 
     peak, peak_kind = _peaks()
     bytes_per_pass = H * W * (C * 4 + C * 4 + 4)   # read estimate, read guidance, write estimate
