@@ -280,8 +280,17 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    # timed region: one event pair around each step (the 2T passes run
-    # back to back, each kernel overlapping its predecessor's tail)
+    # timed region: one event pair around each step, a step being one call
+    # of the filter (its 2T passes run back to back, each kernel overlapping
+    # its predecessor's tail)
+    uo = torch.empty_like(f)
+
+    def filt(lam):
+        sg.sgwls_filter(f, g, lam, out=uo, workspace=ws, stream=stream, **kw)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            filt(WL["lams"][i % 2])
     step_evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
                 for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -293,7 +302,7 @@ def run_ours(args):
         for i in range(args.steps):
             flush.zero_()
             step_evs[i][0].record(stream)
-            step(WL["lams"][i % 2])
+            filt(WL["lams"][i % 2])
             step_evs[i][1].record(stream)
     torch.cuda.synchronize(dev)
     n1 = sg.launch_count()
@@ -423,7 +432,8 @@ def _timed(fn, steps, warmup, flush, stream):
 def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     """Forward+backward (16 RGB 512x512, r=1, T=3), batched uneven sizes
     (64 gray images, sides U[256, 2048], r=2, T=2, lambda U[0.5, 4]) against
-    single-image calls, and BF16 storage of the main workload."""
+    single-image calls, BF16 storage of the main workload, and guided sparse
+    interpolation (Eq. 21) on a 4x depth-upsampling pattern."""
     import numpy as np
     import torch
 
@@ -495,6 +505,46 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     mp2 = WL["H"] * WL["W"] / 1e6 * WL["iters"]
     out["bf16_storage"] = {"workload": WL["name"] + " (BF16 input/guidance/output, FP32 intermediates)",
                            "value": mp2 / (ms_h / 1e3), "unit": UNIT, "ms_per_step": ms_h}
+    del fb, gb, ub
+
+    # guided sparse interpolation (Eq. 21): 4x depth upsampling pattern on
+    # the workload's size, guidance = the scene's luminance; r = 4, sigma_s
+    # = 4, sigma_r = 3 / 255, lambda = 200 (the paper's 4x setting), T = 2
+    Fd, Hd, _ = synth.sparse_depth(WL["H"], WL["W"], factor=4, seed=6)
+    fd = torch.from_numpy(Fd).to(dev)
+    hd = torch.from_numpy(Hd).to(dev)
+    gd = torch.from_numpy(G2).to(dev)
+    ud = torch.empty_like(fd)
+    kwi = dict(r=4, iters=2, sigma_r=3.0 / 255.0)
+
+    def interp(i):
+        sg.sgwls_interpolate(fd, hd, gd, 200.0, out=ud, stream=stream, **kwi)
+
+    ms_i = _timed(interp, steps, warmup, flush, stream) / steps
+    mpi = WL["H"] * WL["W"] / 1e6 * 2
+    out["interpolate"] = {"workload": f"guided 4x depth upsampling {WL['W']}x{WL['H']}, r=4, T=2, lambda=200 "
+                                      "(depth and index map as 2 right-hand sides)",
+                          "value": mpi / (ms_i / 1e3), "unit": UNIT, "ms_per_step": ms_i}
+    del fd, hd, gd, ud
+
+    # (r, tau) sweep: one filter of a 1-megapixel RGB image, T = 3, the time
+    # per filter for every radius 1..5 and sliding step 1..r (Sec. 2.3)
+    F3 = synth.rgb_scene(1024, 1024, seed=9)
+    f3 = torch.from_numpy(F3).to(dev)
+    g3 = torch.from_numpy(synth.luminance(F3)).to(dev)
+    u3 = torch.empty_like(f3)
+    sweep = {}
+    for r in range(1, 6):
+        for tau in range(1, r + 1):
+            kws = dict(r=r, step=tau, iters=3, sigma_r=0.1)
+            ws3 = torch.empty(max(sg.workspace_bytes(3, 1024, 1024, **kws), 1), dtype=torch.uint8, device=dev)
+
+            def one(i, kws=kws, ws3=ws3):
+                sg.sgwls_filter(f3, g3, 1.0, out=u3, workspace=ws3, stream=stream, **kws)
+
+            sweep[f"r{r}_tau{tau}"] = _timed(one, 3, 1, flush, stream) / 3
+            del ws3
+    out["step_sweep"] = {"workload": "1024x1024 RGB, T=3, lambda=1: ms per filter by (r, tau)", "ms": sweep}
     return out
 
 

@@ -65,9 +65,12 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *   r           neighbourhood radius, (2r+1)x(2r+1) system, 1 <= r <= SGWLS_R_MAX
  *   iters       T, the number of (column pass, row pass) pairs, >= 0 (Sec. 2.3)
  *   step        tau, the sliding step between subsystem centres (Sec. 2.3),
- *               1 <= step <= 2r+1; the last centre is always included
+ *               1 <= step <= 2r+1 (the last centre is always included);
+ *               this build runs step = 1, other values return
+ *               SGWLS_E_UNSUPPORTED
  *   axis_order  0: column direction first (Sec. 2.3), 1: row direction first
- *   refine      reserved (0)
+ *   refine      iterative refinement of each subsystem solve; this build
+ *               runs refine = 0 (other values return SGWLS_E_UNSUPPORTED)
  *   storage     sgwls_dtype of f, g and u
  *   inter_storage  sgwls_dtype of the estimates between passes
  *   chunk_lines 0: automatic; otherwise the number of lines per chunk of
@@ -153,6 +156,27 @@ typedef struct {
   float lambda;    /* per-image lambda >= 0                           */
   void* saved;     /* must be NULL (no checkpoints in batched calls)  */
 } sgwls_image;
+
+/* Guided sparse interpolation (Sec. 2.3, Eq. 21): the SG-WLS filter applied
+ * to the sparse input F and to its index map Hm, and their ratio per pixel,
+ *   U(m) = SGWLS(F)(m) / SGWLS(Hm)(m).
+ * Both are filtered with the same guidance and parameters; F's channels and
+ * Hm are solved as right-hand sides of one factorisation per subsystem
+ * (C + 1 <= 4 share every factor).
+ *   f     device, C x H x W sparse input (FP32), zero where hmap is zero
+ *   hmap  device, H x W index map (FP32): 1 where f holds data, else 0
+ *   g     device, H x W guidance (FP32)
+ *   u     device, C x H x W output (FP32); a pixel that no data reaches
+ *         (filtered index map exactly 0) is 0
+ *   ws    device workspace of at least sgwls_interpolate_workspace_bytes
+ *         bytes, 256-byte aligned
+ * p->storage and p->inter_storage must be SGWLS_F32 (else
+ * SGWLS_E_UNSUPPORTED).  Asynchronous on `stream`; u must not alias f or
+ * hmap.  Other errors as sgwls_filter. */
+size_t sgwls_interpolate_workspace_bytes(int H, int W, int C, const sgwls_params* p);
+sgwls_status sgwls_interpolate(const void* f, const void* hmap, const void* g, void* u, int H, int W, int C,
+                               float lambda, const sgwls_params* p, void* ws, size_t ws_bytes,
+                               void* stream);
 
 /* Workspace bytes sgwls_filter_batched needs for these images (0 if the
  * arguments are invalid).  Host-only; `imgs` is a host array. */

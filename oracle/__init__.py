@@ -38,4 +38,5 @@ from .sgwls import (  # noqa: F401
     coverage_counts,
     sgwls_pass,
     sgwls,
+    sgwls_interpolate,
 )

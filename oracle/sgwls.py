@@ -199,3 +199,17 @@ def sgwls(F: np.ndarray, G: np.ndarray, lam: float, prm: Params, return_inputs: 
         inputs.append(U)
         U = sgwls_pass(U, G, lam, prm, direction)
     return (U, inputs) if return_inputs else U
+
+
+def sgwls_interpolate(F: np.ndarray, Hm: np.ndarray, G: np.ndarray, lam: float, prm: Params,
+                      return_parts: bool = False):
+    """Guided sparse interpolation (Sec. 2.3, Eq. 21): the SG-WLS smoothing
+    applied to the sparse input F and to its index map Hm (1 where F holds
+    data, 0 elsewhere), and their ratio per pixel.  Reading: a pixel that no
+    data reaches (smoothed index map exactly 0) is 0.
+
+    F: (C, H, W) or (H, W), zero where Hm is zero; Hm, G: (H, W)."""
+    N = sgwls(F, G, lam, prm)
+    D = sgwls(np.asarray(Hm, dtype=np.float64), G, lam, prm)[0]
+    U = np.where(D > 0, N / np.where(D > 0, D, 1.0), 0.0)
+    return (U, N, D) if return_parts else U

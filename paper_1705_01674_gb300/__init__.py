@@ -22,6 +22,7 @@ from . import _capi
 from ._capi import SgwlsError, make_params
 
 __all__ = ["sgwls", "sgwls_filter", "sgwls_filter_pass", "sgwls_filter_backward", "sgwls_filter_batched",
+           "sgwls_interpolate",
            "batched_workspace_bytes", "SGWLSFunction",
            "workspace_bytes", "launch_count", "make_params", "SgwlsError"]
 
@@ -87,6 +88,39 @@ def sgwls_filter(f: torch.Tensor, g: torch.Tensor, lam: float, *, out: torch.Ten
         ctypes.c_void_p(saved.data_ptr() if saved is not None else 0),
         ctypes.c_void_p(st.cuda_stream))
     _capi.check(status, "sgwls_filter")
+    return out
+
+
+def sgwls_interpolate(f: torch.Tensor, hmap: torch.Tensor, g: torch.Tensor, lam: float, *,
+                      out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                      stream: torch.cuda.Stream | None = None, **kw) -> torch.Tensor:
+    """Guided sparse interpolation (Eq. 21) through ``sgwls_interpolate``:
+    SG-WLS(f) / SG-WLS(hmap) per pixel.  f: (C,H,W) or (H,W) float32, zero
+    where hmap is zero; hmap, g: (H,W) float32.  Keyword parameters: see
+    ``make_params``."""
+    _check_tensor(f, "f")
+    _check_tensor(hmap, "hmap")
+    _check_tensor(g, "g")
+    C, H, W = _chw(f)
+    if tuple(g.shape) != (H, W) or tuple(hmap.shape) != (H, W):
+        raise ValueError("hmap and g must be (H, W)")
+    if not (f.dtype == hmap.dtype == g.dtype == torch.float32):
+        raise TypeError("f, hmap and g must be float32")
+    p = make_params(**kw)
+    lib = _capi.lib()
+    if out is None:
+        out = torch.empty_like(f)
+    else:
+        _check_tensor(out, "out")
+    nws = lib.sgwls_interpolate_workspace_bytes(H, W, C, ctypes.byref(p))
+    if workspace is None or workspace.numel() < nws:
+        workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    status = lib.sgwls_interpolate(
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(hmap.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+        ctypes.c_void_p(out.data_ptr()), H, W, C, ctypes.c_float(float(lam)), ctypes.byref(p),
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()), ctypes.c_void_p(st.cuda_stream))
+    _capi.check(status, "sgwls_interpolate")
     return out
 
 

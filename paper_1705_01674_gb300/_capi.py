@@ -104,6 +104,10 @@ def _declare(lib):
         lib.sgwls_backward_workspace_bytes.restype = sz
         lib.sgwls_filter_backward.argtypes = [vp, vp, vp, ci, ci, ci, cf, P, vp, vp, vp, vp, sz, vp]
         lib.sgwls_filter_backward.restype = ci
+    lib.sgwls_interpolate_workspace_bytes.argtypes = [ci, ci, ci, P]
+    lib.sgwls_interpolate_workspace_bytes.restype = sz
+    lib.sgwls_interpolate.argtypes = [vp, vp, vp, vp, ci, ci, ci, cf, P, vp, sz, vp]
+    lib.sgwls_interpolate.restype = ci
     return lib
 
 

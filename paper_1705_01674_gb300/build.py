@@ -1,9 +1,12 @@
 """Builds libsgwls.so in-tree with nvcc for sm_103a (GB300).
 
-Each translation unit under csrc/ is compiled in parallel, then linked into
+Translation units: ``csrc/sgwls_api.cu``, ``csrc/sgwls_noalloc.cu`` and
+``csrc/sgwls_inst.cu`` compiled once per (radius 1..8, channel group 1..4)
+pair with ``-DSGWLS_R`` / ``-DSGWLS_CC`` (the kernels of one pair per object,
+so the 34 compilations run in parallel), then linked into
 ``paper_1705_01674_gb300/libsgwls.so``.  Objects go to ``_build/`` next to
-this file.  A TU is rebuilt only when it or a header is newer than its
-object.  Usage: ``python -m paper_1705_01674_gb300.build [--force]``.
+this file; an object is rebuilt only when its source or a header is newer.
+Usage: ``python -m paper_1705_01674_gb300.build [--force]``.
 
 Development shortcut: with ``SGWLS_RADII=1,2`` only those radii are
 compiled; the launchers of the other radii are built as stubs that return
@@ -40,38 +43,47 @@ def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _radius_of(src: str):
-    base = os.path.basename(src)
-    if base.startswith("sgwls_r") and base[7:-3].isdigit():
-        return int(base[7:-3])
-    return None
+RADII = range(1, 9)
+GROUPS = range(1, 5)
 
 
-def _compile(src: str, force: bool, extra) -> str:
+def _units():
+    """(source, object base name, extra flags, radius or None) of every TU."""
+    units = [(os.path.join(CSRC, "sgwls_api.cu"), "sgwls_api", [], None),
+             (os.path.join(CSRC, "sgwls_noalloc.cu"), "sgwls_noalloc", [], None)]
+    inst = os.path.join(CSRC, "sgwls_inst.cu")
+    for r in RADII:
+        for cc in GROUPS:
+            units.append((inst, f"sgwls_inst_r{r}_c{cc}", [f"-DSGWLS_R={r}", f"-DSGWLS_CC={cc}"], r))
+    return units
+
+
+def _compile(unit, force: bool, extra) -> str:
+    src, name, flags, r = unit
     radii = os.environ.get("SGWLS_RADII")
-    r = _radius_of(src)
     stub = bool(radii) and r is not None and str(r) not in radii.split(",")
-    tag = ".stub.o" if stub else ".o"
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", tag))
-    if stub:
-        extra = list(extra) + ["-DSGWLS_STUB_RADIUS"]
+    obj = os.path.join(BUILD, name + (".stub.o" if stub else ".o"))
+    flags = list(flags) + list(extra) + (["-DSGWLS_STUB_RADIUS"] if stub else [])
     if not force and os.path.exists(obj):
         newest = max(os.path.getmtime(p) for p in [src] + _headers())
         if os.path.getmtime(obj) >= newest:
             return obj
-    cmd = [_nvcc(), *ARCH, *NVFLAGS, *extra, "-c", src, "-o", obj]
+    cmd = [_nvcc(), *ARCH, *NVFLAGS, *flags, "-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError(f"nvcc failed for {src}:\n{res.stdout}\n{res.stderr}")
+        raise RuntimeError(f"nvcc failed for {name}:\n{res.stdout}\n{res.stderr}")
     return obj
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    workers = max(1, min(len(srcs), os.cpu_count() or 4))
+    units = _units()
+    # the large radii compile longest: start them first
+    order = sorted(units, key=lambda u: -(u[3] or 0))
+    workers = max(1, min(len(units), os.cpu_count() or 4))
     with cf.ThreadPoolExecutor(workers) as ex:
-        objs = list(ex.map(lambda s: _compile(s, force, list(extra)), srcs))
+        done = dict(zip([u[1] for u in order], ex.map(lambda u: _compile(u, force, list(extra)), order)))
+    objs = [done[u[1]] for u in units]
     if True:  # linking is cheap; relink so stub/full object sets never mix up
         cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -57,12 +57,23 @@ constexpr int kGMax = 8;
 // fewer than kTargetWarps chunk-warps.
 inline int keep_lines(int r) { return r == 1 ? 6 : r == 2 ? 12 : r == 3 ? 8 : 16; }
 
+// Subsystems of a pass across D offsets with sliding step `step`: the
+// regular centres r, r + step, ... <= D-1-r, and the last centre D-1-r
+// appended when the stride misses it (reading D7).  *nreg: regular ones.
+int n_centres(int D, int r, int step, int* nreg) {
+  const int nr = (D - 1 - 2 * r) / step + 1;
+  if (nreg) *nreg = nr;
+  return nr + (((nr - 1) * step != D - 1 - 2 * r) ? 1 : 0);
+}
+
 // keep: the pass keeps its chunk factors (k_backsub follows k_summary; no
 // k_recover tile), so only the summary's tile and 2-ports bound the block.
-Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, bool keep = false) {
-  const int bands = (D + (32 - 2 * r) - 1) / (32 - 2 * r);
-  auto second = [&](int hh, int G) { return keep ? smem_backsub(r, CC, hh, G) : smem_recover(r, CC, hh, G, bwd); };
-  auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G)); };
+Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, bool keep = false, int step = 1) {
+  const int bands = step == 1 ? (D + (32 - 2 * r) - 1) / (32 - 2 * r) : (n_centres(D, r, step, nullptr) + 31) / 32;
+  auto second = [&](int hh, int G) {
+    return keep ? smem_backsub(r, CC, hh, G, step) : smem_recover(r, CC, hh, G, bwd);
+  };
+  auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G, step)); };
   int h;
   if (keep) {
     h = keep_lines(r);
@@ -76,6 +87,8 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   if (chunk_lines > 0) h = std::min(chunk_lines, L);
   while (h > 1 && block(h, 1) > kSmemBlockMax) --h;
   h = std::min(h, L);
+  // the sliding-step path keeps factors, which needs at least two chunks
+  if (step > 1 && h >= L && L >= 2) h = (L + 1) / 2;
   Plan pl;
   pl.h = h;
   pl.P = (L + h - 1) / h;
@@ -85,7 +98,7 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   while (G < kGMax && G < pl.P && block(h, 2 * G) <= gcap) G *= 2;
   pl.G = G;
   pl.NG = (pl.P + G - 1) / G;
-  pl.smem_sum = smem_summary(r, CC, h, G);
+  pl.smem_sum = smem_summary(r, CC, h, G, step);
   pl.smem_rec = smem_recover(r, CC, h, G, bwd);
   return pl;
 }
@@ -115,7 +128,8 @@ size_t psi_bytes(int P, int r, int sstride) { return (size_t)P * r * r * sstride
 // two kernels (needs at least two chunks).
 Plan fwd_plan(const sgwls_params* p, int L, int D, int CC, int sstride, bool* keep) {
   bool k = p->factor_cache == 1 || (p->factor_cache == 0 && fac_bytes(L, p->r, CC, sstride) <= kFactorCacheBytes);
-  Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k);
+  if (p->step > 1) k = true;   // the sliding-step path runs on kept factors only
+  Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k, p->step);
   if (k && pl.P < 2) {
     k = false;
     pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, false);
@@ -137,7 +151,7 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
-    const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
+    const int nsys = (n_centres(D, r, p->step, nullptr) + 31) / 32 * 32;   // padded subsystem stride
     for (int c0 = 0; c0 < C; c0 += kGroupMax) {
       const int CC = std::min(kGroupMax, C - c0);
       bool keep = false;
@@ -194,22 +208,27 @@ sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
   if (C < 1 || C > SGWLS_C_MAX) return SGWLS_E_SHAPE;
   if (H < 2 * p->r + 1 || W < 2 * p->r + 1) return SGWLS_E_SHAPE;
   if (H > 65536 || W > 65536 || (long long)H * W > (1LL << 31) / 4) return SGWLS_E_SHAPE;
-  if (p->step != 1) return SGWLS_E_UNSUPPORTED;
   return SGWLS_OK;
 }
 
-PassLauncher launcher_for(int r) {
-  switch (r) {
-    case 1: return launch_pass_r1;
-    case 2: return launch_pass_r2;
-    case 3: return launch_pass_r3;
-    case 4: return launch_pass_r4;
-    case 5: return launch_pass_r5;
-    case 6: return launch_pass_r6;
-    case 7: return launch_pass_r7;
-    case 8: return launch_pass_r8;
-    default: return nullptr;
+// The sliding step tau > 1 runs on the kernels that keep chunk factors: it
+// needs them kept in every pass (not factor_cache = 2, not beyond the
+// factor-store budget, at least two lines per subsystem).
+sgwls_status check_step(int H, int W, int C, const sgwls_params* p) {
+  if (p->step == 1) return SGWLS_OK;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int L = dir == 0 ? H : W;
+    const int D = dir == 0 ? W : H;
+    const int nsys = (n_centres(D, p->r, p->step, nullptr) + 31) / 32 * 32;
+    for (int c0 = 0; c0 < C; c0 += kGroupMax) {
+      bool keep = false;
+      fwd_plan(p, L, D, std::min(kGroupMax, C - c0), nsys, &keep);
+      if (!keep || p->factor_cache == 2) return SGWLS_E_UNSUPPORTED;
+      if (fac_bytes(L, p->r, std::min(kGroupMax, C - c0), nsys) > kFactorCacheBytes && p->factor_cache != 1)
+        return SGWLS_E_UNSUPPORTED;
+    }
   }
+  return SGWLS_OK;
 }
 
 // Fills the parts of the argument block that depend only on the parameters.
@@ -267,6 +286,43 @@ sgwls_status copy_image(const void* src, int sdt, void* dst, int ddt, long long 
 
 }  // namespace
 
+// Dispatch to the (radius, channel group) instantiations.
+#define SGWLS_CASE_CC(R)                                                         \
+  case R:                                                                        \
+    switch (CC < 0 ? -CC : CC) {                                                 \
+      case 1: return launch_pass_inst<R, 1>(a, pl, CC < 0, st);                 \
+      case 2: return launch_pass_inst<R, 2>(a, pl, CC < 0, st);                 \
+      case 3: return launch_pass_inst<R, 3>(a, pl, CC < 0, st);                 \
+      case 4: return launch_pass_inst<R, 4>(a, pl, CC < 0, st);                 \
+      default: return cudaErrorInvalidValue;                                     \
+    }
+cudaError_t launch_pass_any(int r, int CC, const PassArgs& a, const Plan& pl, cudaStream_t st) {
+  switch (r) {
+    SGWLS_CASE_CC(1) SGWLS_CASE_CC(2) SGWLS_CASE_CC(3) SGWLS_CASE_CC(4)
+    SGWLS_CASE_CC(5) SGWLS_CASE_CC(6) SGWLS_CASE_CC(7) SGWLS_CASE_CC(8)
+    default: return cudaErrorInvalidValue;
+  }
+}
+#undef SGWLS_CASE_CC
+#define SGWLS_CASE_CC(R)                                                         \
+  case R:                                                                        \
+    switch (CC) {                                                                \
+      case 1: return launch_batch_inst<R, 1>(ba, bl, st);                        \
+      case 2: return launch_batch_inst<R, 2>(ba, bl, st);                        \
+      case 3: return launch_batch_inst<R, 3>(ba, bl, st);                        \
+      case 4: return launch_batch_inst<R, 4>(ba, bl, st);                        \
+      default: return cudaErrorInvalidValue;                                     \
+    }
+cudaError_t launch_batch_any(int r, int CC, const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st) {
+  switch (r) {
+    SGWLS_CASE_CC(1) SGWLS_CASE_CC(2) SGWLS_CASE_CC(3) SGWLS_CASE_CC(4)
+    SGWLS_CASE_CC(5) SGWLS_CASE_CC(6) SGWLS_CASE_CC(7) SGWLS_CASE_CC(8)
+    default: return cudaErrorInvalidValue;
+  }
+}
+#undef SGWLS_CASE_CC
+
+
 // One pass along `dir` (Sec. 2.3, the four steps): out = pass(in).
 sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const void* g, int H, int W, int C,
                       float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st, bool zero_counters) {
@@ -289,14 +345,14 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
   a.dir = dir;
   a.L = dir == 0 ? H : W;
   a.D = dir == 0 ? W : H;
-  a.nsys = a.D - 2 * p->r;
+  a.step = p->step;
+  a.nsys = n_centres(a.D, p->r, p->step, &a.nreg);
   a.sstride = (a.nsys + 31) / 32 * 32;
   a.summ = reinterpret_cast<float*>(wsb + lo.summ_off);
   a.xsep = reinterpret_cast<float*>(wsb + lo.xsep_off);
   a.mdata = reinterpret_cast<float*>(wsb + lo.mdata_off);
   a.band_cnt = reinterpret_cast<int*>(wsb + lo.cnt_off);
   fill_weights(a, p, lambda);
-  const PassLauncher launch = launcher_for(p->r);
   for (int c0 = 0; c0 < C; c0 += kGroupMax) {
     const int CC = std::min(kGroupMax, C - c0);
     bool keep = false;
@@ -310,7 +366,7 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.out = static_cast<char*>(out) + (size_t)c0 * plane * dt_size(out_dt);
     a.fac = keep ? reinterpret_cast<float*>(wsb + lo.fac_off) : nullptr;
     a.psi = keep ? reinterpret_cast<float*>(wsb + lo.psi_off) : nullptr;
-    cudaError_t e = launch(a, pl, CC, st);
+    cudaError_t e = launch_pass_any(p->r, CC, a, pl, st);
     if (e != cudaSuccess) return cuda_fail(e);
     __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 2 : 1), __ATOMIC_RELAXED);
   }
@@ -361,23 +417,61 @@ sgwls_status run_filter(const void* f, const void* g, void* u, int H, int W, int
 }
 
 // ---------------------------------------------------------------------------
-// Batched filter: many images of uneven sizes, one launch per kernel per pass.
+// Guided sparse interpolation (Eq. 21): filter [F, Hm] as C + 1 channels of
+// one image (one factorisation per subsystem for up to four channels), then
+// divide.  Workspace: the stacked input, the filtered stack, the filter's own
+// workspace.
 
 namespace {
 
-BatchLauncher batch_launcher_for(int r) {
-  switch (r) {
-    case 1: return launch_batch_r1;
-    case 2: return launch_batch_r2;
-    case 3: return launch_batch_r3;
-    case 4: return launch_batch_r4;
-    case 5: return launch_batch_r5;
-    case 6: return launch_batch_r6;
-    case 7: return launch_batch_r7;
-    case 8: return launch_batch_r8;
-    default: return nullptr;
-  }
+struct InterpLayout {
+  size_t stack_in, stack_out, filt, total;
+};
+
+InterpLayout make_interp_layout(int H, int W, int C, const sgwls_params* p) {
+  InterpLayout lo;
+  const size_t plane = (size_t)H * W * sizeof(float);
+  lo.stack_in = 0;
+  lo.stack_out = align256((size_t)(C + 1) * plane);
+  lo.filt = lo.stack_out + align256((size_t)(C + 1) * plane);
+  lo.total = lo.filt + make_layout(H, W, C + 1, p).total;
+  return lo;
 }
+
+// u[c] = x[c] / x[C] where the filtered index map x[C] is positive, else 0.
+__global__ void k_ratio(const float* __restrict__ x, float* __restrict__ u, long long plane, int C) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= plane) return;
+  const float d = x[(long long)C * plane + i];
+  const float inv = d > 0.f ? 1.0f / d : 0.f;
+  for (int c = 0; c < C; ++c) u[(long long)c * plane + i] = x[(long long)c * plane + i] * inv;
+}
+
+}  // namespace
+
+sgwls_status run_interpolate(const float* f, const float* hmap, const float* g, float* u, int H, int W, int C,
+                             float lambda, const sgwls_params* p, void* ws, cudaStream_t st) {
+  const InterpLayout lo = make_interp_layout(H, W, C, p);
+  char* wsb = static_cast<char*>(ws);
+  float* xin = reinterpret_cast<float*>(wsb + lo.stack_in);
+  float* xout = reinterpret_cast<float*>(wsb + lo.stack_out);
+  const size_t plane = (size_t)H * W;
+  cudaError_t e = cudaMemcpyAsync(xin, f, (size_t)C * plane * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(xin + (size_t)C * plane, hmap, plane * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  sgwls_status s = run_filter(xin, g, xout, H, W, C + 1, lambda, p, wsb + lo.filt, nullptr, st);
+  if (s != SGWLS_OK) return s;
+  k_ratio<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(xout, u, (long long)plane, C);
+  __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SGWLS_OK : cuda_fail(e);
+}
+
+// ---------------------------------------------------------------------------
+// Batched filter: many images of uneven sizes, one launch per kernel per pass.
+
+namespace {
 
 // Whether the passes of a batched call keep their chunk factors: every
 // image's factors within the single-image budget (or factor_cache = 1).
@@ -455,6 +549,7 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
 
 sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) {
   if (B < 1 || !imgs || !p) return SGWLS_E_INVALID;
+  if (p->step != 1) return SGWLS_E_UNSUPPORTED;   // the sliding step runs on single images
   const int C = imgs[0].C;
   if (C < 1 || C > kGroupMax) return C < 1 ? SGWLS_E_SHAPE : SGWLS_E_UNSUPPORTED;
   for (int i = 0; i < B; ++i) {
@@ -500,7 +595,6 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
   }
   const bool keep = batch_keep(B, imgs, p);
   const int h0 = batch_h(r, C, keep);
-  const BatchLauncher launch = batch_launcher_for(r);
   const int OB = 32 - 2 * r;
   const int npass = 2 * p->iters;
   std::vector<BatchImgLayout> lay(B);
@@ -530,6 +624,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
       a.in_dt = t == 0 ? sdt : idt;
       a.g_dt = sdt;
       a.n_in1 = C;
+      a.step = 1;
       fill_weights(a, p, 1.0f);   // sp0 (lambda applied per image)
       ba->nimg = nb;
       BatchLaunch bl = {};
@@ -608,7 +703,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
       bl.nblk[2] = b[2];
       bl.red_smem = red_max <= kReducedSmemMax;
       bl.smem[1] = bl.red_smem ? red_max : 0;
-      cudaError_t e = launch(*ba, bl, C, st);
+      cudaError_t e = launch_batch_any(r, C, *ba, bl, st);
       if (e != cudaSuccess) return cuda_fail(e);
       __atomic_add_fetch(&g_launches, (unsigned long long)(1 + (bl.any_multi ? 1 : 0)), __ATOMIC_RELAXED);
     }
@@ -693,7 +788,6 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
     e = cudaMemcpyAsync(grad_f, grad_u, (size_t)count * sizeof(float), cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? SGWLS_OK : cuda_fail(e);
   }
-  const PassLauncher launch = launcher_for(p->r);
   const float* vbar = grad_u;
   for (int t = npass - 1; t >= 0; --t) {
     const int dir = ((t & 1) == 0) ? p->axis_order : 1 - p->axis_order;
@@ -715,6 +809,8 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
     a.L = dir == 0 ? H : W;
     a.D = dir == 0 ? W : H;
     a.nsys = a.D - 2 * p->r;
+    a.step = 1;
+    a.nreg = a.nsys;
     a.sstride = (a.nsys + 31) / 32 * 32;
     a.summ = reinterpret_cast<float*>(wsb + lo.summ);
     a.xsep = reinterpret_cast<float*>(wsb + lo.xsep);
@@ -733,7 +829,7 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
       a.in2 = w0 + (size_t)c0 * plane;
       a.n_in1 = nch;
       a.out = dst + (size_t)c0 * plane;
-      e = launch(a, pl, -2 * nch, st);
+      e = launch_pass_any(p->r, -2 * nch, a, pl, st);
       if (e != cudaSuccess) return cuda_fail(e);
       __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 2 : 1), __ATOMIC_RELAXED);
     }
@@ -784,13 +880,14 @@ const char* sgwls_status_string(sgwls_status s) {
 const char* sgwls_last_cuda_error(void) { return g_cuda_err; }
 
 size_t sgwls_workspace_bytes(int H, int W, int C, const sgwls_params* p) {
-  if (check_params(H, W, C, p) != SGWLS_OK) return 0;
+  if (check_params(H, W, C, p) != SGWLS_OK || check_step(H, W, C, p) != SGWLS_OK) return 0;
   return make_layout(H, W, C, p).total;
 }
 
 sgwls_status sgwls_filter(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
                           const sgwls_params* p, void* ws, size_t ws_bytes, void* saved, void* stream) {
   sgwls_status s = check_params(H, W, C, p);
+  if (s == SGWLS_OK) s = check_step(H, W, C, p);
   if (s != SGWLS_OK) return s;
   if (!f || !g || !u || f == u) return SGWLS_E_INVALID;
   if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
@@ -802,6 +899,7 @@ sgwls_status sgwls_filter(const void* f, const void* g, void* u, int H, int W, i
 sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
                                const sgwls_params* p, int direction, void* ws, size_t ws_bytes, void* stream) {
   sgwls_status s = check_params(H, W, C, p);
+  if (s == SGWLS_OK) s = check_step(H, W, C, p);
   if (s != SGWLS_OK) return s;
   if (!f || !g || !u || f == u) return SGWLS_E_INVALID;
   if (direction != 0 && direction != 1) return SGWLS_E_INVALID;
@@ -812,6 +910,27 @@ sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int
                   static_cast<cudaStream_t>(stream), true);
 }
 
+size_t sgwls_interpolate_workspace_bytes(int H, int W, int C, const sgwls_params* p) {
+  if (C < 1 || C + 1 > SGWLS_C_MAX || check_params(H, W, C + 1, p) != SGWLS_OK) return 0;
+  if (check_step(H, W, C + 1, p) != SGWLS_OK) return 0;
+  return make_interp_layout(H, W, C, p).total;
+}
+
+sgwls_status sgwls_interpolate(const void* f, const void* hmap, const void* g, void* u, int H, int W, int C,
+                               float lambda, const sgwls_params* p, void* ws, size_t ws_bytes, void* stream) {
+  if (C < 1 || C + 1 > SGWLS_C_MAX) return SGWLS_E_SHAPE;
+  sgwls_status s = check_params(H, W, C + 1, p);
+  if (s == SGWLS_OK) s = check_step(H, W, C + 1, p);
+  if (s != SGWLS_OK) return s;
+  if (p->storage != SGWLS_F32 || p->inter_storage != SGWLS_F32) return SGWLS_E_UNSUPPORTED;
+  if (!f || !hmap || !g || !u || u == f || u == hmap) return SGWLS_E_INVALID;
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
+  const size_t need = make_interp_layout(H, W, C, p).total;
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
+  return run_interpolate(static_cast<const float*>(f), static_cast<const float*>(hmap), static_cast<const float*>(g),
+                         static_cast<float*>(u), H, W, C, lambda, p, ws, static_cast<cudaStream_t>(stream));
+}
+
 unsigned long long sgwls_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 }  // extern "C"
@@ -819,7 +938,7 @@ unsigned long long sgwls_launch_count(void) { return __atomic_load_n(&g_launches
 extern "C" {
 
 size_t sgwls_backward_workspace_bytes(int H, int W, int C, const sgwls_params* p) {
-  if (check_params(H, W, C, p) != SGWLS_OK) return 0;
+  if (check_params(H, W, C, p) != SGWLS_OK || p->step != 1) return 0;
   return make_bwd_layout(H, W, C, p).total;
 }
 
@@ -833,6 +952,7 @@ sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void
   if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
   if (p->storage != SGWLS_F32 || p->inter_storage != SGWLS_F32) return SGWLS_E_UNSUPPORTED;
   if (p->weight == SGWLS_W_FRAC && p->alpha_r < 1.f) return SGWLS_E_UNSUPPORTED;
+  if (p->step != 1) return SGWLS_E_UNSUPPORTED;
   const size_t need = make_bwd_layout(H, W, C, p).total;
   if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
   return run_backward(static_cast<const float*>(grad_u), static_cast<const float*>(g),

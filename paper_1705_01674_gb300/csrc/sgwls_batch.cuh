@@ -76,6 +76,7 @@ __device__ __forceinline__ void build_args(const BatchArgs& ba, int i, PassArgs&
     sa.L = d.L;
     sa.D = d.D;
     sa.nsys = d.nsys;
+    sa.nreg = d.nsys;
     sa.sstride = d.sstride;
     sa.h = d.h;
     sa.P = d.P;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(256) k_backsub_b(const __grid_constant__ Batch
   const int local = blockIdx.x - ba.img[i].b0[2];
   const int by = local / ba.img[i].nbx[2];
   build_args(ba, i, sa);
-  body_backsub<R, CC>(sa, local - by * ba.img[i].nbx[2], by, smem);
+  body_backsub<R, CC, false>(sa, local - by * ba.img[i].nbx[2], by, smem);
 }
 
 }  // namespace sgwls

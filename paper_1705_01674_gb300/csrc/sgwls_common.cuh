@@ -35,7 +35,9 @@ struct PassArgs {
   int dir;             // 0 column direction, 1 row direction
   int D;               // extent across the lines (number of columns for dir 0)
   int L;               // number of lines (rows for dir 0)
-  int nsys;            // number of centres: D - 2r (step 1)
+  int nsys;            // number of centres (subsystems): D - 2r for step 1
+  int step;            // sliding step tau between centres (Sec. 2.3)
+  int nreg;            // regular centres r + s step, s < nreg; centre nsys-1 = D-1-r when nsys > nreg
   int sstride;         // subsystem stride of the scratch arrays: nsys rounded up to 32
   int h;               // lines per chunk
   int P;               // chunks per subsystem
@@ -75,6 +77,13 @@ struct PassArgs {
   float sp0[(2 * kRMax + 1) * kRMax];
   float dgk;
 };
+
+// Across-offset of the centre of subsystem s: r + s step for the regular
+// centres; the last centre D-1-r is appended when the stride misses it
+// (Sec. 2.3 sliding construction; every line stays covered).
+__device__ __forceinline__ int centre_of(const PassArgs& a, int s, int r) {
+  return s < a.nreg ? r + s * a.step : a.D - 1 - r;
+}
 
 __device__ __forceinline__ float ld_px(const void* base, long long idx, int dt) {
   if (dt == DT_F32) return __ldg(reinterpret_cast<const float*>(base) + idx);

@@ -16,9 +16,12 @@ struct Plan {
 };
 
 // Shared memory of the two tiled kernels for a plan (bytes).
-inline size_t tile_floats(int r, int CC, int h, int G) { return (size_t)(CC + 1) * (G * h + 2) * tile_pitch_max(r); }
-inline size_t smem_summary(int r, int CC, int h, int G) {
-  return 4 * (tile_floats(r, CC, h, G) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
+inline size_t tile_floats(int r, int CC, int h, int G, int step = 1) {
+  const int ncol = tile_ncol(r, step);
+  return (size_t)(CC + 1) * (G * h + 2) * std::max(tile_pitch_n(ncol, 0), tile_pitch_n(ncol, 1));
+}
+inline size_t smem_summary(int r, int CC, int h, int G, int step = 1) {
+  return 4 * (tile_floats(r, CC, h, G, step) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
 }
 inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
   const int n = 2 * r + 1;
@@ -31,17 +34,16 @@ inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
 }
 
 // k_backsub: group ports and merge factors, plus the row-direction output
-// staging.
-inline size_t smem_backsub(int r, int CC, int h, int G) {
+// staging; with a sliding step > 1 also each warp's accumulation rows.
+inline size_t smem_backsub(int r, int CC, int h, int G, int step = 1) {
   const size_t merge = (size_t)(G - 1) * (3 * r * r + r * CC) * 32 + 2 * (size_t)r * CC * 32;
-  const size_t otile = (size_t)CC * (32 - 2 * r) * ((G * h) | 1);
-  return 4 * ((size_t)G * 2 * r * CC * 32 + merge + otile);
+  const size_t otile = (size_t)CC * step_own_max(r, step) * ((G * h) | 1);
+  const size_t accum = step > 1 ? (size_t)G * (CC + 1) * step_acc_width(r, step) : 0;
+  return 4 * ((size_t)G * 2 * r * CC * 32 + merge + otile + accum);
 }
 
 constexpr size_t kReducedSmemMax = 96 * 1024;
 
-// Launches the kernels of one pass for a group of CC <= 4 channels.
-using PassLauncher = cudaError_t (*)(const PassArgs&, const Plan&, int CC, cudaStream_t);
 
 // Launch with programmatic stream serialization (the kernels synchronise
 // with griddep_wait before they consume the previous kernel's output).
@@ -89,9 +91,12 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   }
   if constexpr (!BWD) {
     if (b.fac) {   // the factors were kept by k_summary
-      const size_t smem = smem_backsub(R, CC, a.h, pl.G);
-      if ((e = set_smem(k_backsub<R, CC>, smem)) != cudaSuccess) return e;
-      e = launch_pdl(k_backsub<R, CC>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), smem, st, b);
+      const size_t smem = smem_backsub(R, CC, a.h, pl.G, a.step);
+      const int nbx = a.step == 1 ? (a.D + OB - 1) / OB : (a.nsys + step_owned_lanes(R, a.step) - 1) /
+                                                              step_owned_lanes(R, a.step);
+      auto kern = a.step == 1 ? k_backsub<R, CC, false> : k_backsub<R, CC, true>;
+      if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+      e = launch_pdl(kern, dim3(nbx, pl.NG), dim3(32, pl.G), smem, st, b);
       if (e != cudaSuccess) return e;
       return cudaGetLastError();
     }
@@ -100,21 +105,6 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   e = launch_pdl(k_recover<R, CC, BWD>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), pl.smem_rec, st, b);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
-}
-
-// CC > 0: forward pass over CC channels.  CC < 0: backward pass over -CC
-// right-hand sides (u and v planes of -CC/2 channels).
-template <int R>
-cudaError_t launch_pass_r(const PassArgs& a, const Plan& pl, int CC, cudaStream_t st) {
-  switch (CC) {
-    case 1: return launch_pass_rc<R, 1>(a, pl, st);
-    case 2: return launch_pass_rc<R, 2>(a, pl, st);
-    case 3: return launch_pass_rc<R, 3>(a, pl, st);
-    case 4: return launch_pass_rc<R, 4>(a, pl, st);
-    case -2: return launch_pass_rc<R, 2, true>(a, pl, st);
-    case -4: return launch_pass_rc<R, 4, true>(a, pl, st);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 // Batched pass: one launch per kernel over all images of `ba`.
@@ -152,34 +142,16 @@ cudaError_t launch_batch_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStre
   return cudaGetLastError();
 }
 
-template <int R>
-cudaError_t launch_batch_r(const BatchArgs& ba, const BatchLaunch& bl, int CC, cudaStream_t st) {
-  switch (CC) {
-    case 1: return launch_batch_rc<R, 1>(ba, bl, st);
-    case 2: return launch_batch_rc<R, 2>(ba, bl, st);
-    case 3: return launch_batch_rc<R, 3>(ba, bl, st);
-    case 4: return launch_batch_rc<R, 4>(ba, bl, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-using BatchLauncher = cudaError_t (*)(const BatchArgs&, const BatchLaunch&, int CC, cudaStream_t);
-cudaError_t launch_batch_r1(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-cudaError_t launch_batch_r2(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-cudaError_t launch_batch_r3(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-cudaError_t launch_batch_r4(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-cudaError_t launch_batch_r5(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-cudaError_t launch_batch_r6(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-cudaError_t launch_batch_r7(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-cudaError_t launch_batch_r8(const BatchArgs&, const BatchLaunch&, int, cudaStream_t);
-
-cudaError_t launch_pass_r1(const PassArgs&, const Plan&, int, cudaStream_t);
-cudaError_t launch_pass_r2(const PassArgs&, const Plan&, int, cudaStream_t);
-cudaError_t launch_pass_r3(const PassArgs&, const Plan&, int, cudaStream_t);
-cudaError_t launch_pass_r4(const PassArgs&, const Plan&, int, cudaStream_t);
-cudaError_t launch_pass_r5(const PassArgs&, const Plan&, int, cudaStream_t);
-cudaError_t launch_pass_r6(const PassArgs&, const Plan&, int, cudaStream_t);
-cudaError_t launch_pass_r7(const PassArgs&, const Plan&, int, cudaStream_t);
-cudaError_t launch_pass_r8(const PassArgs&, const Plan&, int, cudaStream_t);
+// The launchers are instantiated one (radius, channel group) per object
+// file (sgwls_inst.cu, compiled once per pair by build.py, so the builds of
+// the kernels run in parallel); the dispatchers switch on the runtime r and
+// group size.  CC < 0 in launch_pass_any: the backward pass over -CC
+// right-hand sides (u and v planes of -CC/2 channels).
+template <int R, int CC>
+cudaError_t launch_pass_inst(const PassArgs& a, const Plan& pl, bool bwd, cudaStream_t st);
+template <int R, int CC>
+cudaError_t launch_batch_inst(const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st);
+cudaError_t launch_pass_any(int r, int CC, const PassArgs& a, const Plan& pl, cudaStream_t st);
+cudaError_t launch_batch_any(int r, int CC, const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st);
 
 }  // namespace sgwls

@@ -77,21 +77,40 @@ struct MFields {
 struct Tile {
   float* p;
   int tl0, ntl, off0, pitch;
-  int cs;   // physical column of across-offset off0 (vector-aligned staging)
+  int cs;     // physical column of across-offset off0 (vector-aligned staging)
+  int ncol;   // staged columns (runtime-width staging of the sliding-step path)
   __device__ __forceinline__ const float* row(int plane, int line) const {
     return p + (plane * ntl + (line - tl0)) * pitch + cs;
   }
 };
 
+// Tile columns of a band of 32 subsystems: their strips of 2r+1 offsets,
+// centres step apart (the appended last centre lies inside that span).
+__host__ __device__ constexpr int tile_ncol(int r, int step) { return 31 * step + 2 * r + 1; }
 // Row pitch of the tile in floats: column direction, rows of whole 16-byte
 // quads starting at the 16-byte boundary at or before off0; row direction,
 // an odd pitch (transposed staging without bank conflicts).
-__host__ __device__ constexpr int tile_pitch(int r, int dir) {
-  return dir == 0 ? 4 * ((32 + 2 * r + 3 + 3) / 4) : 33 + 2 * r;
+__host__ __device__ constexpr int tile_pitch_n(int ncol, int dir) {
+  return dir == 0 ? 4 * ((ncol + 3 + 3) / 4) : (ncol | 1);
 }
+__host__ __device__ constexpr int tile_pitch(int r, int dir) { return tile_pitch_n(32 + 2 * r, dir); }
 __host__ __device__ constexpr int tile_pitch_max(int r) {
   return tile_pitch(r, 0) > tile_pitch(r, 1) ? tile_pitch(r, 0) : tile_pitch(r, 1);
 }
+
+// Sliding step > 1 (k_backsub): each warp's lanes are 32 consecutive
+// subsystems, ceil(r / step) + 1 of them on each side halo lanes whose
+// values reach the owned columns (the + 1: the appended last centre lies
+// less than step beyond the last regular one, so it reaches one subsystem
+// further back); a warp owns the columns from its first owned centre to the
+// next warp's (at most step per owned lane, plus the border columns before
+// the first centre and after the last).
+__host__ __device__ constexpr int step_halo(int r, int step) { return step == 1 ? r : (r + step - 1) / step + 1; }
+__host__ __device__ constexpr int step_owned_lanes(int r, int step) { return 32 - 2 * step_halo(r, step); }
+__host__ __device__ constexpr int step_own_max(int r, int step) {
+  return step == 1 ? 32 - 2 * r : step_owned_lanes(r, step) * step + 2 * r + 1;
+}
+__host__ __device__ constexpr int step_acc_width(int r, int step) { return 32 * step + 2 * r + 2; }
 
 // Base of tile plane pl: estimate planes from `in` (then `in2`), the
 // guidance last.  `elem` is the element size of the estimate planes.
@@ -431,6 +450,41 @@ __device__ __forceinline__ void stage_tile(const PassArgs& a, const Tile& t, int
     stage_tile_mixed<CC>(a, t, ncol, p0, p1);
 }
 
+// Tiles of a runtime width (sliding step > 1): one warp per tile row (a
+// line for the column direction, an across-offset for the row direction),
+// lanes along the image's contiguous axis; plain loads, zero outside the
+// image.  Planes [p0, p1).
+template <int CC>
+__device__ __noinline__ void stage_tile_rt(const PassArgs& a, const Tile& t, int p0, int p1) {
+#pragma unroll 1
+  for (int pl = p0; pl < p1; ++pl) {
+    const int dt = pl < CC ? a.in_dt : a.g_dt;
+    const void* base = plane_base<CC>(a, pl, dt == DT_F32 ? 4 : 2);
+    float* dplane = t.p + pl * t.ntl * t.pitch;
+    if (a.dir == 0) {
+      for (int tl = threadIdx.y; tl < t.ntl; tl += blockDim.y) {
+        const int line = t.tl0 + tl;
+        const bool lok = line >= 0 && line < a.L;
+        for (int col = threadIdx.x; col < t.ncol; col += 32) {
+          const int off = t.off0 + col;
+          dplane[tl * t.pitch + col] =
+              (lok && off >= 0 && off < a.D) ? ld_px(base, (long long)line * a.W + off, dt) : 0.f;
+        }
+      }
+    } else {
+      for (int col = threadIdx.y; col < t.ncol; col += blockDim.y) {
+        const int off = t.off0 + col;
+        const bool ook = off >= 0 && off < a.D;
+        for (int tl = threadIdx.x; tl < t.ntl; tl += 32) {
+          const int line = t.tl0 + tl;
+          dplane[tl * t.pitch + col] =
+              (ook && line >= 0 && line < a.L) ? ld_px(base, (long long)off * a.W + line, dt) : 0.f;
+        }
+      }
+    }
+  }
+}
+
 // Column (relative to the lane's strip start) of entry j of a line.
 template <int R, bool ODD>
 __device__ __forceinline__ constexpr int ecol(int j) { return ODD ? 2 * R - j : j; }
@@ -726,8 +780,9 @@ __device__ __forceinline__ float* psi_lane(const PassArgs& a, int sys) {
 // With a.fac set it also keeps, per interior entry, the factor row, z0 and
 // Phi for k_backsub, and psi for the last r interior entries.
 template <int R, int CC, bool KEEP>
-__device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int lane, int sys, int c,
+__device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int col, int sys, int c,
                                               Strided out) {
+  const int lane = col;   // tile column of the lane's strip
   constexpr int n = 2 * R + 1;
   constexpr int NFAC = 2 * R + CC;
   constexpr bool LW = LineUnroll<R>::value > 1;   // a line's weights computed together
@@ -758,6 +813,7 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
     const bool end_ok = line + 1 < a.L;
     float wl[LW ? n : 1][R];
     if constexpr (LW) line_weights<R, ODD>(a, gr, gnr, end_ok, wl);
+    (void)wl;
 #pragma unroll LineUnroll<R>::value
     for (int j = 0; j < n; ++j) {
       float wf[R];
@@ -884,12 +940,16 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
 }
 
 // Tile geometry of a block of G chunks starting at chunk c0.
-__device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int off0, int r, float* p, Tile& t) {
+// ncol columns from off0; fixed: the 32 + 2r columns of step 1 (staged with
+// 4-element transfers when aligned), otherwise the runtime-width staging.
+__device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int off0, int ncol, bool fixed, float* p,
+                                           Tile& t) {
   t.tl0 = c0 * a.h - 1;
   t.ntl = min((c0 + G) * a.h, a.L) + 1 - t.tl0;
   t.off0 = off0;
-  t.cs = (a.dir == 0 && vec_staging(a)) ? (off0 & 3) : 0;
-  t.pitch = tile_pitch(r, a.dir);
+  t.cs = (fixed && a.dir == 0 && vec_staging(a)) ? (off0 & 3) : 0;
+  t.pitch = tile_pitch_n(ncol, a.dir);
+  t.ncol = ncol;
   t.p = p;
 }
 
@@ -1296,26 +1356,31 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   const int nch = min(G, a.P - c0);
   const int c = c0 + threadIdx.y;
 
+  // the band's strips start at its first subsystem's: offset 32 bx for step
+  // 1, that centre minus r in general
+  const bool unit = a.step == 1;
+  const int off0 = unit ? bx * 32 : centre_of(a, bx * 32, R) - R;
   Tile t;
-  group_tile(a, c0, G, bx * 32, R, smem, t);
+  group_tile(a, c0, G, off0, unit ? 32 + 2 * R : tile_ncol(R, a.step), unit, smem, t);
   float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
   // The guidance is an input of the whole filter (no kernel of the filter
   // writes it): its plane is staged before the wait, overlapping the
   // preceding kernel's tail; the estimate planes after it.
-  stage_tile<CC, 32 + 2 * R>(a, t, CC, CC + 1);
+  if (unit) stage_tile<CC, 32 + 2 * R>(a, t, CC, CC + 1); else stage_tile_rt<CC>(a, t, CC, CC + 1);
   griddep_wait();
   griddep_launch();
-  stage_tile<CC, 32 + 2 * R>(a, t, 0, CC);
+  if (unit) stage_tile<CC, 32 + 2 * R>(a, t, 0, CC); else stage_tile_rt<CC>(a, t, 0, CC);
   cp_async_wait_all();
   __syncthreads();
 
   const bool active = sys < a.nsys;
   if (active && threadIdx.y < nch) {
     const Strided out{csum + threadIdx.y * F::N * 32 + lane, 32};
+    const int col = unit ? lane : centre_of(a, sys, R) - R - off0;   // the lane's strip in the tile
     if (a.fac)
-      chunk_summary<R, CC, true>(a, t, lane, sys, c, out);
+      chunk_summary<R, CC, true>(a, t, col, sys, c, out);
     else
-      chunk_summary<R, CC, false>(a, t, lane, sys, c, out);
+      chunk_summary<R, CC, false>(a, t, col, sys, c, out);
   }
   __syncthreads();
   merge_tree<R, CC>(a, csum, lane, sys, grp, c0, nch, G, active);
@@ -1422,23 +1487,48 @@ __device__ __forceinline__ void group_ports(const PassArgs& a, int grp, int c0, 
 }
 
 // Row direction: writes the block's staged output lines ([NOUT][OB][lines],
-// pitch opitch) along the image rows.
+// pitch opitch; across-offsets o0 .. o0 + nown - 1, OB rows per channel)
+// along the image rows.
 template <int NOUT, int OB>
-__device__ __forceinline__ void flush_otile(const PassArgs& a, int bx, int c0, const float* otile, int opitch) {
+__device__ __forceinline__ void flush_otile(const PassArgs& a, int bx, int c0, const float* otile, int opitch,
+                                            int o0 = -1, int nown = OB) {
   const int G = blockDim.y;
   const int oline0 = c0 * a.h;
   const int nl = min((c0 + G) * a.h, a.L) - oline0;
+  if (o0 < 0) o0 = bx * OB;
   for (int row = threadIdx.y; row < NOUT * OB; row += G) {
     const int ch = row / OB;
     const int o = row - ch * OB;
-    const int oabs = bx * OB + o;
-    if (oabs >= a.D) continue;
+    const int oabs = o0 + o;
+    if (o >= nown || oabs >= a.D) continue;
     const float* src = otile + row * opitch;
     const long long gbase = ch * a.plane + (long long)oabs * a.W + oline0;
     float* const outw = reinterpret_cast<float*>(a.out);
     for (int l = threadIdx.x; l < nl; l += 32) {
       if (a.out_dt == DT_F32)
         outw[gbase + l] = src[l];
+      else
+        st_px(a.out, gbase + l, a.out_dt, src[l]);
+    }
+  }
+}
+
+// flush_otile with a runtime number of rows per channel (own), writing
+// across-offsets o0 .. o0 + nown - 1.
+template <int NOUT>
+__device__ __forceinline__ void flush_otile_n(const PassArgs& a, int c0, const float* otile, int opitch, int own,
+                                              int o0, int nown) {
+  const int G = blockDim.y;
+  const int oline0 = c0 * a.h;
+  const int nl = min((c0 + G) * a.h, a.L) - oline0;
+  for (int row = threadIdx.y; row < NOUT * nown; row += G) {
+    const int ch = row / nown;
+    const int o = row - ch * nown;
+    const float* src = otile + (ch * own + o) * opitch;
+    const long long gbase = ch * a.plane + (long long)(o0 + o) * a.W + oline0;
+    for (int l = threadIdx.x; l < nl; l += 32) {
+      if (a.out_dt == DT_F32)
+        reinterpret_cast<float*>(a.out)[gbase + l] = src[l];
       else
         st_px(a.out, gbase + l, a.out_dt, src[l]);
     }
@@ -1474,10 +1564,9 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
   const bool valid = sys_raw >= 0 && sys_raw < a.nsys;
   const int sys = min(max(sys_raw, 0), a.nsys - 1);
   const int mcap = a.h * n;
-  const long long ns = a.sstride;
 
   Tile t;
-  group_tile(a, c0, G, bx * OB - 2 * R, R, smem, t);
+  group_tile(a, c0, G, bx * OB - 2 * R, 32 + 2 * R, true, smem, t);
   float* ports = smem + (CC + 1) * t.ntl * t.pitch;   // [G][2][XS][32]
   float* mbuf = ports + G * 2 * XS * 32;               // [G-1][MF::N][32] merge factors + [2][XS][32]
   float* store = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [G][mcap][NF][32]
@@ -1634,6 +1723,7 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
     constexpr bool ODD = decltype(odd)::value;
     constexpr bool LAST = decltype(last)::value;
     float xl[XREG ? n : 1][CC];
+    (void)xl;
     float* lslot = st + (line - q.line0) * n * NF * 32;
 #pragma unroll LineUnroll<R>::value
     for (int j = n - 1; j >= 0; --j) {
@@ -1763,7 +1853,7 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
 // and averages each pixel's 2r+1 values across the neighbouring centres'
 // lanes.  No tile, no weights: the factors come from L2.  Grid (ceil(D / OB),
 // NG), block (32, G); lane = centre, warp = chunk.
-template <int R, int CC>
+template <int R, int CC, bool STEP>
 __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, float* smem) {
   constexpr int n = 2 * R + 1;
   constexpr int NFAC = 2 * R + CC;
@@ -1776,20 +1866,51 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
   const int c0 = grp * G;
   const int nch = min(G, a.P - c0);
   const int c = c0 + threadIdx.y;
-  const int kc = bx * OB - R + lane;  // this lane's centre
-  const int sys_raw = kc - R;
+  // step 1: lane = across-offset kc (the centre of subsystem kc - r when
+  // that exists), 2r halo lanes; step > 1: lane = subsystem, HL halo lanes
+  constexpr bool unit = !STEP;   // STEP: the launch's step is > 1
+  const int HL = step_halo(R, a.step);
+  const int SB = 32 - 2 * HL;
+  const int kc = bx * OB - R + lane;
+  const int sys_raw = unit ? kc - R : bx * SB - HL + lane;
   const bool valid = sys_raw >= 0 && sys_raw < a.nsys;
   const int sys = min(max(sys_raw, 0), a.nsys - 1);
-  const long long ss = a.sstride;
+  const int OWN = unit ? OB : step_own_max(R, a.step);   // otile rows per channel
 
   float* ports = smem;                                  // [G][2][XS][32]
   float* mbuf = ports + G * 2 * XS * 32;                // [G-1][MF::N][32] + [2][XS][32]
-  float* otile = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [CC][OB][opitch]
+  float* otile = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [CC][OWN][opitch]
+  const int opitch = (G * a.h) | 1;
+  // step > 1: per warp, CC accumulation rows and one of reciprocal counts
+  const int AW = step_acc_width(R, a.step);
+  float* const accw = otile + CC * OWN * opitch + threadIdx.y * (CC + 1) * AW;
+  float* const invw = accw + CC * AW;
+  // columns owned by this lane (step > 1): from its centre to the next
+  // (from 0 for the first subsystem, to D for the last)
+  const bool owner = !unit && valid && lane >= HL && lane < 32 - HL;
+  const int own_lo = (sys == 0) ? 0 : centre_of(a, sys, R);
+  const int own_hi = (sys == a.nsys - 1) ? a.D : centre_of(a, sys + 1, R);
+  const int wsys0 = bx * SB;   // first owned subsystem of the block
+  const int wlo = wsys0 == 0 ? 0 : centre_of(a, min(wsys0, a.nsys - 1), R);
+  const int whi = min(wsys0 + SB, a.nsys) == a.nsys ? a.D : centre_of(a, wsys0 + SB, R);
+  const int abase = centre_of(a, max(wsys0 - HL, 0), R) - R;   // offset of accw[0]
+  const int lcol = centre_of(a, sys, R) - R - abase;           // the lane's strip in accw
   griddep_wait();
   griddep_launch();
   group_ports<R, CC>(a, grp, c0, nch, sys, lane, ports, mbuf);
   const int oline0 = c0 * a.h;
-  const int opitch = (G * a.h) | 1;
+  if (!unit && threadIdx.y < nch) {  // (compile-time false for step 1)
+    // coverage counts of the warp's columns (every column has a centre
+    // within r), then their reciprocals in the owned columns
+    for (int i = lane; i < (CC + 1) * AW; i += 32) accw[i] = 0.f;
+    __syncwarp();
+    if (valid)
+      for (int e2 = 0; e2 < n; ++e2) atomicAdd(&invw[lcol + e2], 1.0f);
+    __syncwarp();
+    if (owner)
+      for (int o = own_lo; o < own_hi; ++o) invw[o - abase] = 1.0f / invw[o - abase];
+    __syncwarp();
+  }
 
   if (threadIdx.y < nch) {  // warp-uniform
     const Chunk q = make_chunk<R>(a, c);
@@ -1818,30 +1939,10 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
     const long long ostride = a.dir == 0 ? 1 : a.W;
     const long long lstride = a.dir == 0 ? a.W : 1;
     float* const outp = reinterpret_cast<float*>(a.out);
-    // r = 1: a line's factor rows (3 x (2 + CC) values) live in registers and
-    // the next line's are fetched while this one is solved
-    constexpr bool PF = false;
-    constexpr int PN = PF ? n : 1, PNF = PF ? NFAC : 1;
-    float cur[PN][PNF];
-    auto fetch = [&](int line, float (&dst)[PN][PNF], bool last_line) {
-      const float* fl = fac + line * n * NFAC * 32;
-#pragma unroll
-      for (int j = 0; j < PN; ++j) {
-        if (last_line && q.bot && j >= n - R) continue;
-#pragma unroll
-        for (int f = 0; f < PNF; ++f)
-          if (f < R + CC || q.top) dst[j][f] = __ldcg(fl + (j * NFAC + f) * 32);
-      }
-    };
-    if constexpr (PF) fetch(q.line1 - 1, cur, true);
     for_lines_rev(q.line0, q.line1, [&](auto odd, auto last, int line) {
       constexpr bool ODD = decltype(odd)::value;
       constexpr bool LAST = decltype(last)::value;
       float xl[n][CC];
-      float nxt[PN][PNF];
-      if constexpr (PF) {
-        if (line > q.line0) fetch(line - 1, nxt, false);
-      }
       const float* fl = fac + line * n * NFAC * 32;
 #pragma unroll LineUnroll<R>::value
       for (int j = n - 1; j >= 0; --j) {
@@ -1854,10 +1955,7 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
               for (int ch = 0; ch < CC; ++ch) x[ch] = xB[i][ch];
         } else {
           const float* fe = fl + j * NFAC * 32;
-          auto fv = [&](int f) -> float {
-            if constexpr (PF) return cur[j < PN ? j : 0][f < PNF ? f : 0];
-            else return __ldcg(fe + f * 32);
-          };
+          auto fv = [&](int f) -> float { return __ldcg(fe + f * 32); };
           float Lrow[R];
 #pragma unroll
           for (int tt = 0; tt < R; ++tt) Lrow[tt] = fv(tt);
@@ -1897,15 +1995,44 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
 #pragma unroll
         for (int ch = 0; ch < CC; ++ch) xl[j][ch] = x[ch];
       }
-      if constexpr (PF) {
-        if (line > q.line0) {
-#pragma unroll
-          for (int j = 0; j < PN; ++j)
-#pragma unroll
-            for (int f = 0; f < PNF; ++f) cur[j][f] = nxt[j][f];
-        }
-      }
+
       // inverse construction + averaging: value at across-offset kc - R + e
+      if constexpr (!unit) {
+        // step > 1: the strips of neighbouring lanes overlap irregularly;
+        // every valid lane adds its 2r+1 values into the warp's rows, the
+        // owners read their columns and scale by 1 / count
+        if (valid) {
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch)
+#pragma unroll
+            for (int e2 = 0; e2 < n; ++e2) atomicAdd(&accw[ch * AW + lcol + e2], xl[ecol<R, ODD>(e2)][ch]);
+        }
+        __syncwarp();
+        if (owner) {
+          for (int oo = own_lo; oo < own_hi; ++oo) {
+            const float ic = invw[oo - abase];
+#pragma unroll
+            for (int ch = 0; ch < CC; ++ch) {
+              const float v = accw[ch * AW + oo - abase] * ic;
+              if (a.dir != 0)
+                otile[(ch * OWN + (oo - wlo)) * opitch + (line - oline0)] = v;
+              else if (a.out_dt == DT_F32)
+                outp[(long long)line * lstride + oo + ch * a.plane] = v;
+              else
+                st_px(a.out, (long long)line * lstride + oo + ch * a.plane, a.out_dt, v);
+            }
+          }
+        }
+        __syncwarp();
+        if (valid) {
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch)
+#pragma unroll
+            for (int e2 = 0; e2 < n; ++e2) accw[ch * AW + lcol + e2] = 0.f;
+        }
+        __syncwarp();
+        return;
+      }
       const long long pix = (long long)line * lstride + (long long)o * ostride;
 #pragma unroll
       for (int ch = 0; ch < CC; ++ch) {
@@ -1931,14 +2058,17 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
   }
   if (a.dir != 0) {
     __syncthreads();
-    flush_otile<CC, OB>(a, bx, c0, otile, opitch);
+    if constexpr (unit)
+      flush_otile<CC, OB>(a, bx, c0, otile, opitch);
+    else
+      flush_otile_n<CC>(a, c0, otile, opitch, OWN, wlo, whi - wlo);
   }
 }
 
-template <int R, int CC>
+template <int R, int CC, bool STEP>
 __global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArgs a) {
   extern __shared__ float smem[];
-  body_backsub<R, CC>(a, blockIdx.x, blockIdx.y, smem);
+  body_backsub<R, CC, STEP>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 }  // namespace sgwls

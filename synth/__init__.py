@@ -117,3 +117,52 @@ def diff_batch(n: int = 16, H: int = 512, W: int = 512, seed: int = 5):
     f = np.stack([rgb_scene(H, W, seed=100 * seed + b) for b in range(n)])
     t = np.stack([rgb_scene(H, W, seed=1000 * seed + b) for b in range(n)])
     return f, t
+
+
+def sparse_depth(H: int, W: int, factor: int = 4, seed: int = 6, noise: float = 0.01):
+    """Guided-upsampling stand-in: a depth map of planar patches (a plane
+    a + b y + c x per rectangle, pasted in draw order over a background
+    plane), sampled on the regular grid of every ``factor``-th row and column
+    (the low-resolution depth projected onto the high-resolution grid), with
+    N(0, noise^2) noise.  Returns (F (1,H,W) float32, zero off the grid;
+    Hm (H,W) float32 index map; dense depth (1,H,W) float32)."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    y, x = yy / max(H - 1, 1), xx / max(W - 1, 1)
+
+    def plane():
+        a, b, c = rng.uniform(0.2, 0.8), rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3)
+        return a + b * y + c * x
+
+    depth = plane()
+    for _ in range(max(4, H * W // 4000)):
+        y0, y1 = np.sort(rng.integers(0, H + 1, size=2))
+        x0, x1 = np.sort(rng.integers(0, W + 1, size=2))
+        p = plane()
+        depth[y0:y1, x0:x1] = p[y0:y1, x0:x1]
+    depth = np.clip(depth, 0.0, 1.0)
+    Hm = np.zeros((H, W))
+    Hm[::factor, ::factor] = 1.0
+    F = (depth + rng.normal(0.0, noise, size=depth.shape)) * Hm
+    return F[None].astype(np.float32), Hm.astype(np.float32), depth[None].astype(np.float32)
+
+
+def scribbles(H: int, W: int, n: int = 12, C: int = 2, seed: int = 7):
+    """Colourisation stand-in: ``n`` random strokes (random walks of 3-pixel
+    wide dots) carrying per-stroke chrominance values U[-0.5, 0.5] in C
+    channels.  Returns (F (C,H,W) float32, zero off the strokes; Hm (H,W))."""
+    rng = np.random.default_rng(seed)
+    F = np.zeros((C, H, W))
+    Hm = np.zeros((H, W))
+    for _ in range(n):
+        val = rng.uniform(-0.5, 0.5, size=C)
+        py, px = rng.uniform(0, H), rng.uniform(0, W)
+        ang = rng.uniform(0, 2 * np.pi)
+        for _ in range(int(rng.integers(5, 40))):
+            ang += rng.normal(0.0, 0.4)
+            py = min(max(py + np.sin(ang), 0.0), H - 1.0)
+            px = min(max(px + np.cos(ang), 0.0), W - 1.0)
+            y0, x0 = int(py), int(px)
+            F[:, max(y0 - 1, 0):y0 + 2, max(x0 - 1, 0):x0 + 2] = val[:, None, None]
+            Hm[max(y0 - 1, 0):y0 + 2, max(x0 - 1, 0):x0 + 2] = 1.0
+    return F.astype(np.float32), Hm.astype(np.float32)

@@ -97,3 +97,28 @@ def test_validation_before_any_launch(capi):
     assert _call(capi, nws=16) == E_WS
     assert _call(capi, ws=0x10010) == E_WS                # misaligned
     assert _call(capi, p=capi.make_params(r=1, refine=1)) == E_UNSUP
+
+
+def test_interpolate_validation_host_only(capi):
+    """sgwls_interpolate rejects bad arguments before any launch."""
+    lib = capi.lib()
+    E_INVALID, E_SHAPE, E_WS, E_UNSUP = -1, -2, -4, -7
+
+    def call(C=1, p=None, f=0x1000, h=0x2000, g=0x3000, u=0x4000, ws=0x10000, nws=1 << 30, lam=1.0):
+        p = p if p is not None else capi.make_params()
+        return lib.sgwls_interpolate(ctypes.c_void_p(f), ctypes.c_void_p(h), ctypes.c_void_p(g),
+                                     ctypes.c_void_p(u), 64, 64, C, ctypes.c_float(lam), ctypes.byref(p),
+                                     ctypes.c_void_p(ws), nws, ctypes.c_void_p(0))
+
+    p = capi.make_params(r=2, iters=2)
+    need = lib.sgwls_interpolate_workspace_bytes(64, 64, 3, ctypes.byref(p))
+    assert need >= lib.sgwls_workspace_bytes(64, 64, 4, ctypes.byref(p)) + 2 * 4 * 64 * 64 * 4
+    assert lib.sgwls_interpolate_workspace_bytes(64, 64, 0, ctypes.byref(p)) == 0
+    assert call(C=0) == E_SHAPE
+    assert call(f=0) == E_INVALID
+    assert call(h=0) == E_INVALID
+    assert call(u=0x1000) == E_INVALID           # u aliases f
+    assert call(u=0x2000) == E_INVALID           # u aliases the index map
+    assert call(lam=-1.0) == E_INVALID
+    assert call(nws=16) == E_WS
+    assert call(p=capi.make_params(storage="bf16")) == E_UNSUP
