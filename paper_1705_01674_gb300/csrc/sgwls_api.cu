@@ -75,7 +75,12 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   };
   auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G, step)); };
   int h;
-  if (keep) {
+  if (keep && step > 1) {
+    // sliding step: fewer subsystems, so fewer warps; shorter chunks would
+    // only add merge work (8 lines measured best or near best on GB300 for
+    // r = 2..5, tau = 2..2r+1 on a 1-megapixel RGB image)
+    h = 8;
+  } else if (keep) {
     h = keep_lines(r);
     while (h > 1 && (long long)L * bands / h < kTargetWarps) --h;
   } else {
