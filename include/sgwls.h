@@ -69,8 +69,16 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *               this build runs step = 1, other values return
  *               SGWLS_E_UNSUPPORTED
  *   axis_order  0: column direction first (Sec. 2.3), 1: row direction first
- *   refine      iterative refinement of each subsystem solve; this build
- *               runs refine = 0 (other values return SGWLS_E_UNSUPPORTED)
+ *   refine      0 or 1: one step of iterative refinement of every
+ *               subsystem solve: u1 = A~^-1 f in FP32, the residual
+ *               f - A u1 with A rebuilt from the guidance in FP64, the
+ *               FP32 solve of the residual added to u1, then the averaging
+ *               (five kernels per pass instead of two).  For ill-conditioned
+ *               settings (frac weights, large lambda: the FP32 weights
+ *               alone move the exact solution by ~1e-3).  Needs step = 1 and
+ *               kept factors (not factor_cache = 2); the batched,
+ *               backward and no-allocation entry points return
+ *               SGWLS_E_UNSUPPORTED for refine = 1
  *   storage     sgwls_dtype of f, g and u
  *   inter_storage  sgwls_dtype of the estimates between passes
  *   chunk_lines 0: automatic; otherwise the number of lines per chunk of

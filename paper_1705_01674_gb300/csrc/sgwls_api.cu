@@ -92,8 +92,6 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   if (chunk_lines > 0) h = std::min(chunk_lines, L);
   while (h > 1 && block(h, 1) > kSmemBlockMax) --h;
   h = std::min(h, L);
-  // the sliding-step path keeps factors, which needs at least two chunks
-  if (step > 1 && h >= L && L >= 2) h = (L + 1) / 2;
   Plan pl;
   pl.h = h;
   pl.P = (L + h - 1) / h;
@@ -119,6 +117,7 @@ struct Layout {
   size_t cnt_off, cnt_bytes;   // per-band block counters of k_summary
   size_t fac_off, fac_bytes;   // chunk factors kept between the kernels of a pass
   size_t psi_off, psi_bytes;
+  size_t rhs_off, xent_off, ent_bytes;   // refinement: residual and first-solve entries
   size_t total;
 };
 
@@ -132,9 +131,13 @@ size_t psi_bytes(int P, int r, int sstride) { return (size_t)P * r * r * sstride
 // Plan of one forward pass; *keep: its chunk factors are kept between the
 // two kernels (needs at least two chunks).
 Plan fwd_plan(const sgwls_params* p, int L, int D, int CC, int sstride, bool* keep) {
-  bool k = p->factor_cache == 1 || (p->factor_cache == 0 && fac_bytes(L, p->r, CC, sstride) <= kFactorCacheBytes);
-  if (p->step > 1) k = true;   // the sliding-step path runs on kept factors only
+  // the sliding step and the refinement run on kept factors only
+  const bool need = p->step > 1 || p->refine;
+  bool k = need || p->factor_cache == 1 ||
+           (p->factor_cache == 0 && fac_bytes(L, p->r, CC, sstride) <= kFactorCacheBytes);
   Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k, p->step);
+  // keeping factors needs at least two chunks
+  if (k && need && pl.P < 2 && L >= 2) pl = make_plan(L, D, p->r, CC, (L + 1) / 2, false, true, p->step);
   if (k && pl.P < 2) {
     k = false;
     pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, false);
@@ -152,7 +155,7 @@ size_t counter_bytes(int H, int W, int r) {
 Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   Layout lo;
   const int r = p->r;
-  size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0;
+  size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0, ent = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
@@ -167,6 +170,7 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
       if (keep) {
         fac = std::max(fac, fac_bytes(L, r, CC, nsys));
         psi = std::max(psi, psi_bytes(pl.P, r, nsys));
+        if (p->refine) ent = std::max(ent, (size_t)L * (2 * r + 1) * CC * nsys * sizeof(float));
       }
     }
   }
@@ -189,7 +193,10 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   lo.fac_bytes = align256(fac);
   lo.psi_off = lo.fac_off + lo.fac_bytes;
   lo.psi_bytes = align256(psi);
-  lo.total = lo.psi_off + lo.psi_bytes;
+  lo.ent_bytes = align256(ent);
+  lo.rhs_off = lo.psi_off + lo.psi_bytes;
+  lo.xent_off = lo.rhs_off + lo.ent_bytes;
+  lo.total = lo.xent_off + lo.ent_bytes;
   return lo;
 }
 
@@ -204,7 +211,7 @@ sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
   if (!isfinite(p->sigma_s) || !isfinite(p->sigma_r) || !isfinite(p->alpha_s) || !isfinite(p->alpha_r) ||
       !isfinite(p->eps))
     return SGWLS_E_INVALID;
-  if (p->refine != 0) return SGWLS_E_UNSUPPORTED;
+  if (p->refine < 0 || p->refine > 1) return SGWLS_E_INVALID;
   if (p->chunk_lines < 0) return SGWLS_E_INVALID;
   if (p->factor_cache < 0 || p->factor_cache > 2) return SGWLS_E_INVALID;
   if ((p->storage != SGWLS_F32 && p->storage != SGWLS_BF16) ||
@@ -220,7 +227,9 @@ sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
 // needs them kept in every pass (not factor_cache = 2, not beyond the
 // factor-store budget, at least two lines per subsystem).
 sgwls_status check_step(int H, int W, int C, const sgwls_params* p) {
-  if (p->step == 1) return SGWLS_OK;
+  // refinement (refine = 1) reuses the keep path at step 1
+  if (p->refine && p->step != 1) return SGWLS_E_UNSUPPORTED;
+  if (p->step == 1 && !p->refine) return SGWLS_OK;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
@@ -249,6 +258,8 @@ void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
   }
   a.eps = p->eps;
   a.dgk = (float)(1.0 / ((double)p->sigma_r * (double)p->sigma_r));
+  a.range64 = p->weight == SGWLS_W_EXP ? 1.0 / (2.0 * (double)p->sigma_r * (double)p->sigma_r) : (double)p->alpha_r;
+  a.eps64 = (double)p->eps;
   // Spatial factor of the pair (p, p+t) with j = p % n: same line -> distance
   // t; next line -> one line over and |4r + 1 - 2j - t| across (the snake
   // turns), for both directions.
@@ -269,6 +280,7 @@ void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
       }
       a.sp[j * r + t - 1] = (float)(lambda * sp);
       a.sp0[j * r + t - 1] = (float)sp;
+      a.sp64[j * r + t - 1] = (double)lambda * sp;
     }
   }
 }
@@ -371,9 +383,13 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.out = static_cast<char*>(out) + (size_t)c0 * plane * dt_size(out_dt);
     a.fac = keep ? reinterpret_cast<float*>(wsb + lo.fac_off) : nullptr;
     a.psi = keep ? reinterpret_cast<float*>(wsb + lo.psi_off) : nullptr;
+    a.refine = (keep && p->refine) ? 1 : 0;
+    a.rhs = a.refine ? reinterpret_cast<float*>(wsb + lo.rhs_off) : nullptr;
+    a.xent = a.refine ? reinterpret_cast<float*>(wsb + lo.xent_off) : nullptr;
+    a.xmode = 0;
     cudaError_t e = launch_pass_any(p->r, CC, a, pl, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 2 : 1), __ATOMIC_RELAXED);
+    __atomic_add_fetch(&g_launches, (unsigned long long)(a.refine ? 5 : (pl.P > 1 ? 2 : 1)), __ATOMIC_RELAXED);
   }
   return SGWLS_OK;
 }
@@ -525,7 +541,7 @@ struct BatchImgLayout {
 BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_params* p, bool keep) {
   const int r = p->r;
   const int h0 = batch_h(r, C, keep);
-  size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0;
+  size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0, ent = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
@@ -554,7 +570,7 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
 
 sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) {
   if (B < 1 || !imgs || !p) return SGWLS_E_INVALID;
-  if (p->step != 1) return SGWLS_E_UNSUPPORTED;   // the sliding step runs on single images
+  if (p->step != 1 || p->refine) return SGWLS_E_UNSUPPORTED;   // sliding step, refinement: single images
   const int C = imgs[0].C;
   if (C < 1 || C > kGroupMax) return C < 1 ? SGWLS_E_SHAPE : SGWLS_E_UNSUPPORTED;
   for (int i = 0; i < B; ++i) {
@@ -836,7 +852,7 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
       a.out = dst + (size_t)c0 * plane;
       e = launch_pass_any(p->r, -2 * nch, a, pl, st);
       if (e != cudaSuccess) return cuda_fail(e);
-      __atomic_add_fetch(&g_launches, (unsigned long long)(pl.P > 1 ? 2 : 1), __ATOMIC_RELAXED);
+      __atomic_add_fetch(&g_launches, (unsigned long long)(a.refine ? 5 : (pl.P > 1 ? 2 : 1)), __ATOMIC_RELAXED);
     }
     vbar = dst;
   }
@@ -957,7 +973,7 @@ sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void
   if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
   if (p->storage != SGWLS_F32 || p->inter_storage != SGWLS_F32) return SGWLS_E_UNSUPPORTED;
   if (p->weight == SGWLS_W_FRAC && p->alpha_r < 1.f) return SGWLS_E_UNSUPPORTED;
-  if (p->step != 1) return SGWLS_E_UNSUPPORTED;
+  if (p->step != 1 || p->refine) return SGWLS_E_UNSUPPORTED;
   const size_t need = make_bwd_layout(H, W, C, p).total;
   if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
   return run_backward(static_cast<const float*>(grad_u), static_cast<const float*>(g),

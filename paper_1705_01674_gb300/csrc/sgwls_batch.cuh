@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) k_backsub_b(const __grid_constant__ Batch
   const int local = blockIdx.x - ba.img[i].b0[2];
   const int by = local / ba.img[i].nbx[2];
   build_args(ba, i, sa);
-  body_backsub<R, CC, false>(sa, local - by * ba.img[i].nbx[2], by, smem);
+  body_backsub<R, CC, 0>(sa, local - by * ba.img[i].nbx[2], by, smem);
 }
 
 }  // namespace sgwls

@@ -65,6 +65,19 @@ struct PassArgs {
   // (the only rows where it is not zero).
   float* fac;
   float* psi;
+  // Refinement of each subsystem solve (refine = 1): first solve with
+  // xmode 1 (every entry's solution to xent, no averaging); k_resid forms
+  // rho = f - A u with A in FP64 into rhs; second solve with rhs as the
+  // right-hand side and xmode 2 (xent added before the averaging).  Both
+  // buffers are [band][e][CC][32] (e = vector entry, 32 subsystems a band).
+  float* rhs;
+  float* xent;
+  int xmode;
+  int refine;          // host: this pass runs the two solves and the residual
+  // FP64 weight constants for the residual: lambda * spatial factor
+  // (sp64[j * r + t - 1]), exp: 1 / (2 sigma_r^2), frac: alpha_r and eps
+  double sp64[(2 * kRMax + 1) * kRMax];
+  double range64, eps64;
   // Planes 0 .. n_in1-1 come from `in`, planes n_in1 .. CC-1 from `in2`
   // (the backward solves u = A^-1 f and v = A^-1 ubar together).
   const void* in2;

@@ -67,15 +67,43 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // later launches (for example inside a CUDA-graph capture) make no call.
 cudaError_t set_smem_raw(const void* kernel, size_t bytes);
 
+// (The default limit of 48 KB covers static and dynamic shared memory
+// together: the batched kernels hold their argument block in static shared
+// memory, so the attribute is raised from 32 KB of dynamic memory on.)
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes <= 32 * 1024) return cudaSuccess;
   return set_smem_raw(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 template <int R, int CC, bool BWD = false>
+cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st);
+
+// Refined pass (refine = 1): first solve keeping every entry's solution,
+// the FP64 residual, the solve of the residual (same factors recomputed
+// from the same tile) adding the first solution, then the averaging.
+template <int R, int CC>
+cudaError_t launch_refined_pass(const PassArgs& a, const Plan& pl, cudaStream_t st) {
+  cudaError_t e;
+  PassArgs b = a;
+  b.refine = 0;
+  b.xmode = 1;
+  b.rhs = nullptr;
+  if ((e = launch_pass_rc<R, CC>(b, pl, st)) != cudaSuccess) return e;
+  b.rhs = a.rhs;
+  const int gy = pl.G;
+  e = launch_pdl(k_resid<R, CC>, dim3((a.nsys + 31) / 32, (a.L + 8 * gy - 1) / (8 * gy)), dim3(32, gy), 0, st, b);
+  if (e != cudaSuccess) return e;
+  b.xmode = 2;
+  return launch_pass_rc<R, CC>(b, pl, st);
+}
+
+template <int R, int CC, bool BWD>
 cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   static_assert(R >= 1 && R <= kRMax, "radius");
+  if constexpr (!BWD) {
+    if (a.refine) return launch_refined_pass<R, CC>(a, pl, st);
+  }
   constexpr int OB = 32 - 2 * R;
   cudaError_t e;
   PassArgs b = a;
@@ -94,7 +122,7 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
       const size_t smem = smem_backsub(R, CC, a.h, pl.G, a.step);
       const int nbx = a.step == 1 ? (a.D + OB - 1) / OB : (a.nsys + step_owned_lanes(R, a.step) - 1) /
                                                               step_owned_lanes(R, a.step);
-      auto kern = a.step == 1 ? k_backsub<R, CC, false> : k_backsub<R, CC, true>;
+      auto kern = a.step != 1 ? k_backsub<R, CC, 1> : (b.xmode != 0 ? k_backsub<R, CC, 2> : k_backsub<R, CC, 0>);
       if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
       e = launch_pdl(kern, dim3(nbx, pl.NG), dim3(32, pl.G), smem, st, b);
       if (e != cudaSuccess) return e;

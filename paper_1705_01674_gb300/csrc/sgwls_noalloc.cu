@@ -53,6 +53,7 @@ extern "C" sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, 
   if (!p) return SGWLS_E_INVALID;
   // the sliding step tau > 1 runs on kept chunk factors, which this scratch does not hold
   if (p->step != 1) return (p->step >= 1 && p->step <= 2 * p->r + 1) ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;
+  if (p->refine) return p->refine == 1 ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;   // needs kept factors
   // a pass needs no intermediate image: size the scratch as for iters == 0
   sgwls_params q = *p;
   q.iters = 0;

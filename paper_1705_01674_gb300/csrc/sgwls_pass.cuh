@@ -772,6 +772,12 @@ __device__ __forceinline__ float* fac_lane(const PassArgs& a, int sys) {
   const size_t band = (size_t)a.L * (2 * R + 1) * (2 * R + CC) * 32;
   return a.fac + (size_t)(sys >> 5) * band + (sys & 31);
 }
+// Per-entry buffers of the refinement (rhs, xent): [band][e][CC][32].
+template <int R, int CC>
+__device__ __forceinline__ float* ent_lane(const PassArgs& a, float* buf, int sys) {
+  const size_t band = (size_t)a.L * (2 * R + 1) * CC * 32;
+  return buf + (size_t)(sys >> 5) * band + (sys & 31);
+}
 template <int R>
 __device__ __forceinline__ float* psi_lane(const PassArgs& a, int sys) {
   const size_t band = (size_t)a.P * R * R * 32;
@@ -779,7 +785,7 @@ __device__ __forceinline__ float* psi_lane(const PassArgs& a, int sys) {
 }
 // With a.fac set it also keeps, per interior entry, the factor row, z0 and
 // Phi for k_backsub, and psi for the last r interior entries.
-template <int R, int CC, bool KEEP>
+template <int R, int CC, bool KEEP, bool RHSB = false>
 __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int col, int sys, int c,
                                               Strided out) {
   const int lane = col;   // tile column of the lane's strip
@@ -790,6 +796,9 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
   const Chunk q = make_chunk<R>(a, c);
   const int pstride = t.ntl * t.pitch;
   float* const fac = KEEP ? fac_lane<R, CC>(a, sys) : nullptr;
+  // RHSB: the right-hand side of every entry comes from a.rhs (the
+  // refinement's residual) instead of the estimate planes of the tile
+  const float* const rhs = RHSB ? ent_lane<R, CC>(a, a.rhs, sys) : nullptr;
 
   float wh[R][R] = {};
   float Lw[R][R] = {};
@@ -828,7 +837,12 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
       for (int tt = 0; tt < R; ++tt) diag += wf[tt] + wh[tt][tt];
       float fj[CC];
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) fj[ch] = fr[ch * pstride + ecol<R, ODD>(j)];
+      for (int ch = 0; ch < CC; ++ch) {
+        if constexpr (RHSB)
+          fj[ch] = __ldcg(rhs + ((line * n + j) * CC + ch) * 32);
+        else
+          fj[ch] = fr[ch * pstride + ecol<R, ODD>(j)];
+      }
       const bool sep = LAST && q.bot && j >= n - R;
       if (!sep) {
         const int lim = FIRST ? min(j, R) : R;
@@ -1377,7 +1391,9 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   if (active && threadIdx.y < nch) {
     const Strided out{csum + threadIdx.y * F::N * 32 + lane, 32};
     const int col = unit ? lane : centre_of(a, sys, R) - R - off0;   // the lane's strip in the tile
-    if (a.fac)
+    if (a.fac && a.rhs)
+      chunk_summary<R, CC, true, true>(a, t, col, sys, c, out);
+    else if (a.fac)
       chunk_summary<R, CC, true>(a, t, col, sys, c, out);
     else
       chunk_summary<R, CC, false>(a, t, col, sys, c, out);
@@ -1853,7 +1869,9 @@ __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArg
 // and averages each pixel's 2r+1 values across the neighbouring centres'
 // lanes.  No tile, no weights: the factors come from L2.  Grid (ceil(D / OB),
 // NG), block (32, G); lane = centre, warp = chunk.
-template <int R, int CC, bool STEP>
+// MODE 0: step 1; 1: step > 1; 2: step 1 with the refinement's entry
+// buffers (xmode).
+template <int R, int CC, int MODE>
 __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, float* smem) {
   constexpr int n = 2 * R + 1;
   constexpr int NFAC = 2 * R + CC;
@@ -1868,7 +1886,7 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
   const int c = c0 + threadIdx.y;
   // step 1: lane = across-offset kc (the centre of subsystem kc - r when
   // that exists), 2r halo lanes; step > 1: lane = subsystem, HL halo lanes
-  constexpr bool unit = !STEP;   // STEP: the launch's step is > 1
+  constexpr bool unit = MODE != 1;   // MODE 1: the launch's step is > 1
   const int HL = step_halo(R, a.step);
   const int SB = 32 - 2 * HL;
   const int kc = bx * OB - R + lane;
@@ -1996,6 +2014,24 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
         for (int ch = 0; ch < CC; ++ch) xl[j][ch] = x[ch];
       }
 
+      // refinement: xmode 1 keeps every entry's solution (no averaging),
+      // xmode 2 adds the kept first solution to this correction
+      if (MODE == 2 && a.xmode != 0) {
+        float* const xe = ent_lane<R, CC>(a, a.xent, sys) + line * n * CC * 32;
+        if (a.xmode == 1) {
+          if (valid) {
+#pragma unroll LineUnroll<R>::value
+            for (int j = 0; j < n; ++j)
+#pragma unroll
+              for (int ch = 0; ch < CC; ++ch) xe[(j * CC + ch) * 32] = xl[j][ch];
+          }
+          return;
+        }
+#pragma unroll LineUnroll<R>::value
+        for (int j = 0; j < n; ++j)
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch) xl[j][ch] += __ldcg(xe + (j * CC + ch) * 32);
+      }
       // inverse construction + averaging: value at across-offset kc - R + e
       if constexpr (!unit) {
         // step > 1: the strips of neighbouring lanes overlap irregularly;
@@ -2056,7 +2092,7 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
       }
     });
   }
-  if (a.dir != 0) {
+  if (a.dir != 0 && !(MODE == 2 && a.xmode == 1)) {
     __syncthreads();
     if constexpr (unit)
       flush_otile<CC, OB>(a, bx, c0, otile, opitch);
@@ -2065,10 +2101,72 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
   }
 }
 
-template <int R, int CC, bool STEP>
+template <int R, int CC, int MODE>
 __global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArgs a) {
   extern __shared__ float smem[];
-  body_backsub<R, CC, STEP>(a, blockIdx.x, blockIdx.y, smem);
+  body_backsub<R, CC, MODE>(a, blockIdx.x, blockIdx.y, smem);
+}
+
+// ---------------------------------------------------------------------------
+// k_resid: the refinement's residual rho = f - A u for every entry of every
+// subsystem, with A rebuilt from the guidance in FP64 (Eq. 2, Eq. 4, Eq. 5)
+// and u the first solve's entries (xent).  A's row of entry e: diagonal
+// 1 + sum lambda w, off-diagonals -lambda w to the entries within r along
+// the vector.  Grid (ceil(nsys / 32), ceil(L / (8 lines x blockDim.y))),
+// block (32, G); lane = subsystem, each warp 8 lines.
+template <int R>
+__device__ __forceinline__ double weight64(const PassArgs& a, int jp, int t, double gp, double gq) {
+  const double dg = gp - gq;
+  const double rf = a.weight == 0 ? exp(-dg * dg * a.range64) : 1.0 / (pow(fabs(dg), a.range64) + a.eps64);
+  return a.sp64[jp * R + t - 1] * rf;   // lambda * w(p, p + t)
+}
+
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs a) {
+  constexpr int n = 2 * R + 1;
+  constexpr int LPW = 8;   // lines per warp
+  const int lane = threadIdx.x;
+  const int sys = blockIdx.x * 32 + lane;
+  const int l0 = (blockIdx.y * blockDim.y + threadIdx.y) * LPW;
+  griddep_wait();
+  griddep_launch();
+  if (sys >= a.nsys || l0 >= a.L) return;
+  const int kc = centre_of(a, sys, R);
+  const long long s_len = (long long)a.L * n;
+  const float* const xe = ent_lane<R, CC>(a, a.xent, sys);
+  float* const re = ent_lane<R, CC>(a, a.rhs, sys);
+  // pixel of entry e (line e / n, snake order within the line)
+  auto pix = [&](long long e) {
+    const int line = (int)(e / n), j = (int)(e - (long long)line * n);
+    const int off = kc - R + ((line & 1) ? 2 * R - j : j);
+    return pix_index(a, line, off);
+  };
+  const int l1 = min(l0 + LPW, a.L);
+  for (long long e = (long long)l0 * n; e < (long long)l1 * n; ++e) {
+    const long long pe = pix(e);
+    const double ge = (double)ld_px(a.g, pe, a.g_dt);
+    const int je = (int)(e % n);
+    double xv[CC], acc[CC];
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) {
+      xv[ch] = (double)__ldcg(xe + (e * CC + ch) * 32);
+      acc[ch] = (double)ld_px(plane_base<CC>(a, ch, a.in_dt == DT_F32 ? 4 : 2), pe, a.in_dt) - xv[ch];
+    }
+    for (int t = 1; t <= R; ++t) {
+      if (e + t < s_len) {   // pair (e, e + t)
+        const double w = weight64<R>(a, je, t, ge, (double)ld_px(a.g, pix(e + t), a.g_dt));
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + ((e + t) * CC + ch) * 32));
+      }
+      if (e - t >= 0) {      // pair (e - t, e)
+        const double w = weight64<R>(a, (int)((e - t) % n), t, (double)ld_px(a.g, pix(e - t), a.g_dt), ge);
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + ((e - t) * CC + ch) * 32));
+      }
+    }
+#pragma unroll
+    for (int ch = 0; ch < CC; ++ch) re[(e * CC + ch) * 32] = (float)acc[ch];
+  }
 }
 
 }  // namespace sgwls

@@ -96,7 +96,8 @@ def test_validation_before_any_launch(capi):
     assert _call(capi, ws=0) == E_WS
     assert _call(capi, nws=16) == E_WS
     assert _call(capi, ws=0x10010) == E_WS                # misaligned
-    assert _call(capi, p=capi.make_params(r=1, refine=1)) == E_UNSUP
+    assert _call(capi, p=capi.make_params(r=1, refine=2)) == E_INVALID
+    assert _call(capi, p=capi.make_params(r=2, refine=1, step=2)) == E_UNSUP
 
 
 def test_interpolate_validation_host_only(capi):
