@@ -545,6 +545,21 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
             sweep[f"r{r}_tau{tau}"] = _timed(one, 3, 1, flush, stream) / 3
             del ws3
     out["step_sweep"] = {"workload": "1024x1024 RGB, T=3, lambda=1: ms per filter by (r, tau)", "ms": sweep}
+    del f3, g3, u3
+
+    # refinement (row a9) at the paper's detail-enhancement setting (frac
+    # weights, alpha = 1.2, lambda = 900): the main workload's image, T = 2
+    fr_ = torch.from_numpy(F2).to(dev)
+    gr_ = torch.from_numpy(G2).to(dev)
+    ur_ = torch.empty_like(fr_)
+    kwr = dict(r=1, iters=2, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+    ms_r = {}
+    for refine in (0, 1):
+        def rf(i, refine=refine):
+            sg.sgwls_filter(fr_, gr_, 900.0, out=ur_, stream=stream, refine=refine, **kwr)
+        ms_r[f"refine{refine}"] = _timed(rf, steps, warmup, flush, stream) / steps
+    out["refine"] = {"workload": WL["name"][:-3] + "_T2 with frac weights, lambda=900: ms per filter",
+                     "ms": ms_r}
     return out
 
 

@@ -92,7 +92,7 @@ cudaError_t launch_refined_pass(const PassArgs& a, const Plan& pl, cudaStream_t 
   if ((e = launch_pass_rc<R, CC>(b, pl, st)) != cudaSuccess) return e;
   b.rhs = a.rhs;
   const int gy = pl.G;
-  e = launch_pdl(k_resid<R, CC>, dim3((a.nsys + 31) / 32, (a.L + 8 * gy - 1) / (8 * gy)), dim3(32, gy), 0, st, b);
+  e = launch_pdl(k_resid<R, CC>, dim3((a.nsys + 31) / 32, (a.L + 4 * gy - 1) / (4 * gy)), dim3(32, gy), 0, st, b);
   if (e != cudaSuccess) return e;
   b.xmode = 2;
   return launch_pass_rc<R, CC>(b, pl, st);

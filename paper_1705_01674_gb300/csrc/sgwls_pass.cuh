@@ -2112,8 +2112,8 @@ __global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArg
 // subsystem, with A rebuilt from the guidance in FP64 (Eq. 2, Eq. 4, Eq. 5)
 // and u the first solve's entries (xent).  A's row of entry e: diagonal
 // 1 + sum lambda w, off-diagonals -lambda w to the entries within r along
-// the vector.  Grid (ceil(nsys / 32), ceil(L / (8 lines x blockDim.y))),
-// block (32, G); lane = subsystem, each warp 8 lines.
+// the vector.  Grid (ceil(nsys / 32), ceil(L / (4 lines x blockDim.y))),
+// block (32, G); lane = subsystem, each warp 4 lines.
 template <int R>
 __device__ __forceinline__ double weight64(const PassArgs& a, int jp, int t, double gp, double gq) {
   const double dg = gp - gq;
@@ -2124,7 +2124,7 @@ __device__ __forceinline__ double weight64(const PassArgs& a, int jp, int t, dou
 template <int R, int CC>
 __global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs a) {
   constexpr int n = 2 * R + 1;
-  constexpr int LPW = 8;   // lines per warp
+  constexpr int LPW = 4;   // lines per warp
   const int lane = threadIdx.x;
   const int sys = blockIdx.x * 32 + lane;
   const int l0 = (blockIdx.y * blockDim.y + threadIdx.y) * LPW;
@@ -2142,7 +2142,19 @@ __global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs 
     return pix_index(a, line, off);
   };
   const int l1 = min(l0 + LPW, a.L);
-  for (long long e = (long long)l0 * n; e < (long long)l1 * n; ++e) {
+  // each pair weight is computed once: wh[u][t-1] = lambda w(e-1-u, e-1-u+t)
+  // holds the forward weights of the previous r entries
+  double wh[R][R];
+  const long long e0 = (long long)l0 * n;
+  for (int u = 0; u < R; ++u)
+    for (int t = 1; t <= R; ++t) {
+      const long long p = e0 - 1 - u;
+      wh[u][t - 1] = (p >= 0 && p + t < s_len)
+                         ? weight64<R>(a, (int)(p % n), t, (double)ld_px(a.g, pix(p), a.g_dt),
+                                       (double)ld_px(a.g, pix(p + t), a.g_dt))
+                         : 0.0;
+    }
+  for (long long e = e0; e < (long long)l1 * n; ++e) {
     const long long pe = pix(e);
     const double ge = (double)ld_px(a.g, pe, a.g_dt);
     const int je = (int)(e % n);
@@ -2152,18 +2164,28 @@ __global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs 
       xv[ch] = (double)__ldcg(xe + (e * CC + ch) * 32);
       acc[ch] = (double)ld_px(plane_base<CC>(a, ch, a.in_dt == DT_F32 ? 4 : 2), pe, a.in_dt) - xv[ch];
     }
+    double wf[R];
+#pragma unroll
     for (int t = 1; t <= R; ++t) {
+      wf[t - 1] = 0.0;
       if (e + t < s_len) {   // pair (e, e + t)
         const double w = weight64<R>(a, je, t, ge, (double)ld_px(a.g, pix(e + t), a.g_dt));
+        wf[t - 1] = w;
 #pragma unroll
         for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + ((e + t) * CC + ch) * 32));
       }
-      if (e - t >= 0) {      // pair (e - t, e)
-        const double w = weight64<R>(a, (int)((e - t) % n), t, (double)ld_px(a.g, pix(e - t), a.g_dt), ge);
+      if (e - t >= 0) {      // pair (e - t, e): entry e - t's forward weight at distance t
+        const double w = wh[t - 1][t - 1];
 #pragma unroll
         for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + ((e - t) * CC + ch) * 32));
       }
     }
+#pragma unroll
+    for (int u = R - 1; u > 0; --u)
+#pragma unroll
+      for (int t = 0; t < R; ++t) wh[u][t] = wh[u - 1][t];
+#pragma unroll
+    for (int t = 0; t < R; ++t) wh[0][t] = wf[t];
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) re[(e * CC + ch) * 32] = (float)acc[ch];
   }

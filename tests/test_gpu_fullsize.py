@@ -55,3 +55,24 @@ def test_fullsize_pass_sampled(api, scene, r, direction):
     got = U[:, :, offsets].transpose(0, 2, 1) if direction == COLUMN else U[:, offsets, :]
     err = float(np.abs(got - ref).max())
     assert err <= TOL, err
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_large_image_pass_sampled(api, direction):
+    """A 4096 x 6144 grayscale image (25 MP, the factor store 0.3 GB per
+    pass): one pass, sampled offsets against the oracle."""
+    import torch
+    from synth import rect_gray
+    F = rect_gray(4096, 6144, seed=12, n_rect=400)
+    G = F[0]
+    f = torch.from_numpy(F).cuda()
+    u = api.sgwls_filter_pass(f, f[0], 2.0, direction, r=1, sigma_r=0.1)
+    torch.cuda.synchronize()
+    C, H, W = F.shape
+    dim = W if direction == COLUMN else H
+    offsets = [0, 1, 2, 777, dim // 2 + 13, dim - 2, dim - 1]
+    ref = oracle_pass_offsets(F, G, 2.0, Params(r=1, iters=1, sigma_s=1.0, sigma_r=0.1), direction, offsets)
+    U = u.cpu().numpy().astype(np.float64)
+    got = U[:, :, offsets].transpose(0, 2, 1) if direction == COLUMN else U[:, offsets, :]
+    err = float(np.abs(got - ref).max())
+    assert err <= TOL, err
