@@ -24,19 +24,24 @@
 //   k_summary   block = 32 neighbouring subsystems (lanes) x G chunks (warps).
 //               The block stages its strip tile (estimate planes and guidance)
 //               in shared memory, every thread eliminates its chunk's
-//               interior (forward sweep), then warp 0 merges the block's G
-//               chunk 2-ports into one group 2-port, keeping the merge
-//               factors for the back-fill.  The last block of each band to
-//               finish solves the band's reduced system: block Cholesky of the
-//               block tridiagonal system on the group separators (r x r
-//               blocks), forward elimination and back substitution.
-//   k_recover   block = 32 neighbouring centres x G chunks.  Warp 0 back-fills
-//               the separators inside the group from the merge factors; every
-//               thread then solves its interior with known separators
-//               (forward sweep into shared memory, backward sweep), writes the
-//               solution back into the strip and averages each pixel's 2r+1
-//               values across the neighbouring centres' lanes with warp
-//               shuffles (steps 3-4 of Sec. 2.3), one output line at a time.
+//               interior (forward sweep) and, when the pass keeps its factors,
+//               stores each entry's LDL^T row, z0 = D^-1 L^-1 f and top-port
+//               column; the warps then merge the block's G chunk 2-ports into
+//               one group 2-port as a binary tree, keeping the merge factors
+//               for the back-fill.  The last block of each band to finish
+//               solves the band's reduced system: block Cholesky of the block
+//               tridiagonal system on the group separators (r x r blocks),
+//               split into segments that the warps fold in parallel.
+//   k_backsub   block = 32 neighbouring centres x G chunks.  The warps
+//               back-fill the separators inside the group down the merge
+//               tree; every thread back-substitutes its interior from the kept
+//               factors, writes the solution back into the strip and averages
+//               each pixel's 2r+1 values across the neighbouring centres'
+//               lanes with warp shuffles (steps 3-4 of Sec. 2.3), one output
+//               line at a time.
+//   k_recover   the same without kept factors: it re-stages the tile and
+//               repeats the forward sweep into shared memory before the
+//               backward sweep (also the adjoint pass of the backward).
 //
 // The sweeps run one line of the vector at a time with the line's parity
 // (snake direction) and its first/last role fixed at compile time, so every
