@@ -86,7 +86,7 @@ __device__ __forceinline__ void build_args(const BatchArgs& ba, int i, PassArgs&
   __syncthreads();
 }
 
-template <int R, int CC>
+template <int R, int CC, int SM>
 __global__ void __launch_bounds__(256) k_summary_b(const __grid_constant__ BatchArgs ba) {
   extern __shared__ float smem[];
   __shared__ PassArgs sa;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_summary_b(const __grid_constant__ Batch
   const int local = blockIdx.x - ba.img[i].b0[0];
   const int by = local / ba.img[i].nbx[0];
   build_args(ba, i, sa);
-  body_summary<R, CC>(sa, local - by * ba.img[i].nbx[0], by, smem);
+  body_summary<R, CC, SM>(sa, local - by * ba.img[i].nbx[0], by, smem);
 }
 
 template <int R, int CC>

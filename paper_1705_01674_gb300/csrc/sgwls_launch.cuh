@@ -113,7 +113,7 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
     const size_t chain = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
     b.chain_smem = (pl.NG > 1 && chain <= kReducedSmemMax) ? 1 : 0;
     const size_t smem = b.chain_smem ? std::max(pl.smem_sum, chain) : pl.smem_sum;
-    auto ks = (!BWD && b.rhs) ? k_summary<R, CC, true> : k_summary<R, CC, false>;
+    auto ks = (!BWD && b.rhs) ? k_summary<R, CC, 2> : (b.fac ? k_summary<R, CC, 1> : k_summary<R, CC, 0>);
     if ((e = set_smem(ks, smem)) != cudaSuccess) return e;
     e = launch_pdl(ks, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), smem, st, b);
     if (e != cudaSuccess) return e;
@@ -155,9 +155,9 @@ cudaError_t launch_batch_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStre
   b.base.chain_smem = bl.red_smem ? 1 : 0;
   if (bl.any_multi) {
     const size_t smem = bl.red_smem ? std::max(bl.smem[0], bl.smem[1]) : bl.smem[0];
-    if ((e = set_smem(k_summary_b<R, CC>, smem)) != cudaSuccess) return e;
-    if ((e = launch_pdl(k_summary_b<R, CC>, dim3(bl.nblk[0]), dim3(32, bl.G), smem, st, b)) != cudaSuccess)
-      return e;
+    auto ks = bl.keep ? k_summary_b<R, CC, 1> : k_summary_b<R, CC, 0>;
+    if ((e = set_smem(ks, smem)) != cudaSuccess) return e;
+    if ((e = launch_pdl(ks, dim3(bl.nblk[0]), dim3(32, bl.G), smem, st, b)) != cudaSuccess) return e;
   }
   if (bl.keep && bl.any_multi) {
     if ((e = set_smem(k_backsub_b<R, CC>, bl.smem[2])) != cudaSuccess) return e;

@@ -1363,9 +1363,11 @@ __device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* sme
   });
 }
 
-// RHSB: the refinement's second solve (right-hand sides from a.rhs, factors
-// kept); a separate instantiation keeps that code out of the plain kernel.
-template <int R, int CC, bool RHSB = false>
+// SM 0: the factors are not kept (k_recover follows); 1: kept (a.fac,
+// k_backsub follows); 2: kept, right-hand sides from a.rhs (the
+// refinement's second solve).  One instantiation per mode keeps the unused
+// sweeps out of each kernel's code.
+template <int R, int CC, int SM>
 __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, float* smem) {
   using F = Fields<R, CC>;
   using MF = MFields<R, CC>;
@@ -1398,12 +1400,7 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   if (active && threadIdx.y < nch) {
     const Strided out{csum + threadIdx.y * F::N * 32 + lane, 32};
     const int col = unit ? lane : centre_of(a, sys, R) - R - off0;   // the lane's strip in the tile
-    if constexpr (RHSB)
-      chunk_summary<R, CC, true, true>(a, t, col, sys, c, out);
-    else if (a.fac)
-      chunk_summary<R, CC, true>(a, t, col, sys, c, out);
-    else
-      chunk_summary<R, CC, false>(a, t, col, sys, c, out);
+    chunk_summary<R, CC, SM != 0, SM == 2>(a, t, col, sys, c, out);
   }
   __syncthreads();
   merge_tree<R, CC>(a, csum, lane, sys, grp, c0, nch, G, active);
@@ -1422,10 +1419,10 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   if (threadIdx.x == 0 && threadIdx.y == 0) a.band_cnt[bx] = 0;   // ready for the next pass
 }
 
-template <int R, int CC, bool RHSB = false>
+template <int R, int CC, int SM>
 __global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
   extern __shared__ float smem[];
-  body_summary<R, CC, RHSB>(a, blockIdx.x, blockIdx.y, smem);
+  body_summary<R, CC, SM>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 // Separator values of every chunk of a group (one block): loads the group's
