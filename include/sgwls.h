@@ -13,7 +13,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Layout     planar C x H x W, row-major, contiguous per image; the guidance
- *            is one H x W plane.  Pixel (y, x) of channel c lives at
+ *            is one H x W plane (or guide_channels planes, planar).  Pixel (y, x) of channel c lives at
  *            c*H*W + y*W + x elements from the base pointer.
  * Pointers   image, guidance, output, workspace and saved-estimate pointers
  *            are DEVICE pointers (cudaMalloc / caching-allocator memory of the
@@ -65,9 +65,10 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *   r           neighbourhood radius, (2r+1)x(2r+1) system, 1 <= r <= SGWLS_R_MAX
  *   iters       T, the number of (column pass, row pass) pairs, >= 0 (Sec. 2.3)
  *   step        tau, the sliding step between subsystem centres (Sec. 2.3),
- *               1 <= step <= 2r+1 (the last centre is always included);
- *               this build runs step = 1, other values return
- *               SGWLS_E_UNSUPPORTED
+ *               1 <= step <= 2r+1 (the last centre is always included).
+ *               step > 1 runs on kept factors (not factor_cache = 2); the
+ *               batched, backward and no-allocation entry points return
+ *               SGWLS_E_UNSUPPORTED for step > 1
  *   axis_order  0: column direction first (Sec. 2.3), 1: row direction first
  *   refine      0 or 1: one step of iterative refinement of every
  *               subsystem solve: u1 = A~^-1 f in FP32, the residual
@@ -92,7 +93,15 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *               4 (2r+1)(2r+C') bytes per pixel of workspace (C' = channels
  *               per group, at most 4) and saves the second kernel's
  *               weights and factorisation.  A tuning knob: the results
- *               agree up to FP32 rounding.                                */
+ *               agree up to FP32 rounding.
+ *   guide_channels  Cg, the number of guidance planes: 0 or 1 (g is H x W)
+ *               or 2 .. SGWLS_GUIDE_MAX (g is Cg x H x W, planar, type
+ *               p->storage); |Gi-Gj| in Eq. 2 is then the Euclidean norm of
+ *               the difference of the two pixels' guidance vectors (for
+ *               example an RGB guidance image).  Cg > 1 runs on kept factors
+ *               (not factor_cache = 2); refine = 1 and the batched, backward
+ *               and no-allocation entry points return SGWLS_E_UNSUPPORTED
+ *               for Cg > 1.                                               */
 typedef struct {
   int weight;
   float sigma_s, sigma_r;
@@ -106,15 +115,17 @@ typedef struct {
   int inter_storage;
   int chunk_lines;
   int factor_cache;
+  int guide_channels;
 } sgwls_params;
 
 #define SGWLS_R_MAX 8
 #define SGWLS_C_MAX 64
+#define SGWLS_GUIDE_MAX 4
 
 /* Defaults: exp weights, sigma_s = 1, sigma_r = 0.1, alpha_s = alpha_r = 1.2,
  * eps = 1e-4 (Sec. 1), r = 1, iters = 1, step = 1, axis_order = 0,
- * refine = 0, FP32 storage, chunk_lines = 0, factor_cache = 0.  `p` must
- * not be NULL. */
+ * refine = 0, FP32 storage, chunk_lines = 0, factor_cache = 0,
+ * guide_channels = 1.  `p` must not be NULL. */
 void sgwls_params_default(sgwls_params* p);
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -129,7 +140,8 @@ size_t sgwls_workspace_bytes(int H, int W, int C, const sgwls_params* p);
 
 /* SG-WLS filter of one image (Sec. 2.3; Eqs. 2, 4, 5).
  *   f       device, C x H x W input (storage type p->storage)
- *   g       device, H x W guidance (p->storage); may equal f when C == 1
+ *   g       device, H x W guidance (p->storage), or Cg x H x W with
+ *           p->guide_channels = Cg > 1; may equal f when C == Cg
  *   u       device, C x H x W output (p->storage); must not alias f
  *   lambda  smoothness weight of Eq. 1 / Eq. 4, >= 0
  *   ws      device workspace of at least sgwls_workspace_bytes(H, W, C, p)
@@ -173,7 +185,8 @@ typedef struct {
  * (C + 1 <= 4 share every factor).
  *   f     device, C x H x W sparse input (FP32), zero where hmap is zero
  *   hmap  device, H x W index map (FP32): 1 where f holds data, else 0
- *   g     device, H x W guidance (FP32)
+ *   g     device, H x W guidance (FP32), or Cg x H x W with
+ *         p->guide_channels = Cg > 1
  *   u     device, C x H x W output (FP32); a pixel that no data reaches
  *         (filtered index map exactly 0) is 0
  *   ws    device workspace of at least sgwls_interpolate_workspace_bytes

@@ -8,7 +8,7 @@ neighbourhood, the formed 1D vector f of length s, the subsystem A_s u = f
 Indices are 0-based internally; the paper's 1-based row number i + 1 is
 spelled out where parity matters.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
 
 * |i - j| in Eq. 2 is the Euclidean distance between the two pixels'
   image coordinates (snake neighbours are 2D neighbours, Sec. 2.1).
@@ -22,6 +22,8 @@ Readings of points the paper leaves open (each also listed in the design doc):
 * The guidance G is fixed for all passes; the multi-channel input is
   filtered channel by channel with the same A_s (A_s depends on G and lambda
   only).
+* For a vector guidance (a colour image), |G_i - G_j| in Eq. 2 is the
+  Euclidean norm of the difference of the two guidance vectors.
 * The default pass order is column direction first, then row direction
   (Sec. 2.3: "along column direction and row direction alternatively");
   axis_order=1 runs the row direction first.
@@ -101,10 +103,16 @@ def guidance_weight(rows_i, cols_i, rows_j, cols_j, G: np.ndarray, prm: Params) 
 
     exp:  exp(-|i-j|^2 / (2 sigma_s^2)) * exp(-|G_i-G_j|^2 / (2 sigma_r^2))
     frac: 1 / (|i-j|^alpha_s + eps) * 1 / (|G_i-G_j|^alpha_r + eps)
-    |i - j| is the Euclidean distance of the image coordinates."""
+    |i - j| is the Euclidean distance of the image coordinates.  G is (H, W)
+    or, for a vector guidance (a colour image), (Cg, H, W); |G_i - G_j| is
+    then the Euclidean norm of the difference of the two guidance vectors."""
     G = np.asarray(G, dtype=np.float64)
     d2 = (rows_i - rows_j).astype(np.float64) ** 2 + (cols_i - cols_j).astype(np.float64) ** 2
-    dg = G[rows_i, cols_i] - G[rows_j, cols_j]
+    if G.ndim == 3:
+        diff = G[:, rows_i, cols_i] - G[:, rows_j, cols_j]          # (Cg, pairs)
+        dg = np.sqrt(np.sum(diff * diff, axis=0))
+    else:
+        dg = G[rows_i, cols_i] - G[rows_j, cols_j]
     if prm.weight == "exp":
         return np.exp(-d2 / (2.0 * prm.sigma_s ** 2)) * np.exp(-(dg ** 2) / (2.0 * prm.sigma_r ** 2))
     if prm.weight == "frac":
@@ -162,7 +170,7 @@ def sgwls_pass(U: np.ndarray, G: np.ndarray, lam: float, prm: Params, direction:
     vector, (2) solve its subsystem, (3) put the solution back into the
     (2r+1)-line patch, and (4) average the values each pixel received.
 
-    U: (C, H, W) current estimate; G: (H, W) guidance."""
+    U: (C, H, W) current estimate; G: (H, W) or (Cg, H, W) guidance."""
     U = np.asarray(U, dtype=np.float64)
     C, H, W = U.shape
     acc = np.zeros_like(U)
@@ -188,7 +196,8 @@ def sgwls(F: np.ndarray, G: np.ndarray, lam: float, prm: Params, return_inputs: 
     """SG-WLS smoothing (Sec. 2.3): the four steps performed T times along
     the column direction and the row direction alternately.
 
-    F: (C, H, W) or (H, W) input; G: (H, W) guidance (fixed for all passes).
+    F: (C, H, W) or (H, W) input; G: (H, W) or (Cg, H, W) guidance (fixed
+    for all passes).
     Returns the (C, H, W) float64 result (and, if ``return_inputs``, the
     list of each pass's input estimate)."""
     U = np.asarray(F, dtype=np.float64)
@@ -208,7 +217,8 @@ def sgwls_interpolate(F: np.ndarray, Hm: np.ndarray, G: np.ndarray, lam: float, 
     data, 0 elsewhere), and their ratio per pixel.  Reading: a pixel that no
     data reaches (smoothed index map exactly 0) is 0.
 
-    F: (C, H, W) or (H, W), zero where Hm is zero; Hm, G: (H, W)."""
+    F: (C, H, W) or (H, W), zero where Hm is zero; Hm: (H, W); G: (H, W) or
+    (Cg, H, W)."""
     N = sgwls(F, G, lam, prm)
     D = sgwls(np.asarray(Hm, dtype=np.float64), G, lam, prm)[0]
     U = np.where(D > 0, N / np.where(D > 0, D, 1.0), 0.0)

@@ -46,6 +46,16 @@ def _chw(f: torch.Tensor):
     raise ValueError("f must be (H, W) or (C, H, W)")
 
 
+def _guide(g: torch.Tensor, H: int, W: int) -> int:
+    """Guidance planes of g: (H, W) -> 1, (Cg, H, W) -> Cg (a vector
+    guidance, |G_i - G_j| of Eq. 2 the Euclidean norm)."""
+    if tuple(g.shape) == (H, W):
+        return 1
+    if g.dim() == 3 and tuple(g.shape[1:]) == (H, W) and g.shape[0] >= 1:
+        return int(g.shape[0])
+    raise ValueError("g must be (H, W) or (Cg, H, W)")
+
+
 def workspace_bytes(C: int, H: int, W: int, **kw) -> int:
     p = make_params(**kw)
     n = _capi.lib().sgwls_workspace_bytes(int(H), int(W), int(C), ctypes.byref(p))
@@ -59,15 +69,15 @@ def sgwls_filter(f: torch.Tensor, g: torch.Tensor, lam: float, *, out: torch.Ten
                  stream: torch.cuda.Stream | None = None, **kw) -> torch.Tensor:
     """SG-WLS filter of one image through ``sgwls_filter`` (C ABI).
 
-    f: (C,H,W) or (H,W); g: (H,W), same dtype as f (float32 or bfloat16).
+    f: (C,H,W) or (H,W); g: (H,W), or (Cg,H,W) for a vector guidance (an
+    RGB image, say), same dtype as f (float32 or bfloat16).
     ``saved`` (optional): a float tensor with 2*iters*C*H*W elements in the
     intermediate storage type that receives each pass's input estimate.
     Keyword parameters: see ``make_params``."""
     _check_tensor(f, "f")
     _check_tensor(g, "g")
     C, H, W = _chw(f)
-    if tuple(g.shape) != (H, W):
-        raise ValueError("g must be (H, W)")
+    kw["guide_channels"] = _guide(g, H, W)
     if g.dtype != f.dtype:
         raise TypeError("g must have the dtype of f")
     kw.setdefault("storage", "bf16" if f.dtype == torch.bfloat16 else "f32")
@@ -96,14 +106,15 @@ def sgwls_interpolate(f: torch.Tensor, hmap: torch.Tensor, g: torch.Tensor, lam:
                       stream: torch.cuda.Stream | None = None, **kw) -> torch.Tensor:
     """Guided sparse interpolation (Eq. 21) through ``sgwls_interpolate``:
     SG-WLS(f) / SG-WLS(hmap) per pixel.  f: (C,H,W) or (H,W) float32, zero
-    where hmap is zero; hmap, g: (H,W) float32.  Keyword parameters: see
-    ``make_params``."""
+    where hmap is zero; hmap: (H,W) float32; g: (H,W) or (Cg,H,W) float32.
+    Keyword parameters: see ``make_params``."""
     _check_tensor(f, "f")
     _check_tensor(hmap, "hmap")
     _check_tensor(g, "g")
     C, H, W = _chw(f)
-    if tuple(g.shape) != (H, W) or tuple(hmap.shape) != (H, W):
-        raise ValueError("hmap and g must be (H, W)")
+    if tuple(hmap.shape) != (H, W):
+        raise ValueError("hmap must be (H, W)")
+    kw["guide_channels"] = _guide(g, H, W)
     if not (f.dtype == hmap.dtype == g.dtype == torch.float32):
         raise TypeError("f, hmap and g must be float32")
     p = make_params(**kw)
@@ -132,8 +143,9 @@ def sgwls_filter_pass(f: torch.Tensor, g: torch.Tensor, lam: float, direction: i
     _check_tensor(f, "f")
     _check_tensor(g, "g")
     C, H, W = _chw(f)
-    if tuple(g.shape) != (H, W) or g.dtype != f.dtype:
-        raise ValueError("g must be (H, W) with the dtype of f")
+    kw["guide_channels"] = _guide(g, H, W)
+    if g.dtype != f.dtype:
+        raise ValueError("g must have the dtype of f")
     kw.setdefault("storage", "bf16" if f.dtype == torch.bfloat16 else "f32")
     p = make_params(**kw)
     lib = _capi.lib()

@@ -47,6 +47,7 @@ class SgwlsParams(ctypes.Structure):
         ("inter_storage", ctypes.c_int),
         ("chunk_lines", ctypes.c_int),
         ("factor_cache", ctypes.c_int),
+        ("guide_channels", ctypes.c_int),
     ]
 
 
@@ -133,7 +134,7 @@ def check(status: int, where: str):
 
 def make_params(r=1, iters=1, step=1, axis_order=0, weight="exp", sigma_s=None, sigma_r=0.1,
                 alpha_s=1.2, alpha_r=1.2, eps=1e-4, storage="f32", inter_storage=None,
-                refine=0, chunk_lines=0, factor_cache=0) -> SgwlsParams:
+                refine=0, chunk_lines=0, factor_cache=0, guide_channels=1) -> SgwlsParams:
     p = SgwlsParams()
     lib().sgwls_params_default(ctypes.byref(p))
     p.weight = {"exp": W_EXP, "frac": W_FRAC}[weight]
@@ -149,6 +150,7 @@ def make_params(r=1, iters=1, step=1, axis_order=0, weight="exp", sigma_s=None, 
     p.refine = int(refine)
     p.chunk_lines = int(chunk_lines)
     p.factor_cache = int(factor_cache)
+    p.guide_channels = int(guide_channels)
     dt = {"f32": F32, "bf16": BF16}
     p.storage = dt[storage]
     p.inter_storage = dt[inter_storage or storage]

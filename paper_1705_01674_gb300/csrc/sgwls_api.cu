@@ -59,7 +59,8 @@ inline int keep_lines(int r) { return r == 1 ? 6 : r == 2 ? 12 : r == 3 ? 8 : 16
 
 // Subsystems of a pass across D offsets with sliding step `step`: the
 // regular centres r, r + step, ... <= D-1-r, and the last centre D-1-r
-// appended when the stride misses it (reading D7).  *nreg: regular ones.
+// appended when the stride misses it (every line stays covered).  *nreg:
+// regular ones.
 int n_centres(int D, int r, int step, int* nreg) {
   const int nr = (D - 1 - 2 * r) / step + 1;
   if (nreg) *nreg = nr;
@@ -68,12 +69,13 @@ int n_centres(int D, int r, int step, int* nreg) {
 
 // keep: the pass keeps its chunk factors (k_backsub follows k_summary; no
 // k_recover tile), so only the summary's tile and 2-ports bound the block.
-Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, bool keep = false, int step = 1) {
+Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, bool keep = false, int step = 1,
+               int gc = 1) {
   const int bands = step == 1 ? (D + (32 - 2 * r) - 1) / (32 - 2 * r) : (n_centres(D, r, step, nullptr) + 31) / 32;
   auto second = [&](int hh, int G) {
     return keep ? smem_backsub(r, CC, hh, G, step) : smem_recover(r, CC, hh, G, bwd);
   };
-  auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G, step)); };
+  auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G, step, gc)); };
   int h;
   if (keep && step > 1) {
     // sliding step: fewer subsystems, so fewer warps; shorter chunks would
@@ -101,7 +103,7 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   while (G < kGMax && G < pl.P && block(h, 2 * G) <= gcap) G *= 2;
   pl.G = G;
   pl.NG = (pl.P + G - 1) / G;
-  pl.smem_sum = smem_summary(r, CC, h, G, step);
+  pl.smem_sum = smem_summary(r, CC, h, G, step, gc);
   pl.smem_rec = smem_recover(r, CC, h, G, bwd);
   return pl;
 }
@@ -128,16 +130,20 @@ size_t fac_bytes(int L, int r, int CC, int sstride) {
   return (size_t)L * (2 * r + 1) * (2 * r + CC) * sstride * sizeof(float);
 }
 size_t psi_bytes(int P, int r, int sstride) { return (size_t)P * r * r * sstride * sizeof(float); }
+// Guidance planes of a call (guide_channels 0 and 1: one plane).
+int guide_planes(const sgwls_params* p) { return p->guide_channels > 1 ? p->guide_channels : 1; }
 // Plan of one forward pass; *keep: its chunk factors are kept between the
 // two kernels (needs at least two chunks).
 Plan fwd_plan(const sgwls_params* p, int L, int D, int CC, int sstride, bool* keep) {
-  // the sliding step and the refinement run on kept factors only
-  const bool need = p->step > 1 || p->refine;
+  // the sliding step, the refinement and a vector guidance run on kept
+  // factors only
+  const int gc = guide_planes(p);
+  const bool need = p->step > 1 || p->refine || gc > 1;
   bool k = need || p->factor_cache == 1 ||
            (p->factor_cache == 0 && fac_bytes(L, p->r, CC, sstride) <= kFactorCacheBytes);
-  Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k, p->step);
+  Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k, p->step, k ? gc : 1);
   // keeping factors needs at least two chunks
-  if (k && need && pl.P < 2 && L >= 2) pl = make_plan(L, D, p->r, CC, (L + 1) / 2, false, true, p->step);
+  if (k && need && pl.P < 2 && L >= 2) pl = make_plan(L, D, p->r, CC, (L + 1) / 2, false, true, p->step, gc);
   if (k && pl.P < 2) {
     k = false;
     pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, false);
@@ -214,6 +220,7 @@ sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
   if (p->refine < 0 || p->refine > 1) return SGWLS_E_INVALID;
   if (p->chunk_lines < 0) return SGWLS_E_INVALID;
   if (p->factor_cache < 0 || p->factor_cache > 2) return SGWLS_E_INVALID;
+  if (p->guide_channels < 0 || p->guide_channels > SGWLS_GUIDE_MAX) return SGWLS_E_INVALID;
   if ((p->storage != SGWLS_F32 && p->storage != SGWLS_BF16) ||
       (p->inter_storage != SGWLS_F32 && p->inter_storage != SGWLS_BF16))
     return SGWLS_E_DTYPE;
@@ -223,13 +230,15 @@ sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
   return SGWLS_OK;
 }
 
-// The sliding step tau > 1 runs on the kernels that keep chunk factors: it
-// needs them kept in every pass (not factor_cache = 2, not beyond the
-// factor-store budget, at least two lines per subsystem).
+// The sliding step tau > 1, the refinement and a vector guidance run on the
+// kernels that keep chunk factors: they need them kept in every pass (not
+// factor_cache = 2, not beyond the factor-store budget, at least two lines
+// per subsystem).
 sgwls_status check_step(int H, int W, int C, const sgwls_params* p) {
-  // refinement (refine = 1) reuses the keep path at step 1
-  if (p->refine && p->step != 1) return SGWLS_E_UNSUPPORTED;
-  if (p->step == 1 && !p->refine) return SGWLS_OK;
+  // refinement (refine = 1) reuses the keep path at step 1; its FP64
+  // residual reads a single guidance plane
+  if (p->refine && (p->step != 1 || guide_planes(p) > 1)) return SGWLS_E_UNSUPPORTED;
+  if (p->step == 1 && !p->refine && guide_planes(p) == 1) return SGWLS_OK;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
@@ -363,6 +372,7 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
   a.L = dir == 0 ? H : W;
   a.D = dir == 0 ? W : H;
   a.step = p->step;
+  a.gc = guide_planes(p);
   a.nsys = n_centres(a.D, p->r, p->step, &a.nreg);
   a.sstride = (a.nsys + 31) / 32 * 32;
   a.summ = reinterpret_cast<float*>(wsb + lo.summ_off);
@@ -570,7 +580,8 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
 
 sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) {
   if (B < 1 || !imgs || !p) return SGWLS_E_INVALID;
-  if (p->step != 1 || p->refine) return SGWLS_E_UNSUPPORTED;   // sliding step, refinement: single images
+  // sliding step, refinement, vector guidance: single images
+  if (p->step != 1 || p->refine || p->guide_channels > 1) return SGWLS_E_UNSUPPORTED;
   const int C = imgs[0].C;
   if (C < 1 || C > kGroupMax) return C < 1 ? SGWLS_E_SHAPE : SGWLS_E_UNSUPPORTED;
   for (int i = 0; i < B; ++i) {
@@ -882,6 +893,7 @@ void sgwls_params_default(sgwls_params* p) {
   p->inter_storage = SGWLS_F32;
   p->chunk_lines = 0;
   p->factor_cache = 0;
+  p->guide_channels = 1;
 }
 
 const char* sgwls_status_string(sgwls_status s) {
@@ -973,7 +985,7 @@ sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void
   if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
   if (p->storage != SGWLS_F32 || p->inter_storage != SGWLS_F32) return SGWLS_E_UNSUPPORTED;
   if (p->weight == SGWLS_W_FRAC && p->alpha_r < 1.f) return SGWLS_E_UNSUPPORTED;
-  if (p->step != 1 || p->refine) return SGWLS_E_UNSUPPORTED;
+  if (p->step != 1 || p->refine || p->guide_channels > 1) return SGWLS_E_UNSUPPORTED;
   const size_t need = make_bwd_layout(H, W, C, p).total;
   if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
   return run_backward(static_cast<const float*>(grad_u), static_cast<const float*>(g),

@@ -27,7 +27,8 @@ enum : int { DT_F32 = 0, DT_BF16 = 1 };
 
 struct PassArgs {
   const void* in;      // C planes, dtype in_dt
-  const void* g;       // guidance plane, dtype g_dt
+  const void* g;       // guidance planes (gc of them, planar), dtype g_dt
+  int gc;              // guidance channels: 1, or 2..4 (vector guidance, |G_i - G_j| the Euclidean norm)
   void* out;           // C planes, dtype out_dt
   long long plane;     // H * W (elements per plane)
   int H, W;
@@ -128,6 +129,13 @@ __device__ __forceinline__ float fast_ex2(float x) {
 __device__ __forceinline__ float range_factor(const PassArgs& a, float dg) {
   if (a.weight == 0) return fast_ex2(dg * dg * a.range_k);
   return 1.0f / (powf(fabsf(dg), a.range_k) + a.eps);
+}
+
+// The same for a vector guidance, from the squared norm d2 of the
+// difference: exp(-d2 / (2 sigma_r^2)), or 1 / (d2^(alpha_r / 2) + eps).
+__device__ __forceinline__ float range_factor_sq(const PassArgs& a, float d2) {
+  if (a.weight == 0) return fast_ex2(d2 * a.range_k);
+  return 1.0f / (powf(d2, 0.5f * a.range_k) + a.eps);
 }
 
 // Programmatic dependent launch: wait for the preceding kernel of the stream

@@ -15,13 +15,14 @@ struct Plan {
   size_t smem_sum, smem_rec;
 };
 
-// Shared memory of the two tiled kernels for a plan (bytes).
-inline size_t tile_floats(int r, int CC, int h, int G, int step = 1) {
+// Shared memory of the two tiled kernels for a plan (bytes); gc guidance
+// planes.
+inline size_t tile_floats(int r, int CC, int h, int G, int step = 1, int gc = 1) {
   const int ncol = tile_ncol(r, step);
-  return (size_t)(CC + 1) * (G * h + 2) * std::max(tile_pitch_n(ncol, 0), tile_pitch_n(ncol, 1));
+  return (size_t)(CC + gc) * (G * h + 2) * std::max(tile_pitch_n(ncol, 0), tile_pitch_n(ncol, 1));
 }
-inline size_t smem_summary(int r, int CC, int h, int G, int step = 1) {
-  return 4 * (tile_floats(r, CC, h, G, step) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
+inline size_t smem_summary(int r, int CC, int h, int G, int step = 1, int gc = 1) {
+  return 4 * (tile_floats(r, CC, h, G, step, gc) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
 }
 inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
   const int n = 2 * r + 1;
@@ -109,11 +110,14 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   PassArgs b = a;
   b.early_stage = a.P > 1 ? 1 : 0;   // k_recover follows k_summary
   if (BWD || a.P < 2) b.fac = b.psi = nullptr;   // factors are kept only by a forward k_summary
+  // a vector guidance is read by the keeping k_summary<..., 3> alone
+  if (a.gc > 1 && (!b.fac || b.rhs)) return cudaErrorInvalidValue;
   if (a.P > 1) {
     const size_t chain = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
     b.chain_smem = (pl.NG > 1 && chain <= kReducedSmemMax) ? 1 : 0;
     const size_t smem = b.chain_smem ? std::max(pl.smem_sum, chain) : pl.smem_sum;
-    auto ks = (!BWD && b.rhs) ? k_summary<R, CC, 2> : (b.fac ? k_summary<R, CC, 1> : k_summary<R, CC, 0>);
+    auto ks = (!BWD && b.rhs) ? k_summary<R, CC, 2>
+                              : (!b.fac ? k_summary<R, CC, 0> : (a.gc > 1 ? k_summary<R, CC, 3> : k_summary<R, CC, 1>));
     if ((e = set_smem(ks, smem)) != cudaSuccess) return e;
     e = launch_pdl(ks, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), smem, st, b);
     if (e != cudaSuccess) return e;

@@ -54,6 +54,8 @@ extern "C" sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, 
   // the sliding step tau > 1 runs on kept chunk factors, which this scratch does not hold
   if (p->step != 1) return (p->step >= 1 && p->step <= 2 * p->r + 1) ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;
   if (p->refine) return p->refine == 1 ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;   // needs kept factors
+  if (p->guide_channels > 1)   // a vector guidance also runs on kept factors
+    return p->guide_channels <= SGWLS_GUIDE_MAX ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;
   // a pass needs no intermediate image: size the scratch as for iters == 0
   sgwls_params q = *p;
   q.iters = 0;

@@ -75,8 +75,8 @@ struct MFields {
 };
 
 // ---------------------------------------------------------------------------
-// Shared-memory strip tile: planes 0..CC-1 = estimate channels, plane CC =
-// guidance; tile[(plane * ntl + tl) * pitch + col] holds (line tl0 + tl,
+// Shared-memory strip tile: planes 0..CC-1 = estimate channels, then the
+// guidance plane(s); tile[(plane * ntl + tl) * pitch + col] holds (line tl0 + tl,
 // across-offset off0 + col), zero outside the image.  pitch is odd so the
 // transposed staging of the row direction is free of bank conflicts.
 struct Tile {
@@ -118,12 +118,12 @@ __host__ __device__ constexpr int step_own_max(int r, int step) {
 __host__ __device__ constexpr int step_acc_width(int r, int step) { return 32 * step + 2 * r + 2; }
 
 // Base of tile plane pl: estimate planes from `in` (then `in2`), the
-// guidance last.  `elem` is the element size of the estimate planes.
+// guidance planes last.  `elem` is the element size of plane pl's type.
 template <int CC>
 __device__ __forceinline__ const char* plane_base(const PassArgs& a, int pl, int elem) {
   if (pl < a.n_in1) return static_cast<const char*>(a.in) + (size_t)pl * a.plane * elem;
   if (pl < CC) return static_cast<const char*>(a.in2) + (size_t)(pl - a.n_in1) * a.plane * elem;
-  return static_cast<const char*>(a.g);
+  return static_cast<const char*>(a.g) + (size_t)(pl - CC) * a.plane * elem;
 }
 
 // Mixed storage types (BF16 guidance with FP32 estimates): plain loop.
@@ -140,7 +140,8 @@ __device__ __noinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, 
     float v = 0.f;
     if (line >= 0 && line < a.L && off >= 0 && off < a.D) {
       const long long pix = pix_index(a, line, off);
-      v = pl < CC ? ld_px(plane_base<CC>(a, pl, a.in_dt == DT_F32 ? 4 : 2), pix, a.in_dt) : ld_px(a.g, pix, a.g_dt);
+      v = pl < CC ? ld_px(plane_base<CC>(a, pl, a.in_dt == DT_F32 ? 4 : 2), pix, a.in_dt)
+                  : ld_px(plane_base<CC>(a, pl, a.g_dt == DT_F32 ? 4 : 2), pix, a.g_dt);
     }
     t.p[(pl * t.ntl + tl) * t.pitch + col] = v;
   }
@@ -503,46 +504,91 @@ struct LineUnroll {
 
 // lambda * w(p, p+t), t = 1..R, for entry j of a line (Eq. 2).  gr / gnr:
 // guidance rows of this line and the next (lane-relative); `end_ok`: the next
-// line exists (pairs that cross into it are inside the vector).
-template <int R, bool ODD>
+// line exists (pairs that cross into it are inside the vector).  GCM: a.gc
+// guidance planes gs floats apart (the norm of the difference vector).
+template <int R, bool ODD, bool GCM = false>
 __device__ __forceinline__ void forward_weights(const PassArgs& a, const float* gr, const float* gnr, int j,
-                                                bool end_ok, float (&wf)[R]) {
+                                                bool end_ok, float (&wf)[R], int gs = 0) {
   constexpr int n = 2 * R + 1;
   const float g0 = gr[ecol<R, ODD>(j)];
 #pragma unroll
   for (int t = 1; t <= R; ++t) {
     const int jt = j + t;
-    const float gq = jt < n ? gr[ecol<R, ODD>(jt)] : gnr[ecol<R, !ODD>(jt - n)];
-    const float w = a.sp[j * R + t - 1] * range_factor(a, g0 - gq);
+    float w;
+    if constexpr (GCM) {
+      const float* gp = gr + ecol<R, ODD>(j);
+      const float* gq = jt < n ? gr + ecol<R, ODD>(jt) : gnr + ecol<R, !ODD>(jt - n);
+      float d2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k < a.gc) {
+          const float d = gp[k * gs] - gq[k * gs];
+          d2 += d * d;
+        }
+      }
+      w = a.sp[j * R + t - 1] * range_factor_sq(a, d2);
+    } else {
+      const float gq = jt < n ? gr[ecol<R, ODD>(jt)] : gnr[ecol<R, !ODD>(jt - n)];
+      w = a.sp[j * R + t - 1] * range_factor(a, g0 - gq);
+    }
     wf[t - 1] = (jt < n || end_ok) ? w : 0.f;
   }
 }
 
 // lambda * w(p, p+t) of every entry of a line (j = 0..2r, t = 1..r), one
 // branch on the weight form per line instead of one per pair.
-template <int R, bool ODD>
+template <int R, bool ODD, bool GCM = false>
 __device__ __forceinline__ void line_weights(const PassArgs& a, const float* gr, const float* gnr, bool end_ok,
-                                             float (&wl)[2 * R + 1][R]) {
+                                             float (&wl)[2 * R + 1][R], int gs = 0) {
   constexpr int n = 2 * R + 1;
   float g[n + R];   // guidance of the line's entries, then of the next line's first r
-#pragma unroll
-  for (int j = 0; j < n; ++j) g[j] = gr[ecol<R, ODD>(j)];
-#pragma unroll
-  for (int k = 0; k < R; ++k) g[n + k] = gnr[ecol<R, !ODD>(k)];
-  if (a.weight == 0) {
+  if constexpr (GCM) {
+    // squared norms of the guidance differences, plane by plane
+    float d2[n][R];
 #pragma unroll
     for (int j = 0; j < n; ++j)
 #pragma unroll
-      for (int t = 1; t <= R; ++t) {
-        const float d = g[j] - g[j + t];
-        wl[j][t - 1] = a.sp[j * R + t - 1] * fast_ex2(d * d * a.range_k);
+      for (int t = 0; t < R; ++t) d2[j][t] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k < a.gc) {
+#pragma unroll
+        for (int j = 0; j < n; ++j) g[j] = gr[k * gs + ecol<R, ODD>(j)];
+#pragma unroll
+        for (int m = 0; m < R; ++m) g[n + m] = gnr[k * gs + ecol<R, !ODD>(m)];
+#pragma unroll
+        for (int j = 0; j < n; ++j)
+#pragma unroll
+          for (int t = 1; t <= R; ++t) {
+            const float d = g[j] - g[j + t];
+            d2[j][t - 1] += d * d;
+          }
       }
+    }
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int t = 1; t <= R; ++t) wl[j][t - 1] = a.sp[j * R + t - 1] * range_factor_sq(a, d2[j][t - 1]);
   } else {
 #pragma unroll
-    for (int j = 0; j < n; ++j)
+    for (int j = 0; j < n; ++j) g[j] = gr[ecol<R, ODD>(j)];
 #pragma unroll
-      for (int t = 1; t <= R; ++t)
-        wl[j][t - 1] = a.sp[j * R + t - 1] / (powf(fabsf(g[j] - g[j + t]), a.range_k) + a.eps);
+    for (int k = 0; k < R; ++k) g[n + k] = gnr[ecol<R, !ODD>(k)];
+    if (a.weight == 0) {
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+#pragma unroll
+        for (int t = 1; t <= R; ++t) {
+          const float d = g[j] - g[j + t];
+          wl[j][t - 1] = a.sp[j * R + t - 1] * fast_ex2(d * d * a.range_k);
+        }
+    } else {
+#pragma unroll
+      for (int j = 0; j < n; ++j)
+#pragma unroll
+        for (int t = 1; t <= R; ++t)
+          wl[j][t - 1] = a.sp[j * R + t - 1] / (powf(fabsf(g[j] - g[j + t]), a.range_k) + a.eps);
+    }
   }
   if (!end_ok) {
 #pragma unroll
@@ -667,7 +713,7 @@ __device__ __forceinline__ Chunk make_chunk(const PassArgs& a, int c) {
 }
 
 // Weights of the line above a chunk (its top separator's line) into wh.
-template <int R, int CC>
+template <int R, int CC, bool GCM = false>
 __device__ __forceinline__ void prologue_weights(const PassArgs& a, const Tile& t, int lane, int line,
                                                  float (&wh)[R][R]) {
   constexpr int n = 2 * R + 1;
@@ -678,7 +724,7 @@ __device__ __forceinline__ void prologue_weights(const PassArgs& a, const Tile& 
     float wf[R];
 #pragma unroll LineUnroll<R>::value
     for (int j = 0; j < n; ++j) {
-      forward_weights<R, ODD>(a, gr, gnr, j, true, wf);
+      forward_weights<R, ODD, GCM>(a, gr, gnr, j, true, wf, t.ntl * t.pitch);
       push_weights<R>(wh, wf);
     }
   };
@@ -790,7 +836,7 @@ __device__ __forceinline__ float* psi_lane(const PassArgs& a, int sys) {
 }
 // With a.fac set it also keeps, per interior entry, the factor row, z0 and
 // Phi for k_backsub, and psi for the last r interior entries.
-template <int R, int CC, bool KEEP, bool RHSB = false>
+template <int R, int CC, bool KEEP, bool RHSB = false, bool GCM = false>
 __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int col, int sys, int c,
                                               Strided out) {
   const int lane = col;   // tile column of the lane's strip
@@ -816,7 +862,7 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
   float DS[R][R] = {};
   float FS[R][CC] = {};
 
-  if (q.top) prologue_weights<R, CC>(a, t, lane, q.line0 - 1, wh);
+  if (q.top) prologue_weights<R, CC, GCM>(a, t, lane, q.line0 - 1, wh);
 
   for_lines(q.line0, q.line1, [&](auto odd, const bool FIRST, auto last, int line) {
     constexpr bool ODD = decltype(odd)::value;
@@ -826,7 +872,7 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
     const float* fr = t.row(0, line) + lane;
     const bool end_ok = line + 1 < a.L;
     float wl[LW ? n : 1][R];
-    if constexpr (LW) line_weights<R, ODD>(a, gr, gnr, end_ok, wl);
+    if constexpr (LW) line_weights<R, ODD, GCM>(a, gr, gnr, end_ok, wl, pstride);
     (void)wl;
 #pragma unroll LineUnroll<R>::value
     for (int j = 0; j < n; ++j) {
@@ -835,7 +881,7 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
 #pragma unroll
         for (int tt = 0; tt < R; ++tt) wf[tt] = wl[LW ? j : 0][tt];
       } else {
-        forward_weights<R, ODD>(a, gr, gnr, j, end_ok, wf);
+        forward_weights<R, ODD, GCM>(a, gr, gnr, j, end_ok, wf, pstride);
       }
       float diag = 1.f;
 #pragma unroll
@@ -1365,8 +1411,9 @@ __device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* sme
 
 // SM 0: the factors are not kept (k_recover follows); 1: kept (a.fac,
 // k_backsub follows); 2: kept, right-hand sides from a.rhs (the
-// refinement's second solve).  One instantiation per mode keeps the unused
-// sweeps out of each kernel's code.
+// refinement's second solve); 3: kept, a vector guidance of a.gc planes.
+// One instantiation per mode keeps the unused sweeps out of each kernel's
+// code.
 template <int R, int CC, int SM>
 __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, float* smem) {
   using F = Fields<R, CC>;
@@ -1385,11 +1432,13 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   const int off0 = unit ? bx * 32 : centre_of(a, bx * 32, R) - R;
   Tile t;
   group_tile(a, c0, G, off0, unit ? 32 + 2 * R : tile_ncol(R, a.step), unit, smem, t);
-  float* csum = smem + (CC + 1) * t.ntl * t.pitch;   // [G][F::N][32]
+  // SM 3: a guidance of a.gc planes (tile planes CC .. CC + gc - 1)
+  const int np = CC + (SM == 3 ? a.gc : 1);
+  float* csum = smem + np * t.ntl * t.pitch;   // [G][F::N][32]
   // The guidance is an input of the whole filter (no kernel of the filter
-  // writes it): its plane is staged before the wait, overlapping the
+  // writes it): its planes are staged before the wait, overlapping the
   // preceding kernel's tail; the estimate planes after it.
-  if (unit) stage_tile<CC, 32 + 2 * R>(a, t, CC, CC + 1); else stage_tile_rt<CC>(a, t, CC, CC + 1);
+  if (unit) stage_tile<CC, 32 + 2 * R>(a, t, CC, np); else stage_tile_rt<CC>(a, t, CC, np);
   griddep_wait();
   griddep_launch();
   if (unit) stage_tile<CC, 32 + 2 * R>(a, t, 0, CC); else stage_tile_rt<CC>(a, t, 0, CC);
@@ -1400,7 +1449,7 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   if (active && threadIdx.y < nch) {
     const Strided out{csum + threadIdx.y * F::N * 32 + lane, 32};
     const int col = unit ? lane : centre_of(a, sys, R) - R - off0;   // the lane's strip in the tile
-    chunk_summary<R, CC, SM != 0, SM == 2>(a, t, col, sys, c, out);
+    chunk_summary<R, CC, SM != 0, SM == 2, SM == 3>(a, t, col, sys, c, out);
   }
   __syncthreads();
   merge_tree<R, CC>(a, csum, lane, sys, grp, c0, nch, G, active);

@@ -123,3 +123,35 @@ def test_interpolate_validation_host_only(capi):
     assert call(lam=-1.0) == E_INVALID
     assert call(nws=16) == E_WS
     assert call(p=capi.make_params(storage="bf16")) == E_UNSUP
+
+
+def test_guide_channels_validation_host_only(capi):
+    """A vector guidance (guide_channels = Cg > 1): range checked, runs on
+    kept factors only, and the entry points without a vector-guidance path
+    say so before any launch (the pointers here are never dereferenced)."""
+    lib = capi.lib()
+    E_INVALID, E_UNSUP = -1, -7
+    for bad in (-1, 5):
+        assert _call(capi, p=capi.make_params(guide_channels=bad)) == E_INVALID, bad
+        assert lib.sgwls_workspace_bytes(64, 64, 1, ctypes.byref(capi.make_params(guide_channels=bad))) == 0
+    p = capi.make_params(r=2, iters=2, guide_channels=3)
+    assert lib.sgwls_workspace_bytes(64, 64, 3, ctypes.byref(p)) > 0
+    assert _call(capi, p=capi.make_params(guide_channels=3, factor_cache=2)) == E_UNSUP
+    assert _call(capi, p=capi.make_params(guide_channels=3, refine=1)) == E_UNSUP
+    # batched, backward and the no-allocation pass take one guidance plane
+    img = (capi.SgwlsImage * 1)()
+    img[0].f, img[0].g, img[0].u = 0x1000, 0x2000, 0x3000
+    img[0].H, img[0].W, img[0].C = 64, 64, 1
+    img[0].lam = 1.0
+    img[0].saved = None
+    assert lib.sgwls_filter_batched(1, img, ctypes.byref(p), ctypes.c_void_p(0x10000), 1 << 30,
+                                    ctypes.c_void_p(0)) == E_UNSUP
+    pb = capi.make_params(r=1, iters=1, guide_channels=3)
+    st = lib.sgwls_filter_backward(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000),
+                                   64, 64, 1, ctypes.c_float(1.0), ctypes.byref(pb), ctypes.c_void_p(0x4000),
+                                   ctypes.c_void_p(0), None, ctypes.c_void_p(0x10000), 1 << 30,
+                                   ctypes.c_void_p(0))
+    assert st == E_UNSUP
+    st = lib.sgwls_filter_pass_noalloc(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000),
+                                       64, 64, 1, ctypes.c_float(1.0), ctypes.byref(pb), 0, ctypes.c_void_p(0))
+    assert st == E_UNSUP

@@ -1,7 +1,7 @@
-"""Refinement of every subsystem solve (row a9): u1 = A~^-1 f in FP32, the
+"""Refinement of every subsystem solve: u1 = A~^-1 f in FP32, the
 residual rho = f - A u1 with A rebuilt from the guidance in FP64, u = u1 +
 A~^-1 rho, then the averaging.  At the paper's frac-weight application
-settings (reading D20) the unrefined FP32 result sits up to ~5e-3 from the
+settings (alpha = 1.2, eps = 1e-4, lambda up to 900) the unrefined FP32 result sits up to ~5e-3 from the
 FP64 oracle because A's FP32 entries alone move the solution that far; one
 refinement step brings it back within 2e-4."""
 import numpy as np

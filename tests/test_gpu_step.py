@@ -1,6 +1,6 @@
 """GPU parity of the sliding construction with step tau > 1 (Sec. 2.3):
 centres r, r + tau, ... and the last centre D-1-r appended when the stride
-misses it (reading D7); each pixel averages the subsystems whose strips
+misses it (so every line stays covered); each pixel averages the subsystems whose strips
 cover it.  Against the FP64 oracle, same tolerance as step 1."""
 import numpy as np
 import pytest
@@ -65,7 +65,8 @@ def test_step_chunkings(api, chunk_lines):
 
 def test_step_pass_entry_and_bf16(api):
     """One pass through sgwls_filter_pass (both directions) and BF16 storage
-    (bound per reading D14: one BF16 store per pass plus the FP32 bound)."""
+    (bound: one BF16 rounding of the stored estimate per pass plus the FP32
+    bound)."""
     import torch
     from oracle import sgwls_pass
     F = synth.rgb_scene(45, 66, seed=8, n_rect=10, n_disk=3)
