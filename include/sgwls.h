@@ -74,7 +74,10 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *               subsystem solve: u1 = A~^-1 f in FP32, the residual
  *               f - A u1 with A rebuilt from the guidance in FP64, the
  *               FP32 solve of the residual added to u1, then the averaging
- *               (five kernels per pass instead of two).  For ill-conditioned
+ *               (five kernels per pass instead of two, plus one that
+ *               evaluates the FP64 pair weights once per call; workspace
+ *               grows by 8 (6r - 6) bytes per pixel, 16 for r = 1, and two
+ *               per-entry buffers).  For ill-conditioned
  *               settings (frac weights, large lambda: the FP32 weights
  *               alone move the exact solution by ~1e-3).  Needs step = 1 and
  *               kept factors (not factor_cache = 2); the batched,

@@ -2162,18 +2162,11 @@ __global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArg
 
 // ---------------------------------------------------------------------------
 // k_resid: the refinement's residual rho = f - A u for every entry of every
-// subsystem, with A rebuilt from the guidance in FP64 (Eq. 2, Eq. 4, Eq. 5)
-// and u the first solve's entries (xent).  A's row of entry e: diagonal
-// 1 + sum lambda w, off-diagonals -lambda w to the entries within r along
-// the vector.  Grid (ceil(nsys / 32), ceil(L / (4 lines x blockDim.y))),
-// block (32, G); lane = subsystem, each warp 4 lines.
-template <int R>
-__device__ __forceinline__ double weight64(const PassArgs& a, int jp, int t, double gp, double gq) {
-  const double dg = gp - gq;
-  const double rf = a.weight == 0 ? exp(-dg * dg * a.range64) : 1.0 / (pow(fabs(dg), a.range64) + a.eps64);
-  return a.sp64[jp * R + t - 1] * rf;   // lambda * w(p, p + t)
-}
-
+// subsystem, with A rebuilt in FP64 (Eq. 2, Eq. 4, Eq. 5) from the pair
+// weights of k_pairw64 and u the first solve's entries (xent).  A's row of
+// entry e: diagonal 1 + sum lambda w, off-diagonals -lambda w to the entries
+// within r along the vector.  Grid (ceil(nsys / 32), ceil(L / (4 lines x
+// blockDim.y))), block (32, G); lane = subsystem, each warp 4 lines.
 template <int R, int CC>
 __global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs a) {
   constexpr int n = 2 * R + 1;
@@ -2188,57 +2181,49 @@ __global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs 
   const long long s_len = (long long)a.L * n;
   const float* const xe = ent_lane<R, CC>(a, a.xent, sys);
   float* const re = ent_lane<R, CC>(a, a.rhs, sys);
-  // pixel of entry e (line e / n, snake order within the line)
-  auto pix = [&](long long e) {
+  // image coordinates of entry e (line e / n, snake order within the line)
+  auto coords = [&](long long e, int& x, int& y) {
     const int line = (int)(e / n), j = (int)(e - (long long)line * n);
     const int off = kc - R + ((line & 1) ? 2 * R - j : j);
-    return pix_index(a, line, off);
+    x = a.dir == 0 ? off : line;
+    y = a.dir == 0 ? line : off;
+  };
+  // lambda w of the pair (p, q), read from the canonical orientation
+  auto pair_w = [&](int xp, int yp, int xq, int yq) {
+    int dx = xq - xp, dy = yq - yp;
+    if (dy < 0 || (dy == 0 && dx < 0)) {
+      dx = -dx;
+      dy = -dy;
+      xp = xq;
+      yp = yq;
+    }
+    const int slot = a.pw_slot[dy * (2 * kRMax + 1) + dx + kRMax];
+    return __ldg(a.pw + ((long long)slot * a.H + yp) * a.W + xp);
   };
   const int l1 = min(l0 + LPW, a.L);
-  // each pair weight is computed once: wh[u][t-1] = lambda w(e-1-u, e-1-u+t)
-  // holds the forward weights of the previous r entries
-  double wh[R][R];
-  const long long e0 = (long long)l0 * n;
-  for (int u = 0; u < R; ++u)
-    for (int t = 1; t <= R; ++t) {
-      const long long p = e0 - 1 - u;
-      wh[u][t - 1] = (p >= 0 && p + t < s_len)
-                         ? weight64<R>(a, (int)(p % n), t, (double)ld_px(a.g, pix(p), a.g_dt),
-                                       (double)ld_px(a.g, pix(p + t), a.g_dt))
-                         : 0.0;
-    }
-  for (long long e = e0; e < (long long)l1 * n; ++e) {
-    const long long pe = pix(e);
-    const double ge = (double)ld_px(a.g, pe, a.g_dt);
-    const int je = (int)(e % n);
+  for (long long e = (long long)l0 * n; e < (long long)l1 * n; ++e) {
+    int xe_, ye_;
+    coords(e, xe_, ye_);
+    const long long pe = (long long)ye_ * a.W + xe_;
     double xv[CC], acc[CC];
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) {
       xv[ch] = (double)__ldcg(xe + (e * CC + ch) * 32);
       acc[ch] = (double)ld_px(plane_base<CC>(a, ch, a.in_dt == DT_F32 ? 4 : 2), pe, a.in_dt) - xv[ch];
     }
-    double wf[R];
 #pragma unroll
     for (int t = 1; t <= R; ++t) {
-      wf[t - 1] = 0.0;
-      if (e + t < s_len) {   // pair (e, e + t)
-        const double w = weight64<R>(a, je, t, ge, (double)ld_px(a.g, pix(e + t), a.g_dt));
-        wf[t - 1] = w;
 #pragma unroll
-        for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + ((e + t) * CC + ch) * 32));
-      }
-      if (e - t >= 0) {      // pair (e - t, e): entry e - t's forward weight at distance t
-        const double w = wh[t - 1][t - 1];
+      for (int side = 0; side < 2; ++side) {   // pairs (e, e + t) and (e - t, e)
+        const long long q = side == 0 ? e + t : e - t;
+        if (q < 0 || q >= s_len) continue;
+        int xq, yq;
+        coords(q, xq, yq);
+        const double w = pair_w(xe_, ye_, xq, yq);
 #pragma unroll
-        for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + ((e - t) * CC + ch) * 32));
+        for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + (q * CC + ch) * 32));
       }
     }
-#pragma unroll
-    for (int u = R - 1; u > 0; --u)
-#pragma unroll
-      for (int t = 0; t < R; ++t) wh[u][t] = wh[u - 1][t];
-#pragma unroll
-    for (int t = 0; t < R; ++t) wh[0][t] = wf[t];
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) re[(e * CC + ch) * 32] = (float)acc[ch];
   }

@@ -61,6 +61,38 @@ def test_refine_exp_weights(api, r, C):
         assert err <= TOL, (axis_order, chunk_lines, err)
 
 
+@pytest.mark.parametrize("r", [2, 3])
+def test_refine_frac_larger_radius(api, r):
+    """The frac-weight setting at r = 2, 3: the residual's pairs that cross
+    the snake's turn (pixel offsets (d, 1) with |d| < r) in both pass
+    orders."""
+    F = synth.rgb_scene(45, 58, seed=70 + r, n_rect=15, n_disk=4)
+    G = synth.luminance(F)
+    for axis_order in (0, 1):
+        kw = dict(r=r, iters=1, axis_order=axis_order, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+        prm = Params(r=r, iters=1, axis_order=axis_order, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+        ref = sgwls(F.astype(np.float64), G.astype(np.float64), 40.0, prm)
+        err = float(np.abs(_run(api, F, G, 40.0, refine=1, **kw) - ref).max())
+        assert err <= TOL, (axis_order, err)
+
+
+def test_refine_single_pass_entry(api):
+    """sgwls_filter_pass with refine = 1, both directions."""
+    import torch
+    from oracle import sgwls_pass, COLUMN, ROW
+    F = synth.rgb_scene(41, 66, seed=77, n_rect=12, n_disk=3)
+    G = synth.luminance(F)
+    f = torch.from_numpy(F).cuda()
+    g = torch.from_numpy(G).cuda()
+    prm = Params(r=2, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+    for direction, d in ((0, COLUMN), (1, ROW)):
+        u = api.sgwls_filter_pass(f, g, 40.0, direction, r=2, refine=1, weight="frac", alpha_s=1.2,
+                                  alpha_r=1.2, eps=1e-4)
+        torch.cuda.synchronize()
+        ref = sgwls_pass(F.astype(np.float64), G.astype(np.float64), 40.0, prm, d)
+        assert float(np.abs(u.cpu().numpy() - ref).max()) <= TOL, direction
+
+
 def test_refine_unsupported_paths(api):
     import torch
     F = synth.rgb_scene(30, 40, seed=3, n_rect=5, n_disk=1)
