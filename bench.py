@@ -608,6 +608,31 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     out["rgb_guidance"] = {"workload": WL["name"] + " guided by the RGB image itself (3 guidance planes)",
                            "value": mp2 / (ms_c / 1e3), "unit": UNIT, "ms_per_step": ms_c}
     del fr_, gr_, uc
+
+    # larger neighbourhoods: 1920 x 1080 RGB, luminance guidance, T = 2,
+    # lambda = 1, r = 2, 3, 5; FP32 storage, BF16 storage (FP32 elimination)
+    # and FP32 with the refinement (MP/s per iteration)
+    F4 = synth.rgb_scene(1080, 1920, seed=3)
+    G4 = synth.luminance(F4)
+    f4 = torch.from_numpy(F4).to(dev)
+    g4 = torch.from_numpy(G4).to(dev)
+    f4b, g4b = f4.to(torch.bfloat16), g4.to(torch.bfloat16)
+    u4, u4b = torch.empty_like(f4), torch.empty_like(f4b)
+    mp4 = 1920 * 1080 / 1e6 * 2
+    big = {}
+    for r in (2, 3, 5):
+        kw4 = dict(r=r, iters=2, sigma_r=0.1)
+        row = {}
+        for name, fi, gi, uu, extra in (("f32", f4, g4, u4, {}), ("bf16", f4b, g4b, u4b, {}),
+                                        ("f32_refine", f4, g4, u4, {"refine": 1})):
+            def one(i, fi=fi, gi=gi, uu=uu, extra=extra, kw4=kw4):
+                sg.sgwls_filter(fi, gi, 1.0, out=uu, stream=stream, **kw4, **extra)
+            ms = _timed(one, 3, 1, flush, stream) / 3
+            row[name] = {"value": mp4 / (ms / 1e3), "ms_per_step": ms}
+        big[f"r{r}"] = row
+    out["rgb1920x1080_T2"] = {"workload": "1920x1080 RGB, luminance guidance, T=2, lambda=1, r=2/3/5: FP32, "
+                                          "BF16 storage, FP32 with refinement", "unit": UNIT, "by_r": big}
+    del f4, g4, f4b, g4b, u4, u4b
     return out
 
 

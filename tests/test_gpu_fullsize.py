@@ -76,3 +76,36 @@ def test_large_image_pass_sampled(api, direction):
     got = U[:, :, offsets].transpose(0, 2, 1) if direction == COLUMN else U[:, offsets, :]
     err = float(np.abs(got - ref).max())
     assert err <= TOL, err
+
+
+@pytest.mark.parametrize("r", [2, 3, 5])
+def test_fullsize_pass_bf16_and_refined(api, scene, r):
+    """1920 x 1080 RGB, one column pass per r: BF16 storage (against the
+    oracle on the same BF16-rounded planes: one BF16 rounding of the output,
+    2^-9, plus the FP32 bound) and the refined FP32 pass, on sampled
+    offsets."""
+    import torch
+    F, G = scene
+    C, H, W = F.shape
+    rng = np.random.default_rng(300 + r)
+    offsets = sorted({0, r, 31, 32, W // 2, W - 1 - r, W - 1, *rng.integers(0, W, size=3).tolist()})
+    prm = Params(r=r, iters=1, sigma_s=float(r), sigma_r=0.1)
+
+    def sampled(u):
+        U = u.float().cpu().numpy().astype(np.float64)
+        return U[:, :, offsets].transpose(0, 2, 1)
+
+    fb = torch.from_numpy(F).cuda().to(torch.bfloat16)
+    gb = torch.from_numpy(G).cuda().to(torch.bfloat16)
+    ub = api.sgwls_filter_pass(fb, gb, 1.0, 0, r=r, sigma_r=0.1)
+    torch.cuda.synchronize()
+    Fb = fb.float().cpu().numpy().astype(np.float64)
+    Gb = gb.float().cpu().numpy().astype(np.float64)
+    ref_b = oracle_pass_offsets(Fb, Gb, 1.0, prm, COLUMN, offsets)
+    assert float(np.abs(sampled(ub) - ref_b).max()) <= 2.0 ** -9 + TOL
+
+    uf = api.sgwls_filter_pass(torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda(), 1.0, 0, r=r,
+                               sigma_r=0.1, refine=1)
+    torch.cuda.synchronize()
+    ref = oracle_pass_offsets(F, G, 1.0, prm, COLUMN, offsets)
+    assert float(np.abs(sampled(uf) - ref).max()) <= TOL
