@@ -40,6 +40,13 @@ if ROOT not in sys.path:
 METRIC = "megapixels/s per SG-WLS iteration (fwd) at max-abs err <= 2e-4 vs FP64"
 UNIT = "MP/s/iter"
 WL = dict(name="rgb1024x768_r1_T3", H=768, W=1024, C=3, r=1, iters=3, lams=(0.5, 2.0), sigma_r=0.1, seed=2)
+# DRAM bytes (read + write) of one row / column pass of this workload,
+# k_summary plus k_backsub, from an ncu capture of dram__bytes_read.sum and
+# dram__bytes_write.sum between back-to-back filters (--cache-control none;
+# the mean of 6 passes each; profiles/pass_kernels_rgb1024x768_r1.md).
+# Must be taken again whenever either kernel changes.
+ROW_PASS_DRAM_BYTES = 24.49e6
+COL_PASS_DRAM_BYTES = 30.34e6
 FALLBACK_HBM_GBS = 6800.0
 REF_CROP_ROWS = 192
 
@@ -408,7 +415,7 @@ def run_ours(args):
     achieved = bytes_per_pass / (dom_ms / 1e3) / 1e9
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": None,
+        "traffic": ROW_PASS_DRAM_BYTES if row_ms >= col_ms else COL_PASS_DRAM_BYTES,
         "kernel": "row pass" if row_ms >= col_ms else "column pass",
         "peak_source": f"{peak_kind} hbm_gbs",
         "pass_ms": {"column": col_ms, "row": row_ms},
