@@ -84,6 +84,8 @@ def test_validation_before_any_launch(capi):
     assert _call(capi, H=2, p=capi.make_params(r=1)) == E_SHAPE
     assert _call(capi, W=4, p=capi.make_params(r=2)) == E_SHAPE
     assert _call(capi, C=0) == E_SHAPE
+    assert _call(capi, H=65537, W=5) == E_SHAPE            # longest side 65536
+    assert _call(capi, H=32768, W=32768) == E_SHAPE        # more than 2^29 pixels
     for field, val in (("r", 0), ("r", 9), ("iters", -1), ("step", 0), ("axis_order", 2),
                        ("weight", 5), ("sigma_r", 0.0), ("chunk_lines", -2),
                        ("factor_cache", 3), ("factor_cache", -1)):

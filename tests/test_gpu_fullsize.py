@@ -109,3 +109,31 @@ def test_fullsize_pass_bf16_and_refined(api, scene, r):
     torch.cuda.synchronize()
     ref = oracle_pass_offsets(F, G, 1.0, prm, COLUMN, offsets)
     assert float(np.abs(sampled(uf) - ref).max()) <= TOL
+
+
+@pytest.mark.parametrize("shape", [(65536, 5), (7, 65536)])
+def test_maximum_side_length(api, shape):
+    """The longest side the library accepts (65536) on a thin image: one
+    pass per direction, against the oracle on the whole pass where it has
+    few subsystems and on sampled offsets where it has ~65k."""
+    import torch
+    from oracle import ROW, sgwls_pass
+    H, W = shape
+    rng = np.random.default_rng(H + W)
+    F = rng.uniform(0, 1, size=(2, H, W)).astype(np.float32)
+    G = rng.uniform(0, 1, size=(H, W)).astype(np.float32)
+    prm = Params(r=1, iters=1, sigma_s=1.0, sigma_r=0.3)
+    f, g = torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda()
+    for direction, d in ((0, COLUMN), (1, ROW)):
+        u = api.sgwls_filter_pass(f, g, 2.0, direction, r=1, sigma_r=0.3)
+        torch.cuda.synchronize()
+        U = u.cpu().numpy().astype(np.float64)
+        dim = W if direction == 0 else H
+        if dim <= 64:
+            ref = sgwls_pass(F.astype(np.float64), G.astype(np.float64), 2.0, prm, d)
+            assert float(np.abs(U - ref).max()) <= TOL, direction
+        else:
+            offsets = [0, 1, 2, 31, 32, 33, 4097, dim // 2, dim - 3, dim - 2, dim - 1]
+            ref = oracle_pass_offsets(F, G, 2.0, prm, d, offsets)
+            got = U[:, :, offsets].transpose(0, 2, 1) if direction == 0 else U[:, offsets, :]
+            assert float(np.abs(got - ref).max()) <= TOL, direction
