@@ -49,7 +49,8 @@ typedef enum {
   SGWLS_E_DTYPE = -3,       /* unknown storage type                              */
   SGWLS_E_WORKSPACE = -4,   /* workspace missing or smaller than required        */
   SGWLS_E_CUDA = -5,        /* a CUDA call failed (see sgwls_last_cuda_error)    */
-  SGWLS_E_DEVICE_FLAG = -6, /* a kernel reported an internal error flag          */
+  SGWLS_E_DEVICE_FLAG = -6, /* reserved: a kernel error flag (no kernel of this
+                               build waits on another or sets one)             */
   SGWLS_E_UNSUPPORTED = -7  /* valid request this build does not implement       */
 } sgwls_status;
 
