@@ -55,6 +55,8 @@ def _units():
     for r in RADII:
         for cc in GROUPS:
             units.append((inst, f"sgwls_inst_r{r}_c{cc}", [f"-DSGWLS_R={r}", f"-DSGWLS_CC={cc}"], r))
+    # the backward's widest group at r = 1: u and v of three channels
+    units.append((inst, "sgwls_inst_r1_c6", ["-DSGWLS_R=1", "-DSGWLS_CC=6"], 1))
     return units
 
 

@@ -418,6 +418,8 @@ sgwls_status copy_image(const void* src, int sdt, void* dst, int ddt, long long 
       default: return cudaErrorInvalidValue;                                     \
     }
 cudaError_t launch_pass_any(int r, int CC, const PassArgs& a, const Plan& pl, cudaStream_t st) {
+  // the backward's six right-hand sides (u and v of three channels): r = 1
+  if (CC == -kBwdWideRhs) return r == 1 ? launch_pass_inst<1, kBwdWideRhs>(a, pl, true, st) : cudaErrorInvalidValue;
   switch (r) {
     SGWLS_CASE_CC(1) SGWLS_CASE_CC(2) SGWLS_CASE_CC(3) SGWLS_CASE_CC(4)
     SGWLS_CASE_CC(5) SGWLS_CASE_CC(6) SGWLS_CASE_CC(7) SGWLS_CASE_CC(8)
@@ -867,23 +869,26 @@ struct BwdLayout {
   size_t img0, img1, gbuf, summ, xsep, mdata, cnt, total;
 };
 
+// Channels per backward group (u and v of each solved against one factor):
+// three at r = 1 (six right-hand sides), two otherwise.
+int bwd_group(int r) { return r == 1 ? kBwdWideRhs / 2 : 2; }
+
 BwdLayout make_bwd_layout(int H, int W, int C, const sgwls_params* p) {
   const int r = p->r;
-  const int nch = std::min(C, 2);
+  const int gch = bwd_group(r);
   size_t summ = 0, xsep = 0, mdata = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
     const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
-    for (int c0 = 0; c0 < C; c0 += 2) {
-      const int CC = 2 * std::min(2, C - c0);
+    for (int c0 = 0; c0 < C; c0 += gch) {
+      const int CC = 2 * std::min(gch, C - c0);
       const Plan pl = make_plan(L, D, r, CC, p->chunk_lines, true);
       summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
       xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
       mdata = std::max(mdata, (size_t)pl.NG * std::max(pl.G - 1, 1) * n_mfields(r, CC) * nsys * sizeof(float));
     }
   }
-  (void)nch;
   const size_t img = align256((size_t)C * H * W * sizeof(float));
   BwdLayout lo;
   lo.img0 = 0;
@@ -966,8 +971,9 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
     a.grad_g = grad_g;
     a.grad_lam = grad_lam;
     fill_weights(a, p, lambda);
-    for (int c0 = 0; c0 < C; c0 += 2) {
-      const int nch = std::min(2, C - c0);
+    const int gch = bwd_group(p->r);
+    for (int c0 = 0; c0 < C; c0 += gch) {
+      const int nch = std::min(gch, C - c0);
       const Plan pl = make_plan(a.L, a.D, p->r, 2 * nch, p->chunk_lines, true);
       a.h = pl.h;
       a.P = pl.P;

@@ -22,6 +22,7 @@ namespace sgwls {
 
 constexpr int kRMax = 8;
 constexpr int kGroupMax = 4;   // channels solved together against one factor
+constexpr int kBwdWideRhs = 6; // right-hand sides of the backward's widest group (r = 1)
 
 enum : int { DT_F32 = 0, DT_BF16 = 1 };
 

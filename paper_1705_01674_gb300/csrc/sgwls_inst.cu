@@ -1,5 +1,7 @@
 // One (radius, channel group) of the SG-WLS pass kernels.  build.py compiles
-// this file once per pair with SGWLS_R (1..8) and SGWLS_CC (1..4) defined;
+// this file once per pair with SGWLS_R (1..8) and SGWLS_CC (1..4) defined,
+// and once with SGWLS_R = 1, SGWLS_CC = 6 (the backward's u and v of three
+// channels, backward kernels only);
 // with SGWLS_STUB_RADIUS the launchers only report "not supported" (the
 // development shortcut that builds a subset of the radii).
 #include "sgwls_launch.cuh"
@@ -18,10 +20,12 @@ cudaError_t launch_pass_inst(const PassArgs& a, const Plan& pl, bool bwd, cudaSt
 #else
   if (bwd) {
     // the backward solves u and v together: an even number of right-hand sides
-    if constexpr (CC == 2 || CC == 4) return launch_pass_rc<R, CC, true>(a, pl, st);
+    if constexpr (CC % 2 == 0) return launch_pass_rc<R, CC, true>(a, pl, st);
     return cudaErrorInvalidValue;
   }
-  return launch_pass_rc<R, CC, false>(a, pl, st);
+  // more than kGroupMax right-hand sides: the backward's wide group only
+  if constexpr (CC <= kGroupMax) return launch_pass_rc<R, CC, false>(a, pl, st);
+  return cudaErrorInvalidValue;
 #endif
 }
 
@@ -36,6 +40,8 @@ cudaError_t launch_batch_inst(const BatchArgs& ba, const BatchLaunch& bl, cudaSt
 }
 
 template cudaError_t launch_pass_inst<SGWLS_R, SGWLS_CC>(const PassArgs&, const Plan&, bool, cudaStream_t);
+#if SGWLS_CC <= 4
 template cudaError_t launch_batch_inst<SGWLS_R, SGWLS_CC>(const BatchArgs&, const BatchLaunch&, cudaStream_t);
+#endif
 
 }  // namespace sgwls

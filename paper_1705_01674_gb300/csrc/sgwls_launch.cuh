@@ -116,8 +116,13 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
     const size_t chain = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
     b.chain_smem = (pl.NG > 1 && chain <= kReducedSmemMax) ? 1 : 0;
     const size_t smem = b.chain_smem ? std::max(pl.smem_sum, chain) : pl.smem_sum;
-    auto ks = (!BWD && b.rhs) ? k_summary<R, CC, 2>
-                              : (!b.fac ? k_summary<R, CC, 0> : (a.gc > 1 ? k_summary<R, CC, 3> : k_summary<R, CC, 1>));
+    void (*ks)(PassArgs) = k_summary<R, CC, 0>;
+    if constexpr (!BWD) {
+      if (b.rhs)
+        ks = k_summary<R, CC, 2>;
+      else if (b.fac)
+        ks = a.gc > 1 ? k_summary<R, CC, 3> : k_summary<R, CC, 1>;
+    }
     if ((e = set_smem(ks, smem)) != cudaSuccess) return e;
     e = launch_pdl(ks, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), smem, st, b);
     if (e != cudaSuccess) return e;
