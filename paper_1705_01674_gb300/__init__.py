@@ -38,6 +38,14 @@ def _check_tensor(x: torch.Tensor, name: str):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _check_like(x: torch.Tensor, ref: torch.Tensor, name: str):
+    """x must be a contiguous CUDA tensor with ref's shape and dtype (the
+    library writes exactly that many elements)."""
+    _check_tensor(x, name)
+    if x.shape != ref.shape or x.dtype != ref.dtype:
+        raise ValueError(f"{name} must have shape {tuple(ref.shape)} and dtype {ref.dtype}")
+
+
 def _chw(f: torch.Tensor):
     if f.dim() == 2:
         return 1, f.shape[0], f.shape[1]
@@ -86,7 +94,12 @@ def sgwls_filter(f: torch.Tensor, g: torch.Tensor, lam: float, *, out: torch.Ten
     if out is None:
         out = torch.empty_like(f)
     else:
-        _check_tensor(out, "out")
+        _check_like(out, f, "out")
+    if saved is not None:
+        _check_tensor(saved, "saved")
+        sdt = torch.bfloat16 if p.inter_storage == _capi.BF16 else torch.float32
+        if saved.dtype != sdt or saved.numel() < 2 * p.iters * C * H * W:
+            raise ValueError(f"saved must hold 2*iters*C*H*W = {2 * p.iters * C * H * W} elements of {sdt}")
     nws = lib.sgwls_workspace_bytes(H, W, C, ctypes.byref(p))
     if workspace is None or workspace.numel() < nws:
         workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=f.device)
@@ -122,7 +135,7 @@ def sgwls_interpolate(f: torch.Tensor, hmap: torch.Tensor, g: torch.Tensor, lam:
     if out is None:
         out = torch.empty_like(f)
     else:
-        _check_tensor(out, "out")
+        _check_like(out, f, "out")
     nws = lib.sgwls_interpolate_workspace_bytes(H, W, C, ctypes.byref(p))
     if workspace is None or workspace.numel() < nws:
         workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=f.device)
@@ -151,6 +164,8 @@ def sgwls_filter_pass(f: torch.Tensor, g: torch.Tensor, lam: float, direction: i
     lib = _capi.lib()
     if out is None:
         out = torch.empty_like(f)
+    else:
+        _check_like(out, f, "out")
     nws = lib.sgwls_workspace_bytes(H, W, C, ctypes.byref(p))
     if workspace is None or workspace.numel() < nws:
         workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=f.device)
@@ -181,7 +196,11 @@ def sgwls_filter_backward(grad_u: torch.Tensor, g: torch.Tensor, saved: torch.Te
         if x.dtype != torch.float32:
             raise TypeError(f"{name} must be float32 for the backward")
     C, H, W = _chw(grad_u)
+    if tuple(g.shape) != (H, W):
+        raise ValueError("g must be (H, W): the backward takes a single guidance plane")
     p = make_params(**kw)
+    if saved.numel() < 2 * p.iters * C * H * W:
+        raise ValueError(f"saved must hold 2*iters*C*H*W = {2 * p.iters * C * H * W} elements")
     lib = _capi.lib()
     grad_f = torch.empty_like(grad_u)
     grad_g = torch.empty((H, W), dtype=torch.float32, device=grad_u.device)
@@ -244,6 +263,8 @@ def _image_table(fs, gs, lams, outs):
         C, H, W = _chw(f)
         if tuple(g.shape) != (H, W) or g.dtype != f.dtype:
             raise ValueError(f"gs[{i}] must be (H, W) with the dtype of fs[{i}]")
+        if u is not f:
+            _check_like(u, f, f"outs[{i}]")
         tab[i].f, tab[i].g, tab[i].u = f.data_ptr(), g.data_ptr(), u.data_ptr()
         tab[i].H, tab[i].W, tab[i].C = H, W, C
         tab[i].lam = float(lam)

@@ -214,3 +214,28 @@ def test_config_rgb_1024x768_full(api, lam, factor_cache):
         _FULL_REF[lam] = _oracle(F, G, lam, **kw)
     err = _maxerr(_gpu(api, F, G, lam, factor_cache=factor_cache, **kw), _FULL_REF[lam])
     assert err <= TOL, err
+
+
+def test_binding_rejects_mis_sized_buffers(api):
+    """The binding checks every buffer the library writes or reads by size
+    before the call: an output of the wrong shape or dtype, a checkpoint
+    buffer that is too small, a vector guidance for the backward."""
+    import torch
+    f = torch.from_numpy(synth.rgb_scene(20, 24, seed=1, n_rect=3, n_disk=1)).cuda()
+    g = f[0].contiguous()
+    with pytest.raises(ValueError):
+        api.sgwls_filter(f, g, 1.0, out=torch.empty((3, 20, 23), device="cuda"))
+    with pytest.raises(ValueError):
+        api.sgwls_filter(f, g, 1.0, out=torch.empty((3, 20, 24), device="cuda", dtype=torch.bfloat16))
+    with pytest.raises(ValueError):
+        api.sgwls_filter_pass(f, g, 1.0, 0, out=torch.empty((2, 20, 24), device="cuda"))
+    with pytest.raises(ValueError):
+        api.sgwls_filter(f, g, 1.0, iters=2, saved=torch.empty((3, 3, 20, 24), device="cuda"))
+    saved = torch.empty((2, 3, 20, 24), device="cuda")
+    api.sgwls_filter(f, g, 1.0, iters=1, saved=saved)
+    with pytest.raises(ValueError):
+        api.sgwls_filter_backward(torch.ones_like(f), f, saved, 1.0, iters=1)
+    with pytest.raises(ValueError):
+        api.sgwls_filter_backward(torch.ones_like(f), g, saved[:1], 1.0, iters=1)
+    with pytest.raises(ValueError):
+        api.sgwls_filter_batched([f], [g], [1.0], outs=[torch.empty((3, 20, 20), device="cuda")])
