@@ -99,3 +99,24 @@ def test_batched_cuda_graph(api):
     for x, lam, u in zip(new, lams, outs):
         ref = sgwls(x.astype(np.float64), x[0].astype(np.float64), lam, prm)
         assert float(np.abs(u.cpu().numpy().astype(np.float64) - ref).max()) <= TOL
+
+
+@pytest.mark.parametrize("inter", ["f32", "bf16"])
+def test_batched_bf16_storage(api, inter):
+    """BF16 inputs, guidance and outputs (FP32 elimination) in one batched
+    call: against the oracle on the same BF16-rounded planes, with one BF16
+    rounding per stored estimate (2^-9 for values in [0, 1]) per pass that
+    stores BF16, plus the FP32 bound."""
+    import torch
+    imgs, guides, lams = _batch(5, seed=61, lo=20, hi=80, C=3)
+    kw = dict(r=1, iters=2, sigma_r=0.1, inter_storage=inter)
+    fs = [torch.from_numpy(x).cuda().to(torch.bfloat16) for x in imgs]
+    gs = [torch.from_numpy(x).cuda().to(torch.bfloat16) for x in guides]
+    outs = api.sgwls_filter_batched(fs, gs, lams, **kw)
+    torch.cuda.synchronize()
+    stores = 1 if inter == "f32" else 4
+    prm = Params(r=1, iters=2, sigma_s=1.0, sigma_r=0.1)
+    for f, g, lam, u in zip(fs, gs, lams, outs):
+        ref = sgwls(f.float().cpu().numpy().astype(np.float64), g.float().cpu().numpy().astype(np.float64), lam, prm)
+        err = float(np.abs(u.float().cpu().numpy().astype(np.float64) - ref).max())
+        assert err <= stores * 2.0 ** -9 + TOL, (tuple(f.shape), err)

@@ -31,7 +31,7 @@ def _check(api, F, Hm, G, lam, **kw):
     u = api.sgwls_interpolate(torch.from_numpy(F).cuda(), torch.from_numpy(Hm).cuda(),
                               torch.from_numpy(G).cuda(), lam, **kw)
     torch.cuda.synchronize()
-    prm = Params(r=kw["r"], iters=kw["iters"], sigma_s=float(kw["r"]), sigma_r=kw["sigma_r"])
+    prm = Params(r=kw["r"], iters=kw["iters"], step=kw.get("step", 1), sigma_s=float(kw["r"]), sigma_r=kw["sigma_r"])
     U, N, D = sgwls_interpolate(F.astype(np.float64), Hm.astype(np.float64), G.astype(np.float64), lam, prm,
                                 return_parts=True)
     got = u.cpu().numpy().astype(np.float64).reshape(U.shape)
@@ -58,3 +58,11 @@ def test_colourisation_scribbles(api, C):
     F, Hm = synth.scribbles(57, 83, n=14, C=C, seed=30 + C)
     G = synth.luminance(synth.rgb_scene(57, 83, seed=30 + C, n_rect=12, n_disk=3))
     _check(api, F, Hm, G, 20.0, r=2, iters=3, sigma_r=0.05)
+
+
+def test_depth_upsampling_with_sliding_step(api):
+    """The paper's depth-upsampling setting r = 4 with sliding step 4
+    (Sec. 2.3), 4x grid, 73 x 90."""
+    F, Hm, _ = synth.sparse_depth(73, 90, factor=4, seed=44)
+    G = synth.luminance(synth.rgb_scene(73, 90, seed=44, n_rect=12, n_disk=3))
+    _check(api, F, Hm, G, 4.0, r=4, step=4, iters=2, sigma_r=0.1)
