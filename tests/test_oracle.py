@@ -367,3 +367,30 @@ def test_sampled_pass_offsets_match_whole_pass():
             got = oracle_pass_offsets(F, G, 1.3, prm, d, offs)
             ref = whole if d == ROW else whole.transpose(0, 2, 1)
             assert np.abs(got - ref).max() < 1e-12
+
+
+# --------------------------------- the BF16 tolerance's premise (reading D14)
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("weight", ["exp", "frac"])
+def test_pass_is_max_norm_nonexpansive(r, weight):
+    """A_s^-1 is entrywise non-negative with unit row sums (A_s is an
+    M-matrix with A_s 1 = 1), so every subsystem solve and hence every pass
+    (a convex average of solves) is non-expansive in the max norm: a
+    rounding of the stored estimate by e moves the next pass's output by at
+    most e.  The BF16 storage bound rests on this."""
+    rng = np.random.default_rng(7 * r + (weight == "frac"))
+    H, W = 9, 4 * r + 3
+    G = rng.uniform(0, 1, size=(H, W))
+    lam = 3.0 if weight == "exp" else 0.01
+    prm = Params(r=r, sigma_s=float(r), sigma_r=0.1, weight=weight)
+    rows, cols = neighbourhood_construction(COLUMN, r + 1, r, H, W)
+    Ainv = np.linalg.inv(_band_to_dense(subsystem_band(rows, cols, G, lam, prm), r))
+    assert Ainv.min() >= -1e-12
+    np.testing.assert_allclose(Ainv.sum(axis=1), 1.0, atol=1e-10)
+    for direction in (COLUMN, ROW):
+        for _ in range(3):
+            X = rng.uniform(0, 1, size=(2, H, W))
+            Y = X + rng.uniform(-1e-3, 1e-3, size=X.shape)
+            dx = np.abs(sgwls_pass(X, G, lam, prm, direction) - sgwls_pass(Y, G, lam, prm, direction)).max()
+            assert dx <= np.abs(X - Y).max() * (1 + 1e-9)
