@@ -120,3 +120,26 @@ def test_batched_bf16_storage(api, inter):
         ref = sgwls(f.float().cpu().numpy().astype(np.float64), g.float().cpu().numpy().astype(np.float64), lam, prm)
         err = float(np.abs(u.float().cpu().numpy().astype(np.float64) - ref).max())
         assert err <= stores * 2.0 ** -9 + TOL, (tuple(f.shape), err)
+
+
+def test_batched_full_uneven_workload(api):
+    """The full uneven workload (64 gray images, sides U[256, 2048], r = 2,
+    T = 2, lambda U[0.5, 4], guidance = input): the batched call equals the
+    single-image calls for every image, and the two smallest images match
+    the FP64 oracle over every pixel."""
+    import torch
+    imgs, lams = synth.batch_uneven_gray(n=64, seed=4)
+    kw = dict(r=2, iters=2, sigma_r=0.1)
+    fs = [torch.from_numpy(x).cuda() for x in imgs]
+    gs = [f[0] for f in fs]
+    outs = api.sgwls_filter_batched(fs, gs, lams, **kw)
+    torch.cuda.synchronize()
+    for f, g, lam, u in zip(fs, gs, lams, outs):
+        v = api.sgwls_filter(f, g, lam, **kw)
+        torch.cuda.synchronize()
+        assert float((u - v).abs().max()) <= TOL, tuple(f.shape)
+    prm = Params(r=2, iters=2, sigma_s=2.0, sigma_r=0.1)
+    for b in sorted(range(len(imgs)), key=lambda i: imgs[i].size)[:2]:
+        x = imgs[b].astype(np.float64)
+        ref = sgwls(x, x[0], lams[b], prm)
+        assert float(np.abs(outs[b].cpu().numpy().astype(np.float64) - ref).max()) <= TOL, x.shape
