@@ -22,7 +22,7 @@ from . import _capi
 from ._capi import SgwlsError, make_params
 
 __all__ = ["sgwls", "sgwls_filter", "sgwls_filter_pass", "sgwls_filter_backward", "sgwls_filter_batched",
-           "sgwls_interpolate",
+           "sgwls_interpolate", "sgwls_filter_sharded",
            "batched_workspace_bytes", "SGWLSFunction",
            "workspace_bytes", "launch_count", "make_params", "SgwlsError"]
 
@@ -297,3 +297,6 @@ def sgwls_filter_batched(fs, gs, lams, *, outs=None, workspace: torch.Tensor | N
                                       ctypes.c_size_t(workspace.numel()), ctypes.c_void_p(st.cuda_stream))
     _capi.check(status, "sgwls_filter_batched")
     return outs
+
+
+from .shard import sgwls_filter_sharded  # noqa: E402  (one image over several ranks)

@@ -61,3 +61,62 @@ def test_reference_arm_runs_on_rank_zero_only():
                           "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert res.returncode == 0, res.stderr[-2000:]
     assert res.stdout.strip() == ""
+
+
+_SHARD_CODE = r"""
+import json, os, sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch
+import torch.distributed as dist
+import synth
+from oracle import COLUMN, ROW, Params, sgwls, sgwls_pass
+from paper_1705_01674_gb300.shard import filter_sharded, split
+dist.init_process_group("gloo")
+rank, world = dist.get_rank(), dist.get_world_size()
+H, W, r, T, order = {H}, {W}, {r}, {T}, {order}
+F = synth.rgb_scene(H, W, seed=31, n_rect=10, n_disk=2)[:2].astype(np.float64)
+G = synth.luminance(synth.rgb_scene(H, W, seed=31, n_rect=10, n_disk=2)).astype(np.float64)
+prm = Params(r=r, iters=1, sigma_s=float(r), sigma_r=0.2)
+
+def oracle_pass(U, Gs, lam, d):
+    return torch.from_numpy(sgwls_pass(U.numpy(), Gs.numpy(), lam, prm, COLUMN if d == 0 else ROW))
+
+a, b = split(W, world)[rank]
+out = filter_sharded(torch.from_numpy(F[:, :, a:b].copy()), torch.from_numpy(G[:, a:b].copy()), 1.7, H, W,
+                     oracle_pass, r=r, iters=T, axis_order=order)
+ref = sgwls(F, G, 1.7, Params(r=r, iters=T, axis_order=order, sigma_s=float(r), sigma_r=0.2))
+err = float(np.abs(out.numpy() - ref[:, :, a:b]).max())
+print(json.dumps({{"rank": rank, "err": err, "cols": [a, b]}}))
+dist.destroy_process_group()
+"""
+
+
+@pytest.mark.parametrize("world,H,W,r,T,order", [
+    (2, 17, 23, 1, 2, 0),
+    (3, 14, 19, 2, 1, 1),     # strips narrower than the 2r halo: blocks from two ranks away
+    (3, 21, 30, 1, 2, 1),
+])
+def test_sharded_filter_equals_whole_image(world, H, W, r, T, order):
+    """One image split into column strips over gloo ranks: every pass runs
+    on each rank's strip plus a 2r halo, the ranks re-partition between
+    directions, and the stitched result equals the whole-image filter (the
+    oracle's pass is the per-rank compute here, on the CPU)."""
+    pytest.importorskip("torch")
+    port = _free_port()
+    code = _SHARD_CODE.format(root=ROOT, H=H, W=W, r=r, T=T, order=order)
+    procs = []
+    for rank in range(world):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=180)
+        assert p.returncode == 0, err[-3000:]
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    cols = sorted(tuple(d["cols"]) for d in outs)
+    assert cols[0][0] == 0 and cols[-1][1] == W and all(cols[i][1] == cols[i + 1][0] for i in range(world - 1))
+    for d in outs:
+        assert d["err"] < 1e-12, d
