@@ -101,6 +101,14 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _hbm_frac(mp_per_s_iter: float, bytes_per_px_iter: float) -> float:
+    """Fraction of the measured HBM copy bandwidth that mp_per_s_iter
+    megapixels/s per iteration moves at bytes_per_px_iter algorithmic bytes
+    per pixel per iteration (two passes)."""
+    peak, _ = _peaks()
+    return mp_per_s_iter * 1e6 * bytes_per_px_iter / (peak * 1e9)
+
+
 def _inputs(seed):
     import synth
     F = synth.rgb_scene(WL["H"], WL["W"], seed=seed)
@@ -506,6 +514,9 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     out["fwd_bwd"] = {"workload": "16 x RGB 512x512, r=1, T=3, loss sum((U - target)^2)",
                       "value": mp / (ms_fb / 1e3), "unit": UNIT, "ms_per_step": ms_fb,
                       "fwd_value": mp / (ms_f / 1e3)}
+    # per pass: forward 28 B/px (RGB FP32 + luminance), backward 48 B/px
+    # (checkpoint, guidance, u-bar in, f-bar out, g-bar read and written)
+    out["fwd_bwd"]["hbm_frac"] = _hbm_frac(out["fwd_bwd"]["value"], 2 * (28.0 + 48.0))
     del fs, ts, gs, saved
 
     # batched uneven sizes: one batched call vs. a loop of single calls
@@ -542,6 +553,7 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
                       "value": mpb / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b,
                       "graph_replay_value": mpb / (ms_g / 1e3),
                       "single_calls_value": mpb / (ms_s / 1e3), "speedup_vs_single_calls": ms_s / ms_b}
+    out["batched"]["hbm_frac"] = _hbm_frac(out["batched"]["value"], 2 * 12.0)   # gray FP32, guidance = input
     del bf, bg, bo, bws
 
     # BF16 storage of the main workload
@@ -648,6 +660,7 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
                 sg.sgwls_filter(fi, gi, 1.0, out=uu, stream=stream, **kw4, **extra)
             ms = _timed(one, 3, 1, flush, stream) / 3
             row[name] = {"value": mp4 / (ms / 1e3), "ms_per_step": ms}
+            row[name]["hbm_frac"] = _hbm_frac(row[name]["value"], 2 * (14.0 if name == "bf16" else 28.0))
         big[f"r{r}"] = row
     out["rgb1920x1080_T2"] = {"workload": "1920x1080 RGB, luminance guidance, T=2, lambda=1, r=2/3/5: FP32, "
                                           "BF16 storage, FP32 with refinement", "unit": UNIT, "by_r": big}
