@@ -42,6 +42,15 @@
 //   k_recover   the same without kept factors: it re-stages the tile and
 //               repeats the forward sweep into shared memory before the
 //               backward sweep (also the adjoint pass of the backward).
+//   k_resid     the refinement's residual f - A u for every vector entry,
+//               A's couplings read from the FP64 pair-weight table that the
+//               library fills once per call.
+//
+// Compile-time modes: k_summary keeps its factors or not, takes its
+// right-hand sides from the tile or from the refinement's residual, and
+// reads one guidance plane or several (the norm of the guidance
+// difference); k_backsub runs step 1, a sliding step > 1 (a lane per
+// centre, averaging through shared memory) or the refinement's two solves.
 //
 // The sweeps run one line of the vector at a time with the line's parity
 // (snake direction) and its first/last role fixed at compile time, so every
