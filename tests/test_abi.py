@@ -185,3 +185,45 @@ def test_refinement_workspace_counts_pair_slots(capi):
             nsys = (W - 2 * r + 31) // 32 * 32
             ent = H * (2 * r + 1) * C * nsys * 4
             assert n1 - n0 == 2 * a256(ent) + a256(len(canon) * H * W * 8), (r, C)
+
+
+def test_batched_validation_host_only(capi):
+    """sgwls_filter_batched and its workspace query reject bad image tables
+    on the host (the pointers here are never dereferenced)."""
+    lib = capi.lib()
+    E_INVALID, E_SHAPE, E_WS, E_UNSUP = -1, -2, -4, -7
+
+    def table(specs):
+        tab = (capi.SgwlsImage * len(specs))()
+        for i, sp in enumerate(specs):
+            d = dict(f=0x1000 * (3 * i + 1), g=0x1000 * (3 * i + 2), u=0x1000 * (3 * i + 3), H=64, W=80, C=1,
+                     lam=1.0, saved=None)
+            d.update(sp)
+            tab[i].f, tab[i].g, tab[i].u = d["f"], d["g"], d["u"]
+            tab[i].H, tab[i].W, tab[i].C, tab[i].lam, tab[i].saved = d["H"], d["W"], d["C"], d["lam"], d["saved"]
+        return tab
+
+    def call(specs, p=None, ws=0x100000, nws=1 << 30):
+        p = p if p is not None else capi.make_params(r=2, iters=2)
+        tab = table(specs)
+        return lib.sgwls_filter_batched(len(specs), tab, ctypes.byref(p), ctypes.c_void_p(ws), nws,
+                                        ctypes.c_void_p(0))
+
+    p = capi.make_params(r=2, iters=2)
+    good = table([{}, {"H": 100, "W": 33}])
+    assert lib.sgwls_batched_workspace_bytes(2, good, ctypes.byref(p)) > 0
+    assert lib.sgwls_filter_batched(0, good, ctypes.byref(p), ctypes.c_void_p(0x100000), 1 << 30,
+                                    ctypes.c_void_p(0)) == E_INVALID
+    assert call([{}, {"C": 2}]) == E_UNSUP                 # every image the same channel count
+    assert call([{"C": 5}]) == E_UNSUP                     # one channel group per batched call
+    assert call([{"C": 0}]) == E_SHAPE
+    assert call([{}, {"H": 4}]) == E_SHAPE                 # smaller than 2r+1
+    assert call([{"f": 0}]) == E_INVALID
+    assert call([{"u": 0x1000}]) == E_INVALID              # output aliases the input
+    assert call([{"lam": -1.0}]) == E_INVALID
+    assert call([{"lam": float("nan")}]) == E_INVALID
+    assert call([{"saved": 0x9000}]) == E_UNSUP            # no checkpoints in batched calls
+    assert call([{}], p=capi.make_params(r=9)) == E_INVALID
+    assert call([{}], p=capi.make_params(r=2, step=2)) == E_UNSUP
+    assert call([{}], nws=16) == E_WS
+    assert call([{}], ws=0x100010) == E_WS                 # misaligned workspace
