@@ -227,3 +227,28 @@ def test_batched_validation_host_only(capi):
     assert call([{}], p=capi.make_params(r=2, step=2)) == E_UNSUP
     assert call([{}], nws=16) == E_WS
     assert call([{}], ws=0x100010) == E_WS                 # misaligned workspace
+
+
+def test_backward_validation_host_only(capi):
+    """sgwls_filter_backward rejects bad arguments before any launch."""
+    lib = capi.lib()
+    E_INVALID, E_WS, E_UNSUP = -1, -4, -7
+
+    def call(gu=0x1000, g=0x2000, saved=0x3000, gf=0x4000, p=None, lam=1.0, ws=0x100000, nws=1 << 30):
+        p = p if p is not None else capi.make_params(r=1, iters=1)
+        return lib.sgwls_filter_backward(ctypes.c_void_p(gu), ctypes.c_void_p(g), ctypes.c_void_p(saved), 64, 64, 3,
+                                         ctypes.c_float(lam), ctypes.byref(p), ctypes.c_void_p(gf),
+                                         ctypes.c_void_p(0), None, ctypes.c_void_p(ws), nws, ctypes.c_void_p(0))
+
+    p = capi.make_params(r=1, iters=1)
+    assert lib.sgwls_backward_workspace_bytes(64, 64, 3, ctypes.byref(p)) > 0
+    assert call(gu=0) == E_INVALID
+    assert call(gf=0) == E_INVALID
+    assert call(gf=0x1000) == E_INVALID                  # grad_f aliases grad_u
+    assert call(saved=0) == E_INVALID                    # iters > 0 needs the checkpoints
+    assert call(lam=-2.0) == E_INVALID
+    assert call(p=capi.make_params(storage="bf16")) == E_UNSUP
+    assert call(p=capi.make_params(weight="frac", alpha_r=0.8)) == E_UNSUP   # |x|^alpha not differentiable at 0
+    assert call(p=capi.make_params(r=2, step=2)) == E_UNSUP
+    assert call(p=capi.make_params(refine=1)) == E_UNSUP
+    assert call(nws=64) == E_WS
