@@ -702,6 +702,8 @@ BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_pa
 
 sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) {
   if (B < 1 || !imgs || !p) return SGWLS_E_INVALID;
+  sgwls_status s0 = check_params(imgs[0].H, imgs[0].W, imgs[0].C, p);   // out-of-range values first
+  if (s0 != SGWLS_OK) return s0;
   // sliding step, refinement, vector guidance: single images
   if (p->step != 1 || p->refine || p->guide_channels > 1) return SGWLS_E_UNSUPPORTED;
   const int C = imgs[0].C;

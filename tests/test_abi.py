@@ -225,6 +225,9 @@ def test_batched_validation_host_only(capi):
     assert call([{"saved": 0x9000}]) == E_UNSUP            # no checkpoints in batched calls
     assert call([{}], p=capi.make_params(r=9)) == E_INVALID
     assert call([{}], p=capi.make_params(r=2, step=2)) == E_UNSUP
+    bad = capi.make_params(r=2)
+    bad.step = 0
+    assert call([{}], p=bad) == E_INVALID                  # out of range, not merely unsupported
     assert call([{}], nws=16) == E_WS
     assert call([{}], ws=0x100010) == E_WS                 # misaligned workspace
 
