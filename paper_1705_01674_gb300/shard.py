@@ -133,7 +133,9 @@ def filter_sharded(f_strip: torch.Tensor, g_strip: torch.Tensor, lam: float, H: 
 def sgwls_filter_sharded(f_strip: torch.Tensor, g_strip: torch.Tensor, lam: float, H: int, W: int, *,
                          group=None, **kw) -> torch.Tensor:
     """filter_sharded with the library's CUDA pass on every rank (CUDA
-    tensors; NCCL or any backend with point-to-point sends).  Keyword
+    tensors; NCCL or any backend with point-to-point sends; with NCCL each
+    rank sets its CUDA device before the process group's first call).
+    Every rank of the group takes part in every re-partition.  Keyword
     parameters as ``sgwls_filter``; the sliding step must be 1 (strips of
     a sliding-step pass would not share the whole image's centres)."""
     from . import sgwls_filter_pass
