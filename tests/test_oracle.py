@@ -274,13 +274,14 @@ def test_subsystem_solution_invariants(r):
 
 # ------------------------------------------------- Sec. 2.3, whole passes
 
-def _bruteforce_pass(U, G, lam, r, sigma_s, sigma_r, direction):
-    """Independent pass: explicit strip arrays, dense matrices, dense solve."""
+def _bruteforce_pass(U, G, lam, r, sigma_s, sigma_r, direction, centres=None):
+    """Independent pass: explicit strip arrays, dense matrices, dense solve;
+    `centres` (default: every r .. dim-1-r) lists the strips' centres."""
     C, H, W = U.shape
     acc = np.zeros_like(U)
     cnt = np.zeros((H, W))
     dim = W if direction == COLUMN else H
-    for k in range(r, dim - r):
+    for k in (range(r, dim - r) if centres is None else centres):
         if direction == COLUMN:
             rr, cc = np.mgrid[0:H, k - r:k + r + 1]
         else:
@@ -308,6 +309,31 @@ def test_pass_bruteforce_tiny(r, direction):
     got = sgwls_pass(U, G, 1.3, prm, direction)
     ref = _bruteforce_pass(U, G, 1.3, r, prm.sigma_s, prm.sigma_r, direction)
     np.testing.assert_allclose(got, ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("r,step,dim", [(1, 2, 8), (1, 3, 9), (2, 3, 12), (2, 5, 13)])
+@pytest.mark.parametrize("direction", [COLUMN, ROW])
+def test_sliding_step_pass_bruteforce(r, step, dim, direction):
+    """Sec. 2.3 with a sliding step: the centres r, r + tau, ... (and the
+    last centre dim-1-r when the stride misses it, so every line is
+    covered); each pixel averages the strips that contain it.  Checked
+    against the explicit brute-force pass on that centre list."""
+    rng = np.random.default_rng(50 + 10 * r + step)
+    H, W = (7, dim) if direction == COLUMN else (dim, 7)
+    U = rng.uniform(0, 1, size=(2, H, W))
+    G = rng.uniform(0, 1, size=(H, W))
+    prm = Params(r=r, step=step, sigma_s=float(r), sigma_r=0.25)
+    centres = list(range(r, dim - r, step))
+    if centres[-1] != dim - 1 - r:
+        centres.append(dim - 1 - r)
+    assert centre_indices(dim, r, step) == centres
+    got = sgwls_pass(U, G, 1.3, prm, direction)
+    ref = _bruteforce_pass(U, G, 1.3, r, prm.sigma_s, prm.sigma_r, direction, centres)
+    np.testing.assert_allclose(got, ref, atol=1e-13)
+    # invariants survive the sparser centre set: constants, the range, lambda = 0
+    np.testing.assert_allclose(sgwls_pass(np.full_like(U, 0.4), G, 1.3, prm, direction), 0.4, atol=1e-13)
+    assert got.min() >= U.min() - 1e-12 and got.max() <= U.max() + 1e-12
+    np.testing.assert_allclose(sgwls_pass(U, G, 0.0, prm, direction), U, atol=1e-14)
 
 
 @pytest.mark.parametrize("r", [1, 2])
