@@ -23,8 +23,9 @@
  * Stream     `stream` is a cudaStream_t passed as void* (NULL = legacy
  *            default stream).  Every call is asynchronous on that stream:
  *            results are ready when the stream has reached the call.
- * Aliasing   the output may not alias the input; the guidance may alias the
- *            input (guidance = input, as in the grayscale workloads).
+ * Aliasing   the output may alias neither the input nor the guidance
+ *            (SGWLS_E_INVALID); the guidance may alias the input (guidance =
+ *            input, as in the grayscale workloads).
  * Errors     arguments are validated on the host before anything is
  *            launched; a failed validation returns an SGWLS_E_* code and
  *            touches no memory.  A CUDA launch failure returns SGWLS_E_CUDA
@@ -146,7 +147,7 @@ size_t sgwls_workspace_bytes(int H, int W, int C, const sgwls_params* p);
  *   f       device, C x H x W input (storage type p->storage)
  *   g       device, H x W guidance (p->storage), or Cg x H x W with
  *           p->guide_channels = Cg > 1; may equal f when C == Cg
- *   u       device, C x H x W output (p->storage); must not alias f
+ *   u       device, C x H x W output (p->storage); must not alias f or g
  *   lambda  smoothness weight of Eq. 1 / Eq. 4, >= 0
  *   ws      device workspace of at least sgwls_workspace_bytes(H, W, C, p)
  *           bytes, 256-byte aligned; contents on entry are ignored
@@ -252,20 +253,26 @@ sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void
  * memory when they filter (a host with a fixed device-memory budget, or a
  * code path that must not enter the allocator): it takes no workspace.  The
  * paper has no counterpart; this is an interface convenience.
- *   Scratch: a file-scope device array of 16 MiB inside libsgwls.so, held by
- *   every GPU that loads the library until the process exits.  Requests
- *   whose scratch (sgwls_workspace_bytes with iters = 0) exceeds 16 MiB
- *   return SGWLS_E_WORKSPACE; e.g. RGB FP32 at r = 1 fits up to about
- *   1920 x 1080.
- *   Set-up: the first call on a device looks up the array's device address
- *   with that device current (cudaGetSymbolAddress) and keeps it; make that
- *   first call before any stream capture.
+ *   Scratch: a file-scope device array of 16 MiB inside libsgwls.so.
+ *   Requests whose scratch (sgwls_workspace_bytes with iters = 0 and
+ *   factor_cache = 2) exceeds 16 MiB return SGWLS_E_WORKSPACE; e.g. RGB FP32
+ *   at r = 1 fits up to about 1920 x 1080.
+ *   Set-up: the first call on a device loads the library's device code on
+ *   that device, which reserves the 16 MiB there (held until the process
+ *   exits), and looks up the array's device address with that device current
+ *   (cudaGetSymbolAddress); later calls reuse the address.  Callers under a
+ *   memory budget should therefore make one call per device during their own
+ *   set-up, and that first call must come before any stream capture.
  *   Sharing: all calls share the one array and leave their contents in it;
  *   each call clears the array's small block-counter region on its stream
  *   before its kernels (every other value the kernels read is written
  *   earlier in the same call); calls that overlap on the GPU (other streams,
  *   other host threads) race on it -- serialise them.
  *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *   Checks: the parameters are validated as sgwls_filter_pass validates them
+ *   (same codes); then step > 1, refine = 1, guide_channels > 1 and
+ *   factor_cache = 1 (kept factors, which the scratch cannot hold) return
+ *   SGWLS_E_UNSUPPORTED; u may alias neither f nor g.
  * Other arguments and results as sgwls_filter_pass. */
 sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, void* u, int H, int W, int C,
                                        float lambda, const sgwls_params* p, int direction, void* stream);

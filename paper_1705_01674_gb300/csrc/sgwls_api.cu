@@ -407,6 +407,14 @@ sgwls_status copy_image(const void* src, int sdt, void* dst, int ddt, long long 
 
 }  // namespace
 
+// Argument checks of a single pass, in the order sgwls_filter_pass applies
+// them (shared with the no-allocation pass so both return the same codes).
+sgwls_status check_pass_params(int H, int W, int C, const sgwls_params* p) {
+  sgwls_status s = check_params(H, W, C, p);
+  if (s == SGWLS_OK) s = check_step(H, W, C, p);
+  return s;
+}
+
 // Dispatch to the (radius, channel group) instantiations.
 #define SGWLS_CASE_CC(R)                                                         \
   case R:                                                                        \
@@ -1042,10 +1050,9 @@ size_t sgwls_workspace_bytes(int H, int W, int C, const sgwls_params* p) {
 
 sgwls_status sgwls_filter(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
                           const sgwls_params* p, void* ws, size_t ws_bytes, void* saved, void* stream) {
-  sgwls_status s = check_params(H, W, C, p);
-  if (s == SGWLS_OK) s = check_step(H, W, C, p);
+  const sgwls_status s = check_pass_params(H, W, C, p);
   if (s != SGWLS_OK) return s;
-  if (!f || !g || !u || f == u) return SGWLS_E_INVALID;
+  if (!f || !g || !u || f == u || g == u) return SGWLS_E_INVALID;
   if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
   const size_t need = make_layout(H, W, C, p).total;
   if (need > 0 && (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255))) return SGWLS_E_WORKSPACE;
@@ -1054,10 +1061,9 @@ sgwls_status sgwls_filter(const void* f, const void* g, void* u, int H, int W, i
 
 sgwls_status sgwls_filter_pass(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
                                const sgwls_params* p, int direction, void* ws, size_t ws_bytes, void* stream) {
-  sgwls_status s = check_params(H, W, C, p);
-  if (s == SGWLS_OK) s = check_step(H, W, C, p);
+  const sgwls_status s = check_pass_params(H, W, C, p);
   if (s != SGWLS_OK) return s;
-  if (!f || !g || !u || f == u) return SGWLS_E_INVALID;
+  if (!f || !g || !u || f == u || g == u) return SGWLS_E_INVALID;
   if (direction != 0 && direction != 1) return SGWLS_E_INVALID;
   if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
   const Layout lo = make_layout(H, W, C, p);

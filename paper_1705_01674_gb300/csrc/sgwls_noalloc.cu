@@ -15,6 +15,7 @@
 #include "sgwls_common.cuh"
 
 namespace sgwls {
+sgwls_status check_pass_params(int H, int W, int C, const sgwls_params* p);
 sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const void* g, int H, int W, int C,
                       float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st, bool zero_counters);
 }
@@ -50,24 +51,27 @@ sgwls_status scratch_for_current_device(void** out) {
 extern "C" sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, void* u, int H, int W, int C,
                                                    float lambda, const sgwls_params* p, int direction,
                                                    void* stream) {
-  if (!p) return SGWLS_E_INVALID;
-  // the sliding step tau > 1 runs on kept chunk factors, which this scratch does not hold
-  if (p->step != 1) return (p->step >= 1 && p->step <= 2 * p->r + 1) ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;
-  if (p->refine) return p->refine == 1 ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;   // needs kept factors
-  if (p->guide_channels > 1)   // a vector guidance also runs on kept factors
-    return p->guide_channels <= SGWLS_GUIDE_MAX ? SGWLS_E_UNSUPPORTED : SGWLS_E_INVALID;
-  // a pass needs no intermediate image: size the scratch as for iters == 0
+  // the caller's parameters are checked exactly as sgwls_filter_pass checks
+  // them, so both entry points return the same code for the same mistake
+  sgwls_status s = sgwls::check_pass_params(H, W, C, p);
+  if (s != SGWLS_OK) return s;
+  // kept chunk factors (needed by a sliding step > 1, the refinement and a
+  // vector guidance) do not fit this scratch
+  if (p->step != 1 || p->refine || p->guide_channels > 1 || p->factor_cache == 1) return SGWLS_E_UNSUPPORTED;
+  // u is written while other blocks of the same kernel still read f and g
+  if (!f || !g || !u || f == u || g == u) return SGWLS_E_INVALID;
+  if (direction != 0 && direction != 1) return SGWLS_E_INVALID;
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
+  // a pass needs no intermediate image: size the scratch as for iters == 0,
+  // with the chunk factors recomputed rather than kept
   sgwls_params q = *p;
   q.iters = 0;
-  q.factor_cache = 2;   // the chunk factors are recomputed, not kept in the scratch
+  q.factor_cache = 2;
   const size_t need = sgwls_workspace_bytes(H, W, C, &q);
   if (need == 0) return SGWLS_E_INVALID;
   if (need > kNoAllocScratchBytes) return SGWLS_E_WORKSPACE;
-  if (!f || !g || !u || f == u) return SGWLS_E_INVALID;
-  if (direction != 0 && direction != 1) return SGWLS_E_INVALID;
-  if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
   void* ws = nullptr;
-  const sgwls_status s = scratch_for_current_device(&ws);
+  s = scratch_for_current_device(&ws);
   if (s != SGWLS_OK) return s;
   return sgwls::run_pass(f, q.storage, u, q.storage, g, H, W, C, lambda, &q, direction, ws,
                          static_cast<cudaStream_t>(stream), true);

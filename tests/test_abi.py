@@ -255,3 +255,46 @@ def test_backward_validation_host_only(capi):
     assert call(p=capi.make_params(r=2, step=2)) == E_UNSUP
     assert call(p=capi.make_params(refine=1)) == E_UNSUP
     assert call(nws=64) == E_WS
+
+
+def test_noalloc_validation_matches_workspace_pass(capi):
+    """The no-allocation pass validates the caller's parameters exactly as
+    sgwls_filter_pass does (same status for the same mistake), and both
+    reject an output that aliases the input or the guidance; the pointers
+    are never dereferenced because every case fails on the host."""
+    lib = capi.lib()
+    E_INVALID, E_SHAPE, E_DTYPE, E_UNSUP = -1, -2, -3, -7
+
+    def both(p, H=64, W=80, C=3, f=0x1000, g=0x2000, u=0x3000, lam=1.0, direction=0):
+        a = lib.sgwls_filter_pass(ctypes.c_void_p(f), ctypes.c_void_p(g), ctypes.c_void_p(u), H, W, C,
+                                  ctypes.c_float(lam), ctypes.byref(p), direction, ctypes.c_void_p(0x100000),
+                                  1 << 30, ctypes.c_void_p(0))
+        b = lib.sgwls_filter_pass_noalloc(ctypes.c_void_p(f), ctypes.c_void_p(g), ctypes.c_void_p(u), H, W, C,
+                                          ctypes.c_float(lam), ctypes.byref(p), direction, ctypes.c_void_p(0))
+        return a, b
+
+    bad_dtype = capi.make_params(r=1)
+    bad_dtype.storage = 5
+    assert both(bad_dtype) == (E_DTYPE, E_DTYPE)
+    bad_inter = capi.make_params(r=1)
+    bad_inter.inter_storage = 9
+    assert both(bad_inter) == (E_DTYPE, E_DTYPE)
+    p = capi.make_params(r=2)
+    assert both(p, H=4) == (E_SHAPE, E_SHAPE)               # smaller than 2r + 1
+    assert both(p, C=0) == (E_SHAPE, E_SHAPE)
+    assert both(p, W=70000) == (E_SHAPE, E_SHAPE)
+    bad_fc = capi.make_params(r=1)
+    bad_fc.factor_cache = 7
+    assert both(bad_fc) == (E_INVALID, E_INVALID)            # out of range, not silently replaced
+    bad_r = capi.make_params(r=1)
+    bad_r.r = 0
+    assert both(bad_r) == (E_INVALID, E_INVALID)
+    assert both(p, u=0x1000) == (E_INVALID, E_INVALID)       # output aliases the input
+    assert both(p, u=0x2000) == (E_INVALID, E_INVALID)       # output aliases the guidance
+    assert both(p, lam=-1.0) == (E_INVALID, E_INVALID)
+    assert both(p, direction=2) == (E_INVALID, E_INVALID)
+    # kept factors do not fit the fixed scratch
+    st = lib.sgwls_filter_pass_noalloc(ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000),
+                                       64, 80, 3, ctypes.c_float(1.0),
+                                       ctypes.byref(capi.make_params(r=1, factor_cache=1)), 0, ctypes.c_void_p(0))
+    assert st == E_UNSUP

@@ -2,9 +2,14 @@
 
 Such callers (a host with a fixed device-memory budget, or a path that must
 not enter the allocator) get a pass whose scratch is a fixed device array
-inside the library.  This file is collected last; the test calls the entry
-point through the C ABI twice in a row and compares each result with the
-workspace-taking sgwls_filter_pass on the same inputs.
+inside the library.  This file is collected last.  The test calls the entry
+point through the C ABI twice in a row per case and compares each result
+with the FP64 oracle's pass (oracle.sgwls_pass) on the same inputs, so a
+fault shared with the workspace-taking pass cannot hide; a BF16-storage
+case is held to the BF16 bound (one rounding of the output, 2^-9 on [0, 1],
+plus the FP32 tolerance; the oracle filters the same BF16-rounded inputs).
+After a warm-up call, two more calls must leave the device's free memory
+unchanged.
 """
 import ctypes
 
@@ -16,37 +21,71 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-4
+BF16_TOL = 2.0 ** -9 + TOL
 
 
-def test_noalloc_pass_matches_workspace_pass():
+def _setup():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1705_01674_gb300 import build
     build.build()
-    import paper_1705_01674_gb300 as sg
     from paper_1705_01674_gb300 import _capi
+    return torch, _capi, _capi.lib()
 
-    lib = _capi.lib()
+
+def _call(lib, _capi, torch, f, g, u, lam, p, direction):
+    C, H, W = f.shape
     stream = torch.cuda.current_stream()
+    return lib.sgwls_filter_pass_noalloc(
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+        H, W, C, ctypes.c_float(lam), ctypes.byref(p), direction, ctypes.c_void_p(stream.cuda_stream))
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_noalloc_pass_matches_oracle(storage):
+    torch, _capi, lib = _setup()
+    from oracle import Params, sgwls_pass
+
     cases = [(0, synth.rgb_scene(96, 130, seed=21, n_rect=20, n_disk=4), 1.5, 1),
              (1, synth.rgb_scene(77, 101, seed=22, n_rect=15, n_disk=3), 0.7, 2)]
     for direction, F, lam, r in cases:
         G = synth.luminance(F)
-        f = torch.from_numpy(F).cuda()
-        g = torch.from_numpy(G).cuda()
-        C, H, W = f.shape
-        p = _capi.make_params(r=r, sigma_r=0.1)
-        u = torch.full_like(f, float("nan"))
-        st = lib.sgwls_filter_pass_noalloc(
-            ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(u.data_ptr()),
-            H, W, C, ctypes.c_float(lam), ctypes.byref(p), direction, ctypes.c_void_p(stream.cuda_stream))
-        assert st == 0, _capi.STATUS_NAMES.get(st, st)
-        ref = sg.sgwls_filter_pass(f, g, lam, direction, r=r, sigma_r=0.1)
-        torch.cuda.synchronize()
-        err = float((u - ref).abs().max())
-        assert err <= TOL, err
-        assert bool(torch.isfinite(u).all())
+        dt = torch.float32 if storage == "f32" else torch.bfloat16
+        f = torch.from_numpy(F).to(dt)
+        g = torch.from_numpy(G).to(dt)
+        F, G = f.float().numpy(), g.float().numpy()   # the values the GPU sees
+        f, g = f.cuda(), g.cuda()
+        p = _capi.make_params(r=r, sigma_r=0.1, storage=storage)
+        ref = sgwls_pass(F.astype(np.float64), G.astype(np.float64), lam,
+                         Params(r=r, sigma_s=float(r), sigma_r=0.1), direction)
+        tol = TOL if storage == "f32" else BF16_TOL
+        for _ in range(2):   # the second call finds the previous call's contents in the scratch
+            u = torch.full_like(f, float("nan"))
+            st = _call(lib, _capi, torch, f, g, u, lam, p, direction)
+            assert st == 0, _capi.STATUS_NAMES.get(st, st)
+            torch.cuda.synchronize()
+            got = u.float().cpu().numpy().astype(np.float64)
+            assert np.isfinite(got).all()
+            err = float(np.abs(got - ref).max())
+            assert err <= tol, (direction, r, storage, err)
+
+
+def test_noalloc_pass_allocates_nothing():
+    torch, _capi, lib = _setup()
+    F = synth.rgb_scene(120, 160, seed=23, n_rect=20, n_disk=4)
+    f = torch.from_numpy(F).cuda()
+    g = torch.from_numpy(synth.luminance(F)).cuda()
+    u = torch.empty_like(f)
+    p = _capi.make_params(r=1, sigma_r=0.1)
+    assert _call(lib, _capi, torch, f, g, u, 1.0, p, 0) == 0   # warm-up: loads the device code once
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for direction in (0, 1):
+        assert _call(lib, _capi, torch, f, g, u, 1.0, p, direction) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_rejects_oversized_request():
