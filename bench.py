@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """SG-WLS throughput on GB300: megapixels per second per SG-WLS iteration.
 
-Workload (default): one 1024 x 768 RGB synthetic scene (200 rectangles, 50
-disks, sinusoidal texture, noise), guidance = luminance, r = 1, T = 3
-iterations, range parameter 0.1, lambda alternating 0.5 / 2.0 between
-steps.  One step = one full SG-WLS filter (2T passes) of that image.
+Headline workload: one 1920 x 1080 RGB synthetic scene (200 rectangles, 50
+disks, sinusoidal texture, noise), guidance = luminance, r = 2, T = 2
+iterations, lambda = 1, range parameter 0.1, FP32.  One step = one full
+SG-WLS filter (2T passes) of that image.  The same line reports r = 3 and
+r = 5 on that image (`by_r`), the forward + backward of 16 RGB 512 x 512
+images (`fwd_bwd`), and the other workloads under `secondary`.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -12,19 +14,29 @@ Timing: W untimed steps, then K steps; before every timed step L2 is
 flushed by writing a 256 MiB buffer (outside the timed events); each step
 is bracketed by CUDA events on the stream it runs on.  `value` = megapixels
 x iterations / summed device time.  The roofline's per-pass duration comes
-from a second run of the same K steps with an event pair around every pass.  `e2e` repeats the measurement through
-the one-call API with pinned host buffers, every step's host->device and
-device->host copies inside the timed region (pipelined: the copies of the
-neighbouring steps overlap each filter, on their own streams).  With N > 1 (torchrun) every rank filters
-its own image (weak scaling, no collective on the data path); rank 0
-prints the max-over-ranks timing.
+from a second run of the same K steps with an event pair around every pass.
+`e2e` repeats the measurement through the one-call API with pinned host
+buffers, every step's host->device and device->host copies inside the timed
+region (pipelined: the copies of the neighbouring steps overlap each filter,
+on their own streams).  With N > 1 (torchrun) every rank filters its own
+image (weak scaling, no collective on the data path); rank 0 prints the
+max-over-ranks timing.
+
+Rooflines (per pass, the slower direction): HBM = algorithmic bytes (read
+the C estimate planes and the guidance, write the C output planes) over the
+pass time against the measured copy bandwidth; ALU = counted FP32 flops and
+MUFU operations of the method (Eq. 2 weights, the banded LDL^T, the
+substitutions and the averaging, per subsystem entry) over the pass time
+against the SM count x lanes x clock.
 
 `--impl reference` times the FP64 CPU oracle on this host's cores on a
-bounded sample of the same workload (a 1024 x 192 crop per step).
+bounded sample of the headline workload (a 1920 x 64 crop, one iteration,
+per step).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -37,18 +49,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "megapixels/s per SG-WLS iteration (fwd) at max-abs err <= 2e-4 vs FP64"
+METRIC = "megapixels/s per SG-WLS iteration (fwd, fwd+bwd) at max-abs err<=2e-4 vs FP64; % HBM roofline"
 UNIT = "MP/s/iter"
-WL = dict(name="rgb1024x768_r1_T3", H=768, W=1024, C=3, r=1, iters=3, lams=(0.5, 2.0), sigma_r=0.1, seed=2)
-# DRAM bytes (read + write) of one row / column pass of this workload,
-# k_summary plus k_backsub, from an ncu capture of dram__bytes_read.sum and
-# dram__bytes_write.sum between back-to-back filters (--cache-control none;
-# the mean of 6 passes each; profiles/pass_kernels_rgb1024x768_r1.md).
-# Must be taken again whenever either kernel changes.
-ROW_PASS_DRAM_BYTES = 24.49e6
-COL_PASS_DRAM_BYTES = 30.34e6
+WL = dict(name="rgb1920x1080_r2_T2", H=1080, W=1920, C=3, r=2, iters=2, lam=1.0, sigma_r=0.1, seed=3)
+EXTRA_R = (3, 5)
+# oracle samples (rows of the 1920-wide image, one iteration) per radius:
+# about 5 s of single-thread work each on the dev host
+CPU_CROP_ROWS = {1: 256, 2: 192, 3: 128, 5: 64}
+REF_CROP_ROWS = 64
+DIFF = dict(name="fwd_bwd_16xrgb512_r1_T3", n=16, H=512, W=512, r=1, iters=3, lam=1.0, sigma_r=0.1, seed=5)
 FALLBACK_HBM_GBS = 6800.0
-REF_CROP_ROWS = 192
+# GB300: 152 SMs, 128 FP32 lanes and 16 MUFU lanes per SM, at most 2070 MHz
+N_SM, FP32_LANES, MUFU_LANES, FALLBACK_SM_MHZ = 152, 128, 16, 2070.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_per_pass.txt")
 
 
 def _args():
@@ -92,45 +105,157 @@ def _job_value(world: int, mp_per_step: float, steps: int, total_ms: float) -> f
 
 
 def _peaks():
+    """(HBM GB/s, SM MHz, source) from the measured peaks file, else the
+    fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", FALLBACK_SM_MHZ)), "measured"
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, FALLBACK_SM_MHZ, "fallback"
 
 
 def _hbm_frac(mp_per_s_iter: float, bytes_per_px_iter: float) -> float:
     """Fraction of the measured HBM copy bandwidth that mp_per_s_iter
     megapixels/s per iteration moves at bytes_per_px_iter algorithmic bytes
     per pixel per iteration (two passes)."""
-    peak, _ = _peaks()
+    peak, _, _ = _peaks()
     return mp_per_s_iter * 1e6 * bytes_per_px_iter / (peak * 1e9)
 
 
-def _inputs(seed):
+# ---------------------------------------------------------------- work model
+
+def pass_bytes(H: int, W: int, C: int, elem: int = 4, g_elem: int = 4) -> int:
+    """Algorithmic bytes of one forward pass: read the C estimate planes and
+    the guidance, write the C output planes (the band, weights and factors
+    never need to touch HBM)."""
+    return H * W * (2 * C * elem + g_elem)
+
+
+def n_centres(D: int, r: int) -> int:
+    """Subsystems of one pass at sliding step 1: centres r .. D-1-r."""
+    return D - 2 * r
+
+
+def flops_per_entry(r: int, C: int) -> int:
+    """Counted FP32 flops per subsystem entry (an FMA counts 2): the r
+    forward pair weights of Eq. 2 (difference, square, scale, spatial
+    factor: 4 each), the diagonal 1 + sum of the 2r weights (2r adds), the
+    LDL^T row (r(r-1)/2 FMAs, r scalings, r FMAs for the pivot), forward
+    and backward substitution of C channels (r FMAs each way, C scalings by
+    the inverse pivot) and the accumulation of C averaged values."""
+    return 4 * r + 2 * r + (r * (r - 1) + r + 2 * r) + 2 * r * C + (2 * r * C + C) + C
+
+
+def mufu_per_entry(r: int) -> int:
+    """Counted MUFU operations per entry: r exponentials and one reciprocal."""
+    return r + 1
+
+
+def pass_work(H: int, W: int, C: int, r: int, direction: int):
+    """(flops, MUFU ops) of one pass: every centre's subsystem has (2r+1) L
+    entries."""
+    L, D = (H, W) if direction == 0 else (W, H)
+    ent = n_centres(D, r) * (2 * r + 1) * L
+    return ent * flops_per_entry(r, C), ent * mufu_per_entry(r)
+
+
+def alu_peaks(sm_mhz: float):
+    """FP32 flop/s (FMA = 2) and MUFU op/s of the whole GPU at sm_mhz."""
+    hz = sm_mhz * 1e6
+    return N_SM * FP32_LANES * 2 * hz, N_SM * MUFU_LANES * hz
+
+
+def source_hash() -> str:
+    """Hash of the CUDA sources: the DRAM counters in the traffic file are
+    valid only for the kernels they were taken from."""
+    csrc = os.path.join(ROOT, "paper_1705_01674_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, direction: str):
+    """DRAM bytes (read + write) of one pass of `workload` along `direction`
+    from the ncu summary file, or None when the file is missing, has no such
+    entry, or was taken from other kernel sources."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            lines = [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    kv = {tuple(x[:-1]): x[-1] for x in lines if len(x) >= 2}
+    if kv.get(("source_hash",)) != source_hash():
+        return None
+    v = kv.get((workload, direction))
+    return float(v) if v is not None else None
+
+
+def roofline_lines(H, W, C, r, col_ms, row_ms, workload, elem=4, g_elem=4):
+    """The HBM roofline of the slower pass direction, and its ALU roofline
+    (counted FP32 flops and MUFU operations)."""
+    peak, sm_mhz, kind = _peaks()
+    dom_ms, dom, d = (row_ms, "row", 1) if row_ms >= col_ms else (col_ms, "column", 0)
+    b = pass_bytes(H, W, C, elem, g_elem)
+    achieved = b / (dom_ms / 1e3) / 1e9
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": measured_traffic(workload, dom), "kernel": f"{dom} pass (k_summary + k_backsub)",
+           "peak_source": f"{kind} hbm_gbs", "pass_ms": {"column": col_ms, "row": row_ms},
+           "algorithmic_bytes_per_launch": b}
+    fl, mu = pass_work(H, W, C, r, d)
+    fpk, mpk = alu_peaks(sm_mhz)
+    fa, ma = fl / (dom_ms / 1e3), mu / (dom_ms / 1e3)
+    alu = {"bound": "alu", "achieved": fa / 1e12, "peak": fpk / 1e12, "unit": "TFLOP/s", "frac": fa / fpk,
+           "mufu_achieved": ma / 1e12, "mufu_peak": mpk / 1e12, "mufu_unit": "Tops/s", "mufu_frac": ma / mpk,
+           "kernel": f"{dom} pass", "flops_per_launch": fl, "mufu_per_launch": mu,
+           "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 (FMA) / {MUFU_LANES} MUFU lanes at "
+                          f"{sm_mhz:.0f} MHz ({kind} sm_max_mhz)"}
+    return hbm, alu
+
+
+def _inputs(seed, H=None, W=None):
     import synth
-    F = synth.rgb_scene(WL["H"], WL["W"], seed=seed)
+    F = synth.rgb_scene(H or WL["H"], W or WL["W"], seed=seed)
     G = synth.luminance(F)
     return F, G
 
 
 # ----------------------------------------------------------------- oracle arm
 
-def _oracle_sample(crop_rows: int | None, iters: int, lam: float, seed: int):
-    """Runs the oracle once; returns (seconds, megapixels x iterations, output)."""
+def _oracle_crop(r: int, crop_rows: int, row0: int, seed: int, lam: float):
+    """The oracle, once, on rows [row0, row0 + crop_rows) of the workload
+    image, one iteration (column pass + row pass).  Returns (seconds,
+    megapixels x iterations, output, crop input, crop guidance)."""
     import numpy as np
 
     from oracle import Params, sgwls
     F, G = _inputs(seed)
-    if crop_rows:
-        F, G = F[:, :crop_rows], G[:crop_rows]
-    prm = Params(r=WL["r"], iters=iters, sigma_s=float(WL["r"]), sigma_r=WL["sigma_r"])
+    F = np.ascontiguousarray(F[:, row0:row0 + crop_rows])
+    G = np.ascontiguousarray(G[row0:row0 + crop_rows])
+    prm = Params(r=r, iters=1, sigma_s=float(r), sigma_r=WL["sigma_r"])
     t0 = time.perf_counter()
     U = sgwls(F.astype(np.float64), G.astype(np.float64), lam, prm)
     dt = time.perf_counter() - t0
-    return dt, F.shape[1] * F.shape[2] / 1e6 * iters, U
+    return dt, F.shape[1] * F.shape[2] / 1e6, U, F, G
+
+
+def _pool_task(job):
+    """One single-threaded oracle run in a pool worker (the pool is started
+    with `spawn`, before any work, with single-thread BLAS)."""
+    r, crop_rows, row0, seed = job
+    dt, mp, _, _, _ = _oracle_crop(r, crop_rows, row0, seed, WL["lam"])
+    return dt, mp
+
+
+def _pool_init():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    import oracle  # noqa: F401  (imports paid before the timed map)
+    import synth  # noqa: F401
 
 
 def _single_thread_env():
@@ -140,19 +265,53 @@ def _single_thread_env():
     return env
 
 
-def _cpu_baseline_subprocess(out_npy: str | None):
-    """The oracle, single-threaded, in a fresh process: the full workload
-    image, T iterations at lambda 2.0 (also the accuracy reference)."""
-    code = (
-        "import sys, json, numpy as np; sys.path.insert(0, %r); import bench; "
-        "dt, mp, U = bench._oracle_sample(None, %d, 2.0, %d); "
-        "np.save(%r, U) if %r else None; print(json.dumps({'dt': dt, 'mp': mp}))"
-    ) % (ROOT, WL["iters"], WL["seed"], out_npy or "", bool(out_npy))
-    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_single_thread_env())
-    if res.returncode != 0:
-        raise RuntimeError(res.stderr[-2000:])
-    d = json.loads(res.stdout.strip().splitlines()[-1])
-    return d["dt"], d["mp"]
+def cpu_baselines(r: int, want_output: bool = False):
+    """The oracle (FP64) on this host: one thread (a fresh single-threaded
+    process) and all cores (one single-threaded oracle process per core of
+    this process's affinity set, each on its own crop, started with spawn:
+    throughput = all processes' megapixels over the wall time).  Returns
+    (one-thread dict, all-cores dict, oracle output of the one-thread crop
+    or None, the crop's first row)."""
+    import multiprocessing as mp_
+
+    import numpy as np
+    crop = CPU_CROP_ROWS[r]
+    row0 = 0
+    fd, npy = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    code = ("import sys, json, numpy as np; sys.path.insert(0, %r); import bench; "
+            "dt, mp, U, _, _ = bench._oracle_crop(%d, %d, %d, %d, %r); np.save(%r, U); "
+            "print(json.dumps({'dt': dt, 'mp': mp}))") % (ROOT, r, crop, row0, WL["seed"], WL["lam"], npy)
+    try:
+        res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_single_thread_env())
+        if res.returncode != 0:
+            raise RuntimeError(res.stderr[-2000:])
+        d = json.loads(res.stdout.strip().splitlines()[-1])
+        U = np.load(npy) if want_output else None
+    finally:
+        os.unlink(npy)
+    sample = (f"{WL['W']}x{crop} crop (rows {row0}-{row0 + crop - 1}) of the workload image, r={r}, one "
+              "iteration (column + row pass), numpy/scipy FP64")
+    one = {"value": d["mp"] / d["dt"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+           "seconds": d["dt"]}
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    offsets = [k * crop for k in range(max(1, WL["H"] // crop))]
+    jobs = [(r, crop, offsets[i % len(offsets)], WL["seed"]) for i in range(ncores)]
+    ctx = mp_.get_context("spawn")
+    with ctx.Pool(ncores, initializer=_pool_init) as pool:
+        pool.map(_pool_init_probe, range(ncores))
+        t0 = time.perf_counter()
+        out = pool.map(_pool_task, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    allc = {"value": sum(m for _, m in out) / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{ncores} single-threaded oracle processes (spawn), each one {WL['W']}x{crop} crop of the "
+                      f"workload image, r={r}, one iteration; throughput = their megapixels / wall time",
+            "seconds": wall}
+    return one, allc, U, row0
+
+
+def _pool_init_probe(_):
+    return os.getpid()
 
 
 def run_reference(args):
@@ -160,16 +319,18 @@ def run_reference(args):
     if rank != 0:
         return 0
     os.environ.update({k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")})
+    offsets = list(range(0, WL["H"] - REF_CROP_ROWS + 1, REF_CROP_ROWS))
     for i in range(args.warmup):
-        _oracle_sample(REF_CROP_ROWS, 1, WL["lams"][i % 2], WL["seed"])
+        _oracle_crop(WL["r"], REF_CROP_ROWS, offsets[i % len(offsets)], WL["seed"], WL["lam"])
     times, mp = [], 0.0
     for i in range(args.steps):
-        dt, m, _ = _oracle_sample(REF_CROP_ROWS, 1, WL["lams"][i % 2], WL["seed"])
+        dt, m, _, _, _ = _oracle_crop(WL["r"], REF_CROP_ROWS, offsets[i % len(offsets)], WL["seed"], WL["lam"])
         times.append(dt)
         mp += m
     total = sum(times)
     value = mp / total
-    sample = f"{WL['W']}x{REF_CROP_ROWS} crop of the workload image, 1 iteration per step"
+    sample = (f"{WL['W']}x{REF_CROP_ROWS} crops of the workload image (step i: rows from 64 (i mod 16)), r=2, "
+              "1 iteration (column + row pass) per step, one thread")
     line = {
         "impl": "reference",
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -185,8 +346,8 @@ def run_reference(args):
 
 def _config_dict():
     return {"workload": WL["name"], "H": WL["H"], "W": WL["W"], "C": WL["C"], "r": WL["r"],
-            "iters": WL["iters"], "lambda": list(WL["lams"]), "sigma_r": WL["sigma_r"],
-            "sigma_s": float(WL["r"]), "weight": "exp", "guidance": "luminance",
+            "iters": WL["iters"], "lambda": WL["lam"], "sigma_r": WL["sigma_r"],
+            "sigma_s": float(WL["r"]), "weight": "exp", "guidance": "luminance", "storage": "f32",
             "l2": "flushed before every timed step (256 MiB write)"}
 
 
@@ -245,8 +406,157 @@ class ClockSampler:
 
 # ------------------------------------------------------------------- GPU arm
 
-def run_ours(args):
+class FilterBench:
+    """Device timing of one filter configuration on one image: whole filter
+    calls (L2 flushed before each), the same steps pass by pass (an event
+    pair around every pass on the launch stream), the kernel launch count,
+    and the pipelined end-to-end leg through pinned host buffers."""
+
+    def __init__(self, sg, dev, stream, flush, F, G, lam, kw):
+        import torch
+        self.sg, self.dev, self.stream, self.flush = sg, dev, stream, flush
+        self.F, self.G, self.lam, self.kw = F, G, lam, kw
+        self.f = torch.from_numpy(F).to(dev)
+        self.g = torch.from_numpy(G).to(dev)
+        self.C, self.H, self.W = F.shape
+        self.T = kw["iters"]
+        self.ws = torch.empty(max(sg.workspace_bytes(self.C, self.H, self.W, **kw), 1), dtype=torch.uint8,
+                              device=dev)
+        self.out = torch.empty_like(self.f)
+        self.bufs = [torch.empty_like(self.f), torch.empty_like(self.f)]
+        self.dirs = [0, 1] * self.T
+
+    def filt(self, out=None, f=None, g=None):
+        self.sg.sgwls_filter(self.f if f is None else f, self.g if g is None else g, self.lam,
+                             out=self.out if out is None else out, workspace=self.ws, stream=self.stream, **self.kw)
+
+    def passes(self, evs=None):
+        src = self.f
+        for t, d in enumerate(self.dirs):
+            dst = self.bufs[t & 1]
+            if evs is not None:
+                evs[t][0].record(self.stream)
+            self.sg.sgwls_filter_pass(src, self.g, self.lam, d, out=dst, workspace=self.ws, stream=self.stream,
+                                      **self.kw)
+            if evs is not None:
+                evs[t][1].record(self.stream)
+            src = dst
+        return src
+
+    def device(self, steps, warmup, barrier=lambda: None):
+        """(summed ms of `steps` filters, kernels launched in them)."""
+        import torch
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(self.stream):
+            for _ in range(warmup):
+                self.filt()
+        step_evs = [(ev(), ev()) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize(self.dev)
+        n0 = self.sg.launch_count()
+        with torch.cuda.stream(self.stream):
+            for i in range(steps):
+                self.flush.zero_()
+                step_evs[i][0].record(self.stream)
+                self.filt()
+                step_evs[i][1].record(self.stream)
+        torch.cuda.synchronize(self.dev)
+        n1 = self.sg.launch_count()
+        barrier()
+        return sum(a.elapsed_time(b) for a, b in step_evs), n1 - n0
+
+    def per_pass(self, steps):
+        """(mean column-pass ms, mean row-pass ms)."""
+        import torch
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        npass = len(self.dirs)
+        with torch.cuda.stream(self.stream):
+            self.passes()
+        evs = [[(ev(), ev()) for _ in range(npass)] for _ in range(steps)]
+        with torch.cuda.stream(self.stream):
+            for i in range(steps):
+                self.flush.zero_()
+                self.passes(evs[i])
+        torch.cuda.synchronize(self.dev)
+        ms = [[evs[i][t][0].elapsed_time(evs[i][t][1]) for t in range(npass)] for i in range(steps)]
+        col = statistics.mean(x[t] for x in ms for t in range(npass) if self.dirs[t] == 0)
+        row = statistics.mean(x[t] for x in ms for t in range(npass) if self.dirs[t] == 1)
+        return col, row
+
+    def e2e(self, steps, warmup, barrier=lambda: None):
+        """End to end through sgwls_filter: every step copies its input and
+        guidance from pinned host memory and its result back.  The copies of
+        steps i-1 and i+1 run on their own streams (two device buffer sets)
+        under the filter of step i; L2 is flushed before every filter.
+        Returns (ms for `steps` steps, h2d bytes per step, d2h bytes per step,
+        max |host result - device result| of the last step)."""
+        import torch
+        Fh = torch.from_numpy(self.F).pin_memory()
+        Gh = torch.from_numpy(self.G).pin_memory()
+        Uh = [torch.empty_like(Fh).pin_memory() for _ in range(2)]
+        fin = [torch.empty_like(self.f) for _ in range(2)]
+        gin = [torch.empty_like(self.g) for _ in range(2)]
+        uo = [torch.empty_like(self.f) for _ in range(2)]
+        s_in, s_out = torch.cuda.Stream(self.dev), torch.cuda.Stream(self.dev)
+        st = self.stream
+
+        def run(nsteps):
+            ev = lambda: torch.cuda.Event(enable_timing=True)
+            in_ready, done, out_read = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+            e0, e1 = ev(), ev()
+            e0.record(st)
+            s_in.wait_event(e0)
+            for i in range(nsteps):
+                b = i & 1
+                if i >= 2:
+                    s_in.wait_event(done[b])          # the filter of step i-2 read fin[b]
+                with torch.cuda.stream(s_in):
+                    fin[b].copy_(Fh, non_blocking=True)
+                    gin[b].copy_(Gh, non_blocking=True)
+                    in_ready[b].record(s_in)
+                st.wait_event(in_ready[b])
+                if i >= 2:
+                    st.wait_event(out_read[b])        # the result of step i-2 left uo[b]
+                with torch.cuda.stream(st):
+                    self.flush.zero_()
+                    self.filt(out=uo[b], f=fin[b], g=gin[b])
+                    done[b].record(st)
+                s_out.wait_event(done[b])
+                with torch.cuda.stream(s_out):
+                    Uh[b].copy_(uo[b], non_blocking=True)
+                    out_read[b].record(s_out)
+            e1.record(s_out)
+            torch.cuda.synchronize(self.dev)
+            return e0.elapsed_time(e1)
+
+        run(warmup)
+        barrier()
+        total = run(steps)
+        barrier()
+        with torch.cuda.stream(st):
+            self.filt()
+        torch.cuda.synchronize(self.dev)
+        diff = float((Uh[(steps - 1) & 1] - self.out.cpu()).abs().max())
+        elem = Fh.element_size()
+        return total, int((Fh.numel() + Gh.numel()) * elem), int(Uh[0].numel() * elem), diff
+
+
+def _crop_error(sg, dev, stream, r, U, row0):
+    """max |GPU - oracle| on the oracle's one-iteration crop."""
     import numpy as np
+    import torch
+    crop = CPU_CROP_ROWS[r]
+    F, G = _inputs(WL["seed"])
+    F = np.ascontiguousarray(F[:, row0:row0 + crop])
+    G = np.ascontiguousarray(G[row0:row0 + crop])
+    with torch.cuda.stream(stream):
+        u = sg.sgwls_filter(torch.from_numpy(F).to(dev), torch.from_numpy(G).to(dev), WL["lam"], r=r, iters=1,
+                            sigma_r=WL["sigma_r"], stream=stream)
+    torch.cuda.synchronize(dev)
+    return float(np.abs(u.cpu().numpy().astype(np.float64) - U).max())
+
+
+def run_ours(args):
     import torch
 
     rank, world, local = _dist()
@@ -262,194 +572,74 @@ def run_ours(args):
         build.build()
     import paper_1705_01674_gb300 as sg
 
-    H, W, C, T = WL["H"], WL["W"], WL["C"], WL["iters"]
-    F, G = _inputs(_rank_seed(rank))
-    f = torch.from_numpy(F).to(dev)
-    g = torch.from_numpy(G).to(dev)
-    bufs = [torch.empty_like(f), torch.empty_like(f)]
-    kw = dict(r=WL["r"], iters=T, sigma_r=WL["sigma_r"])
-    ws = torch.empty(sg.workspace_bytes(C, H, W, **kw), dtype=torch.uint8, device=dev)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    stream = torch.cuda.Stream(dev)
-    dirs = [0, 1] * T
-    npass = len(dirs)
-
-    def step(lam, evs=None):
-        src = f
-        for t, d in enumerate(dirs):
-            dst = bufs[t & 1]
-            if evs is not None:
-                evs[t][0].record(stream)
-            sg.sgwls_filter_pass(src, g, lam, d, out=dst, workspace=ws, stream=stream, **kw)
-            if evs is not None:
-                evs[t][1].record(stream)
-            src = dst
-        return src
-
-    with torch.cuda.stream(stream):
-        for i in range(args.warmup):
-            step(WL["lams"][i % 2])
-    torch.cuda.synchronize(dev)
-
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    # timed region: one event pair around each step, a step being one call
-    # of the filter (its 2T passes run back to back, each kernel overlapping
-    # its predecessor's tail)
-    uo = torch.empty_like(f)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    H, W, C, T = WL["H"], WL["W"], WL["C"], WL["iters"]
+    F, G = _inputs(_rank_seed(rank))
+    mp_per_step = H * W / 1e6 * T
 
-    def filt(lam):
-        sg.sgwls_filter(f, g, lam, out=uo, workspace=ws, stream=stream, **kw)
+    def one_config(r):
+        kw = dict(r=r, iters=T, sigma_r=WL["sigma_r"])
+        fb = FilterBench(sg, dev, stream, flush, F, G, WL["lam"], kw)
+        total_ms, launches = fb.device(args.steps, args.warmup, barrier)
+        total_ms = _max_over_ranks(total_ms, world, dev)
+        col_ms, row_ms = fb.per_pass(args.steps)
+        e2e_ms, h2d, d2h, diff = fb.e2e(args.steps, args.warmup, barrier)
+        e2e_ms = _max_over_ranks(e2e_ms, world, dev)
+        hbm, alu = roofline_lines(H, W, C, r, col_ms, row_ms, f"rgb1920x1080_r{r}_T{T}")
+        res = {"value": _job_value(world, mp_per_step, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
+               "roofline": hbm, "roofline_alu": alu,
+               "e2e": {"value": _job_value(world, mp_per_step, args.steps, e2e_ms), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
+                       "pipelined": "copies of steps i-1, i+1 overlap the filter of step i; L2 flushed before "
+                                    "every filter inside the timed region",
+                       "max_abs_diff_vs_device_result": diff},
+               "gpu_launches": int(launches)}
+        del fb
+        torch.cuda.empty_cache()
+        return res
 
-    with torch.cuda.stream(stream):
-        for i in range(args.warmup):
-            filt(WL["lams"][i % 2])
-    step_evs = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-                for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
-    torch.cuda.synchronize(dev)
-    n0 = sg.launch_count()
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            flush.zero_()
-            step_evs[i][0].record(stream)
-            filt(WL["lams"][i % 2])
-            step_evs[i][1].record(stream)
-    torch.cuda.synchronize(dev)
-    n1 = sg.launch_count()
-    barrier()
+    head = one_config(WL["r"])
+    by_r = {f"r{r}": one_config(r) for r in EXTRA_R}
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in step_evs)
 
-    # per-pass durations for the roofline: the same steps with an event pair
-    # around every pass (on the stream the pass kernels run on)
-    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(npass)]
-           for _ in range(args.steps)]
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            flush.zero_()
-            step(WL["lams"][i % 2], evs[i])
-    torch.cuda.synchronize(dev)
-    pass_ms = [[evs[i][t][0].elapsed_time(evs[i][t][1]) for t in range(npass)] for i in range(args.steps)]
-    col_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 0)
-    row_ms = statistics.mean(x[t] for x in pass_ms for t in range(npass) if dirs[t] == 1)
-    total_ms = _max_over_ranks(total_ms, world, dev)
-    mp_per_step = H * W / 1e6 * T
-    value = _job_value(world, mp_per_step, args.steps, total_ms)
-
-    # accuracy of the last lambda-2.0 output against the oracle (rank 0)
-    # and the CPU baseline: the oracle, single-threaded, same image.
-    err = None
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        with torch.cuda.stream(stream):
-            u = step(2.0)
-        torch.cuda.synchronize(dev)
-        fd, npy = tempfile.mkstemp(suffix=".npy")
-        os.close(fd)
-        try:
-            dt, mp = _cpu_baseline_subprocess(npy)
-            U = np.load(npy)
-            err = float(np.abs(u.cpu().numpy().astype(np.float64) - U).max())
-        finally:
-            os.unlink(npy)
-        cpu = {"value": mp / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"full {W}x{H} RGB image, T={T} iterations at lambda 2.0, one run, "
-                         "single thread (numpy/scipy FP64)"}
-
-    # end to end through the one-call API: pinned host in/out, every step's
-    # host->device copy of its inputs and device->host copy of its result in
-    # the timed region.  Steps are pipelined the way a serving loop runs
-    # them: the copies of steps i+1 and i-1 (their own streams, two device
-    # buffer sets) overlap the filter of step i; L2 is flushed before every
-    # filter inside the timed region.
-    Fh = torch.from_numpy(F).pin_memory()
-    Gh = torch.from_numpy(G).pin_memory()
-    Uh = [torch.empty_like(Fh).pin_memory() for _ in range(2)]
-    fin = [torch.empty_like(f) for _ in range(2)]
-    gin = [torch.empty_like(g) for _ in range(2)]
-    uo2 = [torch.empty_like(f) for _ in range(2)]
-    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-
-    def e2e_run(nsteps):
-        ev = lambda: torch.cuda.Event(enable_timing=True)
-        in_ready, done, out_read = [ev(), ev()], [ev(), ev()], [ev(), ev()]
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        s_in.wait_event(e0)
-        for i in range(nsteps):
-            b = i & 1
-            if i >= 2:
-                s_in.wait_event(done[b])          # the filter of step i-2 read fin[b]
-            with torch.cuda.stream(s_in):
-                fin[b].copy_(Fh, non_blocking=True)
-                gin[b].copy_(Gh, non_blocking=True)
-                in_ready[b].record(s_in)
-            stream.wait_event(in_ready[b])
-            if i >= 2:
-                stream.wait_event(out_read[b])    # the result of step i-2 left uo2[b]
-            with torch.cuda.stream(stream):
-                flush.zero_()
-                sg.sgwls_filter(fin[b], gin[b], WL["lams"][i % 2], out=uo2[b], workspace=ws, stream=stream,
-                                **kw)
-                done[b].record(stream)
-            s_out.wait_event(done[b])
-            with torch.cuda.stream(s_out):
-                Uh[b].copy_(uo2[b], non_blocking=True)
-                out_read[b].record(s_out)
-        e1.record(s_out)
-        torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1)
-
-    e2e_run(args.warmup)
-    barrier()
-    e2e_total = _max_over_ranks(e2e_run(args.steps), world, dev)
-    e2e_value = _job_value(world, mp_per_step, args.steps, e2e_total)
-    # the last step's host result against the same filter run on the device
-    last = args.steps - 1
-    with torch.cuda.stream(stream):
-        filt(WL["lams"][last % 2])
-    torch.cuda.synchronize(dev)
-    e2e_diff = float((Uh[last & 1] - uo.cpu()).abs().max())
-
-    peak, peak_kind = _peaks()
-    bytes_per_pass = H * W * (C * 4 + C * 4 + 4)   # read estimate, read guidance, write estimate
-    dom_ms = max(col_ms, row_ms)
-    achieved = bytes_per_pass / (dom_ms / 1e3) / 1e9
-    roofline = {
-        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": ROW_PASS_DRAM_BYTES if row_ms >= col_ms else COL_PASS_DRAM_BYTES,
-        "kernel": "row pass" if row_ms >= col_ms else "column pass",
-        "peak_source": f"{peak_kind} hbm_gbs",
-        "pass_ms": {"column": col_ms, "row": row_ms},
-        "algorithmic_bytes_per_launch": bytes_per_pass,
-    }
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config_dict(),
-        "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int((Fh.numel() + Gh.numel()) * 4),
-                "d2h_bytes_per_step": int(Uh[0].numel() * 4), "ms_per_step": e2e_total / args.steps,
-                "pipelined": "copies of steps i-1, i+1 overlap the filter of step i; L2 flushed before every "
-                             "filter inside the timed region",
-                "max_abs_diff_vs_device_result": e2e_diff},
-        "gpu_launches": int(n1 - n0),
-        "clocks": clk,
+        "roofline": head["roofline"], "roofline_alu": head["roofline_alu"], "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"], "clocks": clk,
+        "by_r": {"workload": "the same image and settings at r = 3 and r = 5 (sigma_s = r)", **by_r},
     }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        errs = {}
+        for r in (WL["r"],) + EXTRA_R:
+            one, allc, U, row0 = cpu_baselines(r, want_output=True)
+            errs[f"r{r}"] = _crop_error(sg, dev, stream, r, U, row0)
+            tgt = line if r == WL["r"] else line["by_r"][f"r{r}"]
+            tgt["cpu_baseline"] = one
+            tgt["cpu_baseline_all_cores"] = allc
+        line["max_abs_err_vs_oracle"] = errs[f"r{WL['r']}"]
+        line["max_abs_err_vs_oracle_note"] = (
+            f"on the oracle's one-iteration {W}x{CPU_CROP_ROWS[WL['r']]} crop; every pixel of the whole T=2 "
+            "filter is compared with the oracle in the GPU tests")
+        for r in EXTRA_R:
+            line["by_r"][f"r{r}"]["max_abs_err_vs_oracle"] = errs[f"r{r}"]
+
     if rank == 0 and world == 1 and not args.no_secondary:
+        line["fwd_bwd"] = run_fwd_bwd(sg, dev, stream, flush, args.steps, args.warmup)
         line["secondary"] = run_secondary(sg, dev, stream, flush)
-        line["secondary"]["bf16_storage"]["speedup_vs_fp32"] = line["secondary"]["bf16_storage"]["value"] / value
-    if cpu is not None:
-        line["cpu_baseline"] = cpu
-    if err is not None:
-        line["max_abs_err_vs_oracle"] = err
+        line["secondary"]["bf16_storage"]["speedup_vs_fp32"] = (
+            line["secondary"]["bf16_storage"]["value"] / line["value"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -478,46 +668,61 @@ def _timed(fn, steps, warmup, flush, stream):
     return sum(a.elapsed_time(b) for a, b in evs)
 
 
-def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
-    """Forward+backward (16 RGB 512x512, r=1, T=3), batched uneven sizes
-    (64 gray images, sides U[256, 2048], r=2, T=2, lambda U[0.5, 4]) against
-    single-image calls, BF16 storage of the main workload, and guided sparse
-    interpolation (Eq. 21) on a 4x depth-upsampling pattern."""
-    import numpy as np
+def run_fwd_bwd(sg, dev, stream, flush, steps, warmup):
+    """Forward + backward of 16 RGB 512 x 512 images (r = 1, T = 3, loss
+    sum((U - target)^2); gradients with respect to f, the guidance and
+    lambda through the C ABI, checkpoints kept by the forward).  Roofline
+    over the whole step: 2T forward passes at 28 B/px (RGB FP32 estimate in
+    and out, luminance guidance) and 2T backward passes at 48 B/px
+    (checkpoint, guidance, u-bar in, f-bar out, g-bar read and written)."""
     import torch
 
     import synth
-    out = {}
-
-    # forward + backward through the C ABI (checkpoints kept by the forward)
-    F, Tg = synth.diff_batch(n=16, H=512, W=512, seed=5)
+    F, Tg = synth.diff_batch(n=DIFF["n"], H=DIFF["H"], W=DIFF["W"], seed=DIFF["seed"])
     fs = torch.from_numpy(F).to(dev)
     ts = torch.from_numpy(Tg).to(dev)
     gs = torch.stack([torch.from_numpy(synth.luminance(x)) for x in F]).to(dev)
-    kw = dict(r=1, iters=3, sigma_r=0.1)
-    saved = torch.empty((6, 3, 512, 512), device=dev)
+    kw = dict(r=DIFF["r"], iters=DIFF["iters"], sigma_r=DIFF["sigma_r"])
+    T = DIFF["iters"]
+    saved = torch.empty((2 * T, 3, DIFF["H"], DIFF["W"]), device=dev)
     u = torch.empty_like(fs[0])
 
     def fwd_bwd(i):
         for b in range(fs.shape[0]):
-            sg.sgwls_filter(fs[b], gs[b], 1.0, out=u, saved=saved, stream=stream, **kw)
+            sg.sgwls_filter(fs[b], gs[b], DIFF["lam"], out=u, saved=saved, stream=stream, **kw)
             gu = 2.0 * (u - ts[b])
-            sg.sgwls_filter_backward(gu, gs[b], saved, 1.0, stream=stream, **kw)
+            sg.sgwls_filter_backward(gu, gs[b], saved, DIFF["lam"], stream=stream, **kw)
 
     def fwd_only(i):
         for b in range(fs.shape[0]):
-            sg.sgwls_filter(fs[b], gs[b], 1.0, out=u, stream=stream, **kw)
+            sg.sgwls_filter(fs[b], gs[b], DIFF["lam"], out=u, stream=stream, **kw)
 
-    mp = fs.shape[0] * 512 * 512 / 1e6 * 3
+    npx = DIFF["n"] * DIFF["H"] * DIFF["W"]
+    mp = npx / 1e6 * T
     ms_fb = _timed(fwd_bwd, steps, warmup, flush, stream) / steps
     ms_f = _timed(fwd_only, steps, warmup, flush, stream) / steps
-    out["fwd_bwd"] = {"workload": "16 x RGB 512x512, r=1, T=3, loss sum((U - target)^2)",
-                      "value": mp / (ms_fb / 1e3), "unit": UNIT, "ms_per_step": ms_fb,
-                      "fwd_value": mp / (ms_f / 1e3)}
-    # per pass: forward 28 B/px (RGB FP32 + luminance), backward 48 B/px
-    # (checkpoint, guidance, u-bar in, f-bar out, g-bar read and written)
-    out["fwd_bwd"]["hbm_frac"] = _hbm_frac(out["fwd_bwd"]["value"], 2 * (28.0 + 48.0))
-    del fs, ts, gs, saved
+    peak, _, kind = _peaks()
+    step_bytes = npx * 2 * T * (28 + 48)
+    achieved = step_bytes / (ms_fb / 1e3) / 1e9
+    return {"workload": DIFF["name"] + ": 16 x RGB 512x512, luminance guidance, r=1, T=3, loss sum((U - target)^2), "
+                                       "gradients w.r.t. f, g and lambda",
+            "value": mp / (ms_fb / 1e3), "unit": UNIT, "ms_per_step": ms_fb, "fwd_value": mp / (ms_f / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "whole forward + backward step (16 images)",
+                         "peak_source": f"{kind} hbm_gbs", "algorithmic_bytes_per_step": step_bytes}}
+
+
+def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
+    """Batched uneven sizes (64 gray images, sides U[256, 2048], r=2, T=2,
+    lambda U[0.5, 4]) against single-image calls, BF16 storage of the
+    headline workload, the 1024 x 768 RGB r = 1 T = 3 workload, guided
+    sparse interpolation (Eq. 21) on a 4x depth-upsampling pattern, the
+    (r, tau) sweep, the refinement at the frac-weight setting and a colour
+    guidance."""
+    import torch
+
+    import synth
+    out = {}
 
     # batched uneven sizes: one batched call vs. a loop of single calls
     imgs, lams = synth.batch_uneven_gray(n=64, seed=4)
@@ -536,8 +741,9 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
         for f, g, lam, o in zip(bf, bg, lams, bo):
             sg.sgwls_filter(f, g, lam, out=o, stream=stream, **kwb)
 
-    ms_b = _timed(batched, max(2, steps // 2), 1, flush, stream) / max(2, steps // 2)
-    ms_s = _timed(singles, max(2, steps // 2), 1, flush, stream) / max(2, steps // 2)
+    nb = max(2, steps // 2)
+    ms_b = _timed(batched, nb, 1, flush, stream) / nb
+    ms_s = _timed(singles, nb, 1, flush, stream) / nb
     # the whole batched call (all T iterations) captured once in a CUDA graph
     # and replayed per step
     graph = torch.cuda.CUDAGraph()
@@ -547,7 +753,7 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     def replay(i):
         graph.replay()
 
-    ms_g = _timed(replay, max(2, steps // 2), 1, flush, stream) / max(2, steps // 2)
+    ms_g = _timed(replay, nb, 1, flush, stream) / nb
     del graph
     out["batched"] = {"workload": f"64 gray images, sides U[256,2048] ({mpb / 2:.1f} MP), r=2, T=2",
                       "value": mpb / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b,
@@ -556,115 +762,100 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     out["batched"]["hbm_frac"] = _hbm_frac(out["batched"]["value"], 2 * 12.0)   # gray FP32, guidance = input
     del bf, bg, bo, bws
 
-    # BF16 storage of the main workload
+    # BF16 storage of the headline workload (FP32 elimination)
     F2, G2 = _inputs(WL["seed"])
     fb = torch.from_numpy(F2).to(dev).to(torch.bfloat16)
     gb = torch.from_numpy(G2).to(dev).to(torch.bfloat16)
     ub = torch.empty_like(fb)
     kw2 = dict(r=WL["r"], iters=WL["iters"], sigma_r=WL["sigma_r"])
+    for inter in ("f32", "bf16"):
+        def bf16(i, inter=inter):
+            sg.sgwls_filter(fb, gb, WL["lam"], out=ub, stream=stream, inter_storage=inter, **kw2)
 
-    def bf16(i):
-        sg.sgwls_filter(fb, gb, WL["lams"][i % 2], out=ub, stream=stream, **kw2)
-
-    ms_h = _timed(bf16, steps, warmup, flush, stream) / steps
-    mp2 = WL["H"] * WL["W"] / 1e6 * WL["iters"]
-    out["bf16_storage"] = {"workload": WL["name"] + " (BF16 input/guidance/output, FP32 intermediates)",
-                           "value": mp2 / (ms_h / 1e3), "unit": UNIT, "ms_per_step": ms_h}
+        ms_h = _timed(bf16, steps, warmup, flush, stream) / steps
+        mp2 = WL["H"] * WL["W"] / 1e6 * WL["iters"]
+        key = "bf16_storage" if inter == "f32" else "bf16_storage_bf16_intermediates"
+        out[key] = {"workload": WL["name"] + f" (BF16 input/guidance/output, {inter.upper()} intermediates)",
+                    "value": mp2 / (ms_h / 1e3), "unit": UNIT, "ms_per_step": ms_h,
+                    "hbm_frac": _hbm_frac(mp2 / (ms_h / 1e3), 2 * 14.0)}
     del fb, gb, ub
 
-    # guided sparse interpolation (Eq. 21): 4x depth upsampling pattern on
-    # the workload's size, guidance = the scene's luminance; r = 4, sigma_s
-    # = 4, sigma_r = 3 / 255, lambda = 200 (the paper's 4x setting), T = 2
-    Fd, Hd, _ = synth.sparse_depth(WL["H"], WL["W"], factor=4, seed=6)
+    # the 1024 x 768 RGB workload: r = 1, T = 3, lambda 0.5 / 2.0
+    F3, G3 = _inputs(2, 768, 1024)
+    f3 = torch.from_numpy(F3).to(dev)
+    g3 = torch.from_numpy(G3).to(dev)
+    u3 = torch.empty_like(f3)
+    kw3 = dict(r=1, iters=3, sigma_r=0.1)
+
+    def small(i):
+        sg.sgwls_filter(f3, g3, (0.5, 2.0)[i % 2], out=u3, stream=stream, **kw3)
+
+    ms3 = _timed(small, 10, 3, flush, stream) / 10
+    mp3 = 1024 * 768 / 1e6 * 3
+    out["rgb1024x768_r1_T3"] = {"workload": "1024x768 RGB, luminance guidance, r=1, T=3, lambda 0.5/2.0",
+                                "value": mp3 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3,
+                                "hbm_frac": _hbm_frac(mp3 / (ms3 / 1e3), 2 * 28.0)}
+
+    # guided sparse interpolation (Eq. 21): 4x depth upsampling pattern,
+    # guidance = the scene's luminance; r = 4, sigma_s = 4, sigma_r = 3 / 255,
+    # lambda = 200 (the paper's 4x setting), T = 2
+    Fd, Hd, _ = synth.sparse_depth(768, 1024, factor=4, seed=6)
     fd = torch.from_numpy(Fd).to(dev)
     hd = torch.from_numpy(Hd).to(dev)
-    gd = torch.from_numpy(G2).to(dev)
     ud = torch.empty_like(fd)
     kwi = dict(r=4, iters=2, sigma_r=3.0 / 255.0)
 
     def interp(i):
-        sg.sgwls_interpolate(fd, hd, gd, 200.0, out=ud, stream=stream, **kwi)
+        sg.sgwls_interpolate(fd, hd, g3, 200.0, out=ud, stream=stream, **kwi)
 
     ms_i = _timed(interp, steps, warmup, flush, stream) / steps
-    mpi = WL["H"] * WL["W"] / 1e6 * 2
-    out["interpolate"] = {"workload": f"guided 4x depth upsampling {WL['W']}x{WL['H']}, r=4, T=2, lambda=200 "
+    out["interpolate"] = {"workload": "guided 4x depth upsampling 1024x768, r=4, T=2, lambda=200 "
                                       "(depth and index map as 2 right-hand sides)",
-                          "value": mpi / (ms_i / 1e3), "unit": UNIT, "ms_per_step": ms_i}
-    del fd, hd, gd, ud
+                          "value": 1024 * 768 / 1e6 * 2 / (ms_i / 1e3), "unit": UNIT, "ms_per_step": ms_i}
+    del fd, hd, ud
 
     # (r, tau) sweep: one filter of a 1-megapixel RGB image, T = 3, the time
     # per filter for every radius 1..5 and sliding step 1..r (Sec. 2.3)
-    F3 = synth.rgb_scene(1024, 1024, seed=9)
-    f3 = torch.from_numpy(F3).to(dev)
-    g3 = torch.from_numpy(synth.luminance(F3)).to(dev)
-    u3 = torch.empty_like(f3)
+    F4 = synth.rgb_scene(1024, 1024, seed=9)
+    f4 = torch.from_numpy(F4).to(dev)
+    g4 = torch.from_numpy(synth.luminance(F4)).to(dev)
+    u4 = torch.empty_like(f4)
     sweep = {}
     for r in range(1, 6):
         for tau in range(1, r + 1):
             kws = dict(r=r, step=tau, iters=3, sigma_r=0.1)
-            ws3 = torch.empty(max(sg.workspace_bytes(3, 1024, 1024, **kws), 1), dtype=torch.uint8, device=dev)
+            ws4 = torch.empty(max(sg.workspace_bytes(3, 1024, 1024, **kws), 1), dtype=torch.uint8, device=dev)
 
-            def one(i, kws=kws, ws3=ws3):
-                sg.sgwls_filter(f3, g3, 1.0, out=u3, workspace=ws3, stream=stream, **kws)
+            def one(i, kws=kws, ws4=ws4):
+                sg.sgwls_filter(f4, g4, 1.0, out=u4, workspace=ws4, stream=stream, **kws)
 
             sweep[f"r{r}_tau{tau}"] = _timed(one, 3, 1, flush, stream) / 3
-            del ws3
+            del ws4
     out["step_sweep"] = {"workload": "1024x1024 RGB, T=3, lambda=1: ms per filter by (r, tau)", "ms": sweep}
-    del f3, g3, u3
+    del f4, g4, u4
 
-    # refinement of the subsystem solves at the paper's detail-enhancement setting (frac
-    # weights, alpha = 1.2, lambda = 900): the main workload's image, T = 2
-    fr_ = torch.from_numpy(F2).to(dev)
-    gr_ = torch.from_numpy(G2).to(dev)
-    ur_ = torch.empty_like(fr_)
+    # refinement of the subsystem solves at the paper's detail-enhancement
+    # setting (frac weights, alpha = 1.2, lambda = 900): 1024 x 768, T = 2
     kwr = dict(r=1, iters=2, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
     ms_r = {}
     for refine in (0, 1):
         def rf(i, refine=refine):
-            sg.sgwls_filter(fr_, gr_, 900.0, out=ur_, stream=stream, refine=refine, **kwr)
+            sg.sgwls_filter(f3, g3, 900.0, out=u3, stream=stream, refine=refine, **kwr)
         ms_r[f"refine{refine}"] = _timed(rf, steps, warmup, flush, stream) / steps
-    out["refine"] = {"workload": WL["name"][:-3] + "_T2 with frac weights, lambda=900: ms per filter",
-                     "ms": ms_r}
-    del ur_
+    out["refine"] = {"workload": "1024x768 RGB, r=1, T=2, frac weights, lambda=900: ms per filter "
+                                 "(refinement all FP32)", "ms": ms_r}
 
-    # the main workload guided by its own RGB image (Eq. 2 with the norm of
-    # the colour difference) instead of the luminance
-    kwc = dict(r=WL["r"], iters=WL["iters"], sigma_r=WL["sigma_r"] * 3.0 ** 0.5)
-    uc = torch.empty_like(fr_)
+    # the 1024 x 768 workload guided by its own RGB image (Eq. 2 with the
+    # norm of the colour difference) instead of the luminance
+    kwc = dict(r=1, iters=3, sigma_r=0.1 * 3.0 ** 0.5)
 
     def rgbg(i):
-        sg.sgwls_filter(fr_, fr_, WL["lams"][i % 2], out=uc, stream=stream, **kwc)
+        sg.sgwls_filter(f3, f3, (0.5, 2.0)[i % 2], out=u3, stream=stream, **kwc)
 
     ms_c = _timed(rgbg, steps, warmup, flush, stream) / steps
-    out["rgb_guidance"] = {"workload": WL["name"] + " guided by the RGB image itself (3 guidance planes)",
-                           "value": mp2 / (ms_c / 1e3), "unit": UNIT, "ms_per_step": ms_c}
-    del fr_, gr_, uc
-
-    # larger neighbourhoods: 1920 x 1080 RGB, luminance guidance, T = 2,
-    # lambda = 1, r = 2, 3, 5; FP32 storage, BF16 storage (FP32 elimination)
-    # and FP32 with the refinement (MP/s per iteration)
-    F4 = synth.rgb_scene(1080, 1920, seed=3)
-    G4 = synth.luminance(F4)
-    f4 = torch.from_numpy(F4).to(dev)
-    g4 = torch.from_numpy(G4).to(dev)
-    f4b, g4b = f4.to(torch.bfloat16), g4.to(torch.bfloat16)
-    u4, u4b = torch.empty_like(f4), torch.empty_like(f4b)
-    mp4 = 1920 * 1080 / 1e6 * 2
-    big = {}
-    for r in (2, 3, 5):
-        kw4 = dict(r=r, iters=2, sigma_r=0.1)
-        row = {}
-        for name, fi, gi, uu, extra in (("f32", f4, g4, u4, {}), ("bf16", f4b, g4b, u4b, {}),
-                                        ("f32_refine", f4, g4, u4, {"refine": 1})):
-            def one(i, fi=fi, gi=gi, uu=uu, extra=extra, kw4=kw4):
-                sg.sgwls_filter(fi, gi, 1.0, out=uu, stream=stream, **kw4, **extra)
-            ms = _timed(one, 3, 1, flush, stream) / 3
-            row[name] = {"value": mp4 / (ms / 1e3), "ms_per_step": ms}
-            row[name]["hbm_frac"] = _hbm_frac(row[name]["value"], 2 * (14.0 if name == "bf16" else 28.0))
-        big[f"r{r}"] = row
-    out["rgb1920x1080_T2"] = {"workload": "1920x1080 RGB, luminance guidance, T=2, lambda=1, r=2/3/5: FP32, "
-                                          "BF16 storage, FP32 with refinement", "unit": UNIT, "by_r": big}
-    del f4, g4, f4b, g4b, u4, u4b
+    out["rgb_guidance"] = {"workload": "1024x768 RGB r=1 T=3 guided by the RGB image itself (3 guidance planes)",
+                           "value": mp3 / (ms_c / 1e3), "unit": UNIT, "ms_per_step": ms_c}
+    del f3, g3, u3
     return out
 
 

@@ -73,17 +73,17 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *               SGWLS_E_UNSUPPORTED for step > 1
  *   axis_order  0: column direction first (Sec. 2.3), 1: row direction first
  *   refine      0 or 1: one step of iterative refinement of every
- *               subsystem solve: u1 = A~^-1 f in FP32, the residual
- *               f - A u1 with A rebuilt from the guidance in FP64, the
- *               FP32 solve of the residual added to u1, then the averaging
- *               (five kernels per pass instead of two, plus one that
- *               evaluates the FP64 pair weights once per call; workspace
- *               grows by 8 (6r - 6) bytes per pixel, 16 for r = 1, and two
- *               per-entry buffers).  For ill-conditioned
- *               settings (frac weights, large lambda: the FP32 weights
- *               alone move the exact solution by ~1e-3).  Needs step = 1 and
- *               kept factors (not factor_cache = 2); the batched,
- *               backward and no-allocation entry points return
+ *               subsystem solve, all in FP32: u1 = A~^-1 f, the residual
+ *               rho = f - u1 - lambda L u1 with A = I + lambda L applied
+ *               without forming its diagonal (the pair weights recomputed
+ *               from the guidance), the solve of rho added to u1, then the
+ *               averaging (five kernels per pass instead of two; the
+ *               workspace grows by two per-entry buffers).  For
+ *               ill-conditioned settings (frac weights, large lambda: lambda
+ *               w reaches ~1e7 and the FP32 diagonal 1 + lambda sum w loses
+ *               the identity, moving the solution by up to ~5e-3).  Needs
+ *               step = 1 and kept factors (not factor_cache = 2); the
+ *               batched, backward and no-allocation entry points return
  *               SGWLS_E_UNSUPPORTED for refine = 1
  *   storage     sgwls_dtype of f, g and u
  *   inter_storage  sgwls_dtype of the estimates between passes

@@ -111,53 +111,6 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
 int n_fields(int r, int CC) { return 3 * r * r + 2 * r * CC; }
 int n_mfields(int r, int CC) { return 3 * r * r + r * CC; }
 
-// k_pairw64: the FP64 pair weights lambda w(p, q) of Eq. 2 that the
-// refinement's residual uses, one per (pixel, offset slot), computed once
-// per call (the guidance and lambda are the same in every pass).  Offsets
-// are canonical (dy > 0, or dy = 0 and dx > 0); a pair whose second pixel
-// falls outside the image gets 0 (no subsystem holds it).
-constexpr int kPairSlotMax = 48;
-
-struct PairW64Args {
-  const void* g;
-  int g_dt;
-  int H, W;
-  int nslot;
-  int dx[kPairSlotMax], dy[kPairSlotMax];
-  double sp[kPairSlotMax];   // lambda * spatial factor of the slot's offset
-  int weight;                // 0 exp, 1 frac
-  double range64, eps64;     // exp: 1 / (2 sigma_r^2); frac: alpha_r and eps
-  double* pw;                // [nslot][H][W]
-};
-
-__global__ void __launch_bounds__(256) k_pairw64(const __grid_constant__ PairW64Args b) {
-  const long long plane = (long long)b.H * b.W;
-  const long long total = plane * b.nslot;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(i / plane);
-    const long long px = i - (long long)s * plane;
-    const int y = (int)(px / b.W), x = (int)(px - (long long)y * b.W);
-    const int x2 = x + b.dx[s], y2 = y + b.dy[s];
-    double w = 0.0;
-    if (x2 >= 0 && x2 < b.W && y2 < b.H) {
-      const double dg = (double)ld_px(b.g, px, b.g_dt) - (double)ld_px(b.g, (long long)y2 * b.W + x2, b.g_dt);
-      double rf;
-      if (b.weight == 0) {
-        rf = exp(-dg * dg * b.range64);
-      } else {
-        // |dg|^alpha_r as exp(alpha_r log |dg|) (relative error ~1e-15);
-        // 0^alpha is 0 for alpha > 0 and 1 for alpha = 0
-        const double ad = fabs(dg);
-        const double pa = ad > 0.0 ? exp(b.range64 * log(ad)) : (b.range64 > 0.0 ? 0.0 : 1.0);
-        rf = 1.0 / (pa + b.eps64);
-      }
-      w = b.sp[s] * rf;
-    }
-    b.pw[i] = w;
-  }
-}
-
 struct Layout {
   size_t img_off, img_bytes;
   size_t summ_off, summ_bytes;
@@ -167,41 +120,8 @@ struct Layout {
   size_t fac_off, fac_bytes;   // chunk factors kept between the kernels of a pass
   size_t psi_off, psi_bytes;
   size_t rhs_off, xent_off, ent_bytes;   // refinement: residual and first-solve entries
-  size_t pw_off, pw_bytes;               // refinement: FP64 pair weights
   size_t total;
 };
-
-// Pixel offsets of the pairs of a pass's subsystems, both directions, in the
-// canonical orientation (dy > 0, or dy = 0 and dx > 0): along a line
-// (t, 0) and (0, t), t = 1..r; across the snake's turn to the next line
-// (d, 1) and (1, d), |d| <= r - 1.  Fills the slot map (-1: unused) and
-// returns the slot count.
-int pair_slots(int r, int* dx, int* dy, signed char* slot_map) {
-  const int wdt = 2 * kRMax + 1;
-  for (int i = 0; i < (kRMax + 1) * wdt; ++i) slot_map[i] = -1;
-  int ns = 0;
-  auto add = [&](int x, int y) {
-    if (y < 0 || (y == 0 && x < 0)) {
-      x = -x;
-      y = -y;
-    }
-    signed char& sl = slot_map[y * wdt + x + kRMax];
-    if (sl >= 0) return;
-    sl = (signed char)ns;
-    dx[ns] = x;
-    dy[ns] = y;
-    ++ns;
-  };
-  for (int t = 1; t <= r; ++t) {
-    add(t, 0);
-    add(0, t);
-  }
-  for (int d = -(r - 1); d <= r - 1; ++d) {
-    add(d, 1);
-    add(1, d);
-  }
-  return ns;
-}
 
 // Chunk factors of one pass over CC channels: (2r + CC) values per vector
 // entry (L * (2r+1) entries per subsystem), r * r per chunk for psi.
@@ -242,7 +162,6 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   Layout lo;
   const int r = p->r;
   size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0, ent = 0;
-  bool refined = false;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
@@ -259,7 +178,6 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
         psi = std::max(psi, psi_bytes(pl.P, r, nsys));
         if (p->refine) {
           ent = std::max(ent, (size_t)L * (2 * r + 1) * CC * nsys * sizeof(float));
-          refined = true;
         }
       }
     }
@@ -286,11 +204,7 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
   lo.ent_bytes = align256(ent);
   lo.rhs_off = lo.psi_off + lo.psi_bytes;
   lo.xent_off = lo.rhs_off + lo.ent_bytes;
-  int pdx[kPairSlotMax], pdy[kPairSlotMax];
-  signed char pmap[(kRMax + 1) * (2 * kRMax + 1)];
-  lo.pw_bytes = refined ? align256((size_t)pair_slots(r, pdx, pdy, pmap) * H * W * sizeof(double)) : 0;
-  lo.pw_off = lo.xent_off + lo.ent_bytes;
-  lo.total = lo.pw_off + lo.pw_bytes;
+  lo.total = lo.xent_off + lo.ent_bytes;
   return lo;
 }
 
@@ -342,13 +256,6 @@ sgwls_status check_step(int H, int W, int C, const sgwls_params* p) {
   return SGWLS_OK;
 }
 
-// Spatial factor of Eq. 2 for two pixels dx, dy apart (FP64).
-double spatial64(const sgwls_params* p, int dx, int dy) {
-  const double d2 = (double)dx * dx + (double)dy * dy;
-  if (p->weight == SGWLS_W_EXP) return exp(-d2 / (2.0 * (double)p->sigma_s * (double)p->sigma_s));
-  return 1.0 / (pow(sqrt(d2), (double)p->alpha_s) + (double)p->eps);
-}
-
 // Fills the parts of the argument block that depend only on the parameters.
 void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
   const int r = p->r;
@@ -362,8 +269,6 @@ void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
   }
   a.eps = p->eps;
   a.dgk = (float)(1.0 / ((double)p->sigma_r * (double)p->sigma_r));
-  a.range64 = p->weight == SGWLS_W_EXP ? 1.0 / (2.0 * (double)p->sigma_r * (double)p->sigma_r) : (double)p->alpha_r;
-  a.eps64 = (double)p->eps;
   // Spatial factor of the pair (p, p+t) with j = p % n: same line -> distance
   // t; next line -> one line over and |4r + 1 - 2j - t| across (the snake
   // turns), for both directions.
@@ -384,7 +289,6 @@ void fill_weights(PassArgs& a, const sgwls_params* p, float lambda) {
       }
       a.sp[j * r + t - 1] = (float)(lambda * sp);
       a.sp0[j * r + t - 1] = (float)sp;
-      a.sp64[j * r + t - 1] = (double)lambda * sp;
     }
   }
 }
@@ -501,32 +405,7 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.refine = (keep && p->refine) ? 1 : 0;
     a.rhs = a.refine ? reinterpret_cast<float*>(wsb + lo.rhs_off) : nullptr;
     a.xent = a.refine ? reinterpret_cast<float*>(wsb + lo.xent_off) : nullptr;
-    a.pw = a.refine ? reinterpret_cast<const double*>(wsb + lo.pw_off) : nullptr;
     a.xmode = 0;
-    if (a.refine && zero_counters && c0 == 0) {
-      // the pair weights of every pass of this call (first pass only)
-      PairW64Args b;
-      memset(&b, 0, sizeof(b));
-      b.g = g;
-      b.g_dt = a.g_dt;
-      b.H = H;
-      b.W = W;
-      b.nslot = pair_slots(p->r, b.dx, b.dy, a.pw_slot);
-      for (int s = 0; s < b.nslot; ++s) b.sp[s] = (double)lambda * spatial64(p, b.dx[s], b.dy[s]);
-      b.weight = p->weight;
-      b.range64 = a.range64;
-      b.eps64 = a.eps64;
-      b.pw = reinterpret_cast<double*>(wsb + lo.pw_off);
-      const long long total = (long long)b.nslot * H * W;
-      const int nblk = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-      k_pairw64<<<nblk, 256, 0, st>>>(b);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_fail(e);
-      __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED);
-    } else if (a.refine) {
-      int pdx[kPairSlotMax], pdy[kPairSlotMax];
-      pair_slots(p->r, pdx, pdy, a.pw_slot);
-    }
     cudaError_t e = launch_pass_any(p->r, CC, a, pl, st);
     if (e != cudaSuccess) return cuda_fail(e);
     __atomic_add_fetch(&g_launches, (unsigned long long)(a.refine ? 5 : (pl.P > 1 ? 2 : 1)), __ATOMIC_RELAXED);

@@ -69,24 +69,13 @@ struct PassArgs {
   float* psi;
   // Refinement of each subsystem solve (refine = 1): first solve with
   // xmode 1 (every entry's solution to xent, no averaging); k_resid forms
-  // rho = f - A u with A in FP64 into rhs; second solve with rhs as the
+  // rho = f - A u in FP32 (A's identity kept apart) into rhs; second solve with rhs as the
   // right-hand side and xmode 2 (xent added before the averaging).  Both
   // buffers are [band][e][CC][32] (e = vector entry, 32 subsystems a band).
   float* rhs;
   float* xent;
   int xmode;
   int refine;          // host: this pass runs the two solves and the residual
-  // FP64 weight constants: lambda * spatial factor of the pair (p, p+t)
-  // (sp64[j * r + t - 1]), exp: 1 / (2 sigma_r^2), frac: alpha_r and eps
-  double sp64[(2 * kRMax + 1) * kRMax];
-  double range64, eps64;
-  // The residual's FP64 pair weights, computed once per call for both pass
-  // directions (the guidance is fixed): pw[(slot * H + y) * W + x] =
-  // lambda w((x, y), (x + dx, y + dy)) for the slot's pixel offset, stored
-  // in the canonical orientation (dy > 0, or dy = 0 and dx > 0);
-  // pw_slot[dy * (2 kRMax + 1) + dx + kRMax] is the slot of an offset.
-  const double* pw;
-  signed char pw_slot[(kRMax + 1) * (2 * kRMax + 1)];
   // Planes 0 .. n_in1-1 come from `in`, planes n_in1 .. CC-1 from `in2`
   // (the backward solves u = A^-1 f and v = A^-1 ubar together).
   const void* in2;

@@ -43,8 +43,7 @@
 //               repeats the forward sweep into shared memory before the
 //               backward sweep (also the adjoint pass of the backward).
 //   k_resid     the refinement's residual f - A u for every vector entry,
-//               A's couplings read from the FP64 pair-weight table that the
-//               library fills once per call.
+//               in FP32 with A's identity kept apart from its Laplacian.
 //
 // Compile-time modes: k_summary keeps its factors or not, takes its
 // right-hand sides from the tile or from the refinement's residual, and
@@ -2171,11 +2170,16 @@ __global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArg
 
 // ---------------------------------------------------------------------------
 // k_resid: the refinement's residual rho = f - A u for every entry of every
-// subsystem, with A rebuilt in FP64 (Eq. 2, Eq. 4, Eq. 5) from the pair
-// weights of k_pairw64 and u the first solve's entries (xent).  A's row of
-// entry e: diagonal 1 + sum lambda w, off-diagonals -lambda w to the entries
-// within r along the vector.  Grid (ceil(nsys / 32), ceil(L / (4 lines x
-// blockDim.y))), block (32, G); lane = subsystem, each warp 4 lines.
+// subsystem, in FP32, with u the first solve's entries (xent).  A = I +
+// lambda L (Eq. 4, Eq. 5) is never formed: row e of A u is
+//   u_e + sum_q lambda w(e, q) (u_e - u_q)
+// over the entries q within r of e along the vector, so the identity's
+// contribution is not rounded away next to lambda w ~ 1e7 (frac weights on
+// flat guidance), which is what makes the FP32 diagonal 1 + lambda sum w
+// inaccurate.  The pair weights are Eq. 2 in FP32 from the guidance, the
+// same expression the forward sweep uses.  Grid (ceil(nsys / 32), ceil(L /
+// (4 lines x blockDim.y))), block (32, G); lane = subsystem, each warp 4
+// lines.
 template <int R, int CC>
 __global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs a) {
   constexpr int n = 2 * R + 1;
@@ -2187,54 +2191,39 @@ __global__ void __launch_bounds__(256) k_resid(const __grid_constant__ PassArgs 
   griddep_launch();
   if (sys >= a.nsys || l0 >= a.L) return;
   const int kc = centre_of(a, sys, R);
-  const long long s_len = (long long)a.L * n;
+  const int s_len = a.L * n;
   const float* const xe = ent_lane<R, CC>(a, a.xent, sys);
   float* const re = ent_lane<R, CC>(a, a.rhs, sys);
-  // image coordinates of entry e (line e / n, snake order within the line)
-  auto coords = [&](long long e, int& x, int& y) {
-    const int line = (int)(e / n), j = (int)(e - (long long)line * n);
+  // pixel of entry e (line e / n, snake order within the line)
+  auto pix = [&](int e) {
+    const int line = e / n, j = e - line * n;
     const int off = kc - R + ((line & 1) ? 2 * R - j : j);
-    x = a.dir == 0 ? off : line;
-    y = a.dir == 0 ? line : off;
-  };
-  // lambda w of the pair (p, q), read from the canonical orientation
-  auto pair_w = [&](int xp, int yp, int xq, int yq) {
-    int dx = xq - xp, dy = yq - yp;
-    if (dy < 0 || (dy == 0 && dx < 0)) {
-      dx = -dx;
-      dy = -dy;
-      xp = xq;
-      yp = yq;
-    }
-    const int slot = a.pw_slot[dy * (2 * kRMax + 1) + dx + kRMax];
-    return __ldg(a.pw + ((long long)slot * a.H + yp) * a.W + xp);
+    return pix_index(a, line, off);
   };
   const int l1 = min(l0 + LPW, a.L);
-  for (long long e = (long long)l0 * n; e < (long long)l1 * n; ++e) {
-    int xe_, ye_;
-    coords(e, xe_, ye_);
-    const long long pe = (long long)ye_ * a.W + xe_;
-    double xv[CC], acc[CC];
+  for (int e = l0 * n; e < l1 * n; ++e) {
+    const long long pe = pix(e);
+    const float ge = ld_px(a.g, pe, a.g_dt);
+    float xv[CC], acc[CC];
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) {
-      xv[ch] = (double)__ldcg(xe + (e * CC + ch) * 32);
-      acc[ch] = (double)ld_px(plane_base<CC>(a, ch, a.in_dt == DT_F32 ? 4 : 2), pe, a.in_dt) - xv[ch];
+      xv[ch] = __ldcg(xe + (e * CC + ch) * 32);
+      acc[ch] = ld_px(plane_base<CC>(a, ch, a.in_dt == DT_F32 ? 4 : 2), pe, a.in_dt) - xv[ch];
     }
 #pragma unroll
     for (int t = 1; t <= R; ++t) {
 #pragma unroll
       for (int side = 0; side < 2; ++side) {   // pairs (e, e + t) and (e - t, e)
-        const long long q = side == 0 ? e + t : e - t;
+        const int q = side == 0 ? e + t : e - t;
         if (q < 0 || q >= s_len) continue;
-        int xq, yq;
-        coords(q, xq, yq);
-        const double w = pair_w(xe_, ye_, xq, yq);
+        const int p0 = side == 0 ? e : q;   // first entry of the pair: its position in the line picks sp
+        const float w = a.sp[(p0 % n) * R + t - 1] * range_factor(a, ge - ld_px(a.g, pix(q), a.g_dt));
 #pragma unroll
-        for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - (double)__ldcg(xe + (q * CC + ch) * 32));
+        for (int ch = 0; ch < CC; ++ch) acc[ch] -= w * (xv[ch] - __ldcg(xe + (q * CC + ch) * 32));
       }
     }
 #pragma unroll
-    for (int ch = 0; ch < CC; ++ch) re[(e * CC + ch) * 32] = (float)acc[ch];
+    for (int ch = 0; ch < CC; ++ch) re[(e * CC + ch) * 32] = acc[ch];
   }
 }
 

@@ -137,3 +137,24 @@ def test_maximum_side_length(api, shape):
             ref = oracle_pass_offsets(F, G, 2.0, prm, d, offsets)
             got = U[:, :, offsets].transpose(0, 2, 1) if direction == 0 else U[:, offsets, :]
             assert float(np.abs(got - ref).max()) <= TOL, direction
+
+
+_FILTER_REF = {}
+
+
+@pytest.mark.parametrize("r", [2, 3])
+def test_fullsize_filter_every_pixel(api, scene, r):
+    """The headline workload end to end: the whole T = 2 filter of the
+    1920 x 1080 RGB scene (luminance guidance, lambda = 1, range parameter
+    0.1, sigma_s = r) in the launch configuration the benchmark times,
+    every output pixel of every channel against the FP64 oracle."""
+    import torch
+    from oracle import sgwls
+    F, G = scene
+    if r not in _FILTER_REF:
+        _FILTER_REF[r] = sgwls(F.astype(np.float64), G.astype(np.float64), 1.0,
+                               Params(r=r, iters=2, sigma_s=float(r), sigma_r=0.1))
+    u = api.sgwls_filter(torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda(), 1.0, r=r, iters=2, sigma_r=0.1)
+    torch.cuda.synchronize()
+    err = float(np.abs(u.cpu().numpy().astype(np.float64) - _FILTER_REF[r]).max())
+    assert err <= TOL, err

@@ -26,6 +26,7 @@ from oracle import (
 )
 from oracle.rband_lu import solve_dense_rband
 from oracle.wls2d import wls2d
+from scipy.linalg import solve_banded
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -420,3 +421,39 @@ def test_pass_is_max_norm_nonexpansive(r, weight):
             Y = X + rng.uniform(-1e-3, 1e-3, size=X.shape)
             dx = np.abs(sgwls_pass(X, G, lam, prm, direction) - sgwls_pass(Y, G, lam, prm, direction)).max()
             assert dx <= np.abs(X - Y).max() * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_frac_settings_fp32_sensitivity_is_the_diagonal(r):
+    """At the frac-weight application settings (Sec. 3: alpha = 1.2,
+    eps = 1e-4, lambda = 900) lambda w reaches ~1e7.  Rounding only the
+    off-diagonals -lambda w to FP32, with every row's diagonal-dominance
+    margin kept at exactly 1 (Eq. 4: A = I + lambda L), moves the exact
+    subsystem solution by less than 1e-7; rounding the diagonal
+    1 + lambda sum w to FP32 as well moves it by more than 1e-4.  This is
+    why the FP32 residual of the refinement applies A as u + lambda L u
+    (the identity kept apart) instead of forming A's diagonal."""
+    F = synth.rgb_scene(96, 64, seed=11, n_rect=20, n_disk=5)
+    G = synth.luminance(F)
+    prm = Params(r=r, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+    lam = 900.0
+    worst_off = worst_all = 0.0
+    for k in range(r, 64 - r, 9):
+        rows, cols = neighbourhood_construction(COLUMN, k, r, 96, 64)
+        ab = subsystem_band(rows, cols, G, lam, prm)
+        f = F[0, rows, cols]
+        exact = solve_banded((r, r), ab, f)
+        s = ab.shape[1]
+        ab_off = np.zeros_like(ab)
+        ab_off[r] = 1.0
+        for t in range(1, r + 1):
+            w = (-ab[r - t, t:]).astype(np.float32).astype(np.float64)   # lambda w(p, p+t), FP32-rounded
+            ab_off[r - t, t:] = -w
+            ab_off[r + t, :s - t] = -w
+            ab_off[r, :s - t] += w
+            ab_off[r, t:] += w
+        worst_off = max(worst_off, float(np.abs(solve_banded((r, r), ab_off, f) - exact).max()))
+        ab_all = ab.astype(np.float32).astype(np.float64)
+        worst_all = max(worst_all, float(np.abs(solve_banded((r, r), ab_all, f) - exact).max()))
+    assert worst_off < 1e-7, worst_off
+    assert worst_all > 1e-4, worst_all
