@@ -72,6 +72,8 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--case", choices=sorted(CASES), default=None,
+                    help="run only a few calls of one kernel family (for profiling) and exit")
     return ap.parse_args()
 
 
@@ -608,6 +610,8 @@ def run_ours(args):
     clocks.start()
     head = one_config(WL["r"])
     by_r = {f"r{r}": one_config(r) for r in EXTRA_R}
+    tuned = run_autotuned(sg, dev, stream, flush, F, G, args) if rank == 0 and world == 1 and not args.no_secondary \
+        else None
     clk = clocks.stop()
 
     line = {
@@ -619,6 +623,8 @@ def run_ours(args):
         "gpu_launches": head["gpu_launches"], "clocks": clk,
         "by_r": {"workload": "the same image and settings at r = 3 and r = 5 (sigma_s = r)", **by_r},
     }
+    if tuned is not None:
+        line["autotuned"] = tuned
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         errs = {}
@@ -649,6 +655,35 @@ def run_ours(args):
 
 
 # --------------------------------------------------------- secondary workloads
+
+def run_autotuned(sg, dev, stream, flush, F, G, args):
+    """The library's autotuner on the headline workload (its trials run here,
+    untimed, with a throwaway cache file), then the headline timed again
+    with the tuned knobs exactly as the default line is timed."""
+    import torch
+    from paper_1705_01674_gb300 import autotune as at
+    f = torch.from_numpy(F).to(dev)
+    g = torch.from_numpy(G).to(dev)
+    kw = dict(r=WL["r"], iters=WL["iters"], sigma_r=WL["sigma_r"])
+    fd, path = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    old = os.environ.get("SGWLS_TUNE_CACHE")
+    os.environ["SGWLS_TUNE_CACHE"] = path
+    try:
+        entry = at.tune_filter(f, g, WL["lam"], steps=3, warmup=1, **kw)
+    finally:
+        if old is None:
+            os.environ.pop("SGWLS_TUNE_CACHE", None)
+        else:
+            os.environ["SGWLS_TUNE_CACHE"] = old
+        os.unlink(path)
+    fb = FilterBench(sg, dev, stream, flush, F, G, WL["lam"], dict(kw, **entry["knobs"]))
+    total_ms, _ = fb.device(args.steps, args.warmup)
+    mp_per_step = WL["H"] * WL["W"] / 1e6 * WL["iters"]
+    return {"knobs": entry["knobs"], "trials": entry["trials"], "value": mp_per_step * args.steps / (total_ms / 1e3),
+            "ms_per_step": total_ms / args.steps, "tuning_median_ms": {"tuned": entry["ms"],
+                                                                        "automatic": entry["default_ms"]}}
+
 
 def _timed(fn, steps, warmup, flush, stream):
     """Device time (ms) of `steps` calls of fn(i), L2 flushed before each."""
@@ -859,8 +894,57 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     return out
 
 
+# ------------------------------------------------------------ profiling cases
+
+def run_case(args):
+    """A few calls (args.warmup + args.steps) of one kernel family on a
+    moderately sized input, for a profiler's launch list or capture: no
+    timing, no JSON line.  The image is 960 x 540 RGB (luminance guidance),
+    the headline's scene at a quarter of its pixels."""
+    import torch
+
+    import paper_1705_01674_gb300 as sg
+    import synth
+    dev = torch.device("cuda", 0)
+    F, G = _inputs(WL["seed"], 540, 960)
+    f = torch.from_numpy(F).to(dev)
+    g = torch.from_numpy(G).to(dev)
+    n = args.warmup + args.steps
+    kw = dict(r=2, iters=2, sigma_r=0.1)
+    case = args.case
+    if case in ("queue", "two_kernel", "recompute"):
+        extra = {"queue": dict(schedule=2), "two_kernel": dict(schedule=1), "recompute": dict(factor_cache=2)}[case]
+        for _ in range(n):
+            sg.sgwls_filter(f, g, 1.0, **kw, **extra)
+    elif case == "step2":
+        for _ in range(n):
+            sg.sgwls_filter(f, g, 1.0, r=3, iters=2, step=2, sigma_r=0.1)
+    elif case == "refine":
+        for _ in range(n):
+            sg.sgwls_filter(f, g, 900.0, r=1, iters=2, refine=1, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+    elif case == "backward":
+        kwb = dict(r=1, iters=3, sigma_r=0.1)
+        saved = torch.empty((6,) + tuple(f.shape), device=dev)
+        for _ in range(n):
+            u = sg.sgwls_filter(f, g, 1.0, saved=saved, **kwb)
+            sg.sgwls_filter_backward((2.0 * (u - 0.5)).contiguous(), g, saved, 1.0, **kwb)
+    elif case == "batched":
+        imgs, lams = synth.batch_uneven_gray(n=16, seed=4, lo=128, hi=768)
+        fs = [torch.from_numpy(x).to(dev) for x in imgs]
+        gs = [x[0] for x in fs]
+        for _ in range(n):
+            sg.sgwls_filter_batched(fs, gs, lams, **kw)
+    torch.cuda.synchronize(dev)
+    return 0
+
+
+CASES = ("queue", "two_kernel", "recompute", "step2", "refine", "backward", "batched")
+
+
 def main():
     args = _args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -50,8 +50,7 @@ typedef enum {
   SGWLS_E_DTYPE = -3,       /* unknown storage type                              */
   SGWLS_E_WORKSPACE = -4,   /* workspace missing or smaller than required        */
   SGWLS_E_CUDA = -5,        /* a CUDA call failed (see sgwls_last_cuda_error)    */
-  SGWLS_E_DEVICE_FLAG = -6, /* reserved: a kernel error flag (no kernel of this
-                               build waits on another or sets one)             */
+  SGWLS_E_DEVICE_FLAG = -6, /* a kernel's bounded wait gave up (sgwls_device_flag) */
   SGWLS_E_UNSUPPORTED = -7  /* valid request this build does not implement       */
 } sgwls_status;
 
@@ -106,7 +105,28 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *               example an RGB guidance image).  Cg > 1 runs on kept factors
  *               (not factor_cache = 2); refine = 1 and the batched, backward
  *               and no-allocation entry points return SGWLS_E_UNSUPPORTED
- *               for Cg > 1.                                               */
+ *               for Cg > 1.
+ *   schedule    how a forward pass with kept factors (sliding step 1, no
+ *               refinement, one guidance plane) runs: 0 automatic (= 1),
+ *               1 two kernels (every chunk's forward sweep, then every
+ *               back substitution), 2 one persistent kernel taking both
+ *               kinds of work item from a queue, band by band, so that a
+ *               band's factors are read back while they are still in L2
+ *               (its waits are bounded: see sgwls_device_flag).  Other
+ *               passes ignore it.  A tuning knob: both schedules run the
+ *               same arithmetic and give identical results.
+ *   ring_slots  schedule 2 only: 0 automatic (as many bands of factors as
+ *               fit 64 MiB), or the number of band slots (>= 4) of the
+ *               factor-store ring; a band reuses a slot once every reader of
+ *               the band before it finished.  A tuning knob.
+ *   group_warps 0 automatic (up to 8), or 1, 2, 4, 8: the most chunks
+ *               (one warp each) a block of the single-image forward and
+ *               backward kernels takes.  A tuning knob.
+ *   lookahead   schedule 2 only: 0 automatic (about one generation of
+ *               resident blocks), else the number of bands between a band's
+ *               forward sweeps and the back substitutions that read it in
+ *               the work queue (at most ring_slots - 2 with a ring).  A
+ *               tuning knob.                                              */
 typedef struct {
   int weight;
   float sigma_s, sigma_r;
@@ -121,6 +141,10 @@ typedef struct {
   int chunk_lines;
   int factor_cache;
   int guide_channels;
+  int schedule;
+  int ring_slots;
+  int group_warps;
+  int lookahead;
 } sgwls_params;
 
 #define SGWLS_R_MAX 8
@@ -130,7 +154,8 @@ typedef struct {
 /* Defaults: exp weights, sigma_s = 1, sigma_r = 0.1, alpha_s = alpha_r = 1.2,
  * eps = 1e-4 (Sec. 1), r = 1, iters = 1, step = 1, axis_order = 0,
  * refine = 0, FP32 storage, chunk_lines = 0, factor_cache = 0,
- * guide_channels = 1.  `p` must not be NULL. */
+ * guide_channels = 1, schedule = 0, ring_slots = 0, group_warps = 0,
+ * lookahead = 0.  `p` must not be NULL. */
 void sgwls_params_default(sgwls_params* p);
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -177,7 +202,7 @@ typedef struct {
   const void* f;   /* C x H x W input (p->storage)                   */
   const void* g;   /* H x W guidance (p->storage)                    */
   void* u;         /* C x H x W output (p->storage), not aliasing f  */
-  int H, W, C;     /* C must be the same for every image, 1 <= C <= 4 */
+  int H, W, C;     /* any channel count 1 <= C <= SGWLS_C_MAX per image */
   float lambda;    /* per-image lambda >= 0                           */
   void* saved;     /* must be NULL (no checkpoints in batched calls)  */
 } sgwls_image;
@@ -208,14 +233,19 @@ sgwls_status sgwls_interpolate(const void* f, const void* hmap, const void* g, v
  * arguments are invalid).  Host-only; `imgs` is a host array. */
 size_t sgwls_batched_workspace_bytes(int B, const sgwls_image* imgs, const sgwls_params* p);
 
-/* SG-WLS filter of B images of uneven sizes (Sec. 2.3 per image, each with
- * its own lambda, the same r / T / weights).  Every pass runs as one launch
- * per kernel over all images (up to 64 images per launch; larger batches use
- * several): each block finds its image from the per-image block ranges
- * carried in the kernel arguments, so no descriptor is uploaded and the call
- * can be captured in a CUDA graph.
+/* SG-WLS filter of B images of uneven sizes and channel counts (Sec. 2.3
+ * per image, each with its own lambda, the same r / T / weights).  Every
+ * image is split into channel groups of at most four channels (the channels
+ * of a group share each subsystem's factorisation); the groups of equal
+ * size form one uniform batch, and every pass of a uniform batch runs as one
+ * launch per kernel over all its groups (up to 64 per launch; larger
+ * batches use several): each block finds its image from the per-image block
+ * ranges carried in the kernel arguments, so no descriptor is uploaded and
+ * the call can be captured in a CUDA graph.  A batch of RGB and gray images
+ * thus takes two launches per kernel per pass.
  *   imgs  host array of B images; ws: workspace of
- *         sgwls_batched_workspace_bytes bytes, 256-byte aligned. */
+ *         sgwls_batched_workspace_bytes bytes, 256-byte aligned.
+ * The output of an image may alias neither its input nor its guidance. */
 sgwls_status sgwls_filter_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws,
                                   size_t ws_bytes, void* stream);
 
@@ -276,6 +306,20 @@ sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void
  * Other arguments and results as sgwls_filter_pass. */
 sgwls_status sgwls_filter_pass_noalloc(const void* f, const void* g, void* u, int H, int W, int C,
                                        float lambda, const sgwls_params* p, int direction, void* stream);
+
+/* Device error flag of the current device.  The queue-scheduled forward
+ * pass (schedule = 2 in sgwls_params) runs as one persistent kernel whose
+ * blocks wait for
+ * one another's work items; every such wait is bounded (at least 2^20 polls
+ * and 2 s), and a wait that gives up sets this flag and skips its item, so
+ * the kernel always ends but that call's output is not valid.  The flag
+ * stays set (later queue-scheduled passes then skip their work at once)
+ * until it is cleared.  Every wait is on work that an already running
+ * block holds, so a correct run never sets it.
+ *   clear  nonzero: clear the flag after reading it
+ * Returns SGWLS_OK (flag clear), SGWLS_E_DEVICE_FLAG (flag set) or
+ * SGWLS_E_CUDA.  Synchronises with the device (a blocking copy). */
+sgwls_status sgwls_device_flag(int clear);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all devices).  Diagnostics: lets a caller count the kernels

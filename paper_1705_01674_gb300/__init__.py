@@ -19,6 +19,7 @@ import ctypes
 import torch
 
 from . import _capi
+from . import autotune as autotune_mod
 from ._capi import SgwlsError, make_params
 
 __all__ = ["sgwls", "sgwls_filter", "sgwls_filter_pass", "sgwls_filter_backward", "sgwls_filter_batched",
@@ -72,16 +73,30 @@ def workspace_bytes(C: int, H: int, W: int, **kw) -> int:
     return int(n)
 
 
+def _tuned(kind: str, mode, key_fn, tune_fn, kw: dict) -> dict:
+    """kw with the autotuner's cached knobs merged (``autotune`` mode
+    "cache"), after tuning on a cache miss (mode "search")."""
+    mode = autotune_mod.normalise_mode(mode)
+    if mode == "off":
+        return kw
+    explicit = {k for k in autotune_mod.KNOBS if k in kw}
+    knobs = autotune_mod.lookup(key_fn())
+    if knobs is None and mode == "search":
+        knobs = tune_fn()["knobs"]
+    return autotune_mod.merge(kw, knobs, explicit)
+
+
 def sgwls_filter(f: torch.Tensor, g: torch.Tensor, lam: float, *, out: torch.Tensor | None = None,
                  saved: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-                 stream: torch.cuda.Stream | None = None, **kw) -> torch.Tensor:
+                 stream: torch.cuda.Stream | None = None, autotune=None, **kw) -> torch.Tensor:
     """SG-WLS filter of one image through ``sgwls_filter`` (C ABI).
 
     f: (C,H,W) or (H,W); g: (H,W), or (Cg,H,W) for a vector guidance (an
     RGB image, say), same dtype as f (float32 or bfloat16).
     ``saved`` (optional): a float tensor with 2*iters*C*H*W elements in the
     intermediate storage type that receives each pass's input estimate.
-    Keyword parameters: see ``make_params``."""
+    Keyword parameters: see ``make_params``; ``autotune`` ("cache",
+    "search", True, False or None for $SGWLS_AUTOTUNE): see ``autotune``."""
     _check_tensor(f, "f")
     _check_tensor(g, "g")
     C, H, W = _chw(f)
@@ -89,6 +104,8 @@ def sgwls_filter(f: torch.Tensor, g: torch.Tensor, lam: float, *, out: torch.Ten
     if g.dtype != f.dtype:
         raise TypeError("g must have the dtype of f")
     kw.setdefault("storage", "bf16" if f.dtype == torch.bfloat16 else "f32")
+    kw = _tuned("filter", autotune, lambda: autotune_mod.filter_key(f, g, kw),
+                lambda: autotune_mod.tune_filter(f, g, lam, **kw), kw)
     p = make_params(**kw)
     lib = _capi.lib()
     if out is None:
@@ -184,8 +201,15 @@ def launch_count() -> int:
     return int(_capi.lib().sgwls_launch_count())
 
 
+def device_flag(clear: bool = False) -> int:
+    """Status of the current device's error flag through
+    ``sgwls_device_flag``: 0 (clear) or -6 (a bounded wait of the
+    queue-scheduled pass gave up).  Synchronises with the device."""
+    return int(_capi.lib().sgwls_device_flag(1 if clear else 0))
+
+
 def sgwls_filter_backward(grad_u: torch.Tensor, g: torch.Tensor, saved: torch.Tensor, lam: float, *,
-                          stream: torch.cuda.Stream | None = None, **kw):
+                          stream: torch.cuda.Stream | None = None, autotune=None, **kw):
     """dLoss/df, dLoss/dg, dLoss/dlambda through ``sgwls_filter_backward``.
 
     grad_u: (C,H,W) FP32; g: (H,W) FP32; saved: the (2*iters, C, H, W)
@@ -198,6 +222,8 @@ def sgwls_filter_backward(grad_u: torch.Tensor, g: torch.Tensor, saved: torch.Te
     C, H, W = _chw(grad_u)
     if tuple(g.shape) != (H, W):
         raise ValueError("g must be (H, W): the backward takes a single guidance plane")
+    kw = _tuned("backward", autotune, lambda: autotune_mod.backward_key(grad_u, kw),
+                lambda: autotune_mod.tune_backward(grad_u, g, saved, lam, **kw), kw)
     p = make_params(**kw)
     if saved.numel() < 2 * p.iters * C * H * W:
         raise ValueError(f"saved must hold 2*iters*C*H*W = {2 * p.iters * C * H * W} elements")
@@ -279,13 +305,15 @@ def batched_workspace_bytes(fs, gs, lams, **kw) -> int:
 
 
 def sgwls_filter_batched(fs, gs, lams, *, outs=None, workspace: torch.Tensor | None = None,
-                         stream: torch.cuda.Stream | None = None, **kw):
+                         stream: torch.cuda.Stream | None = None, autotune=None, **kw):
     """SG-WLS of many images of uneven sizes through ``sgwls_filter_batched``
     (one launch per kernel per pass over all images).  fs / gs / lams:
     sequences of (C,H,W) inputs, (H,W) guidance tensors and lambdas."""
     if outs is None:
         outs = [torch.empty_like(f) for f in fs]
     kw.setdefault("storage", "bf16" if fs[0].dtype == torch.bfloat16 else "f32")
+    kw = _tuned("batched", autotune, lambda: autotune_mod.batched_key(fs, kw),
+                lambda: autotune_mod.tune_batched(fs, gs, lams, **kw), kw)
     tab = _image_table(fs, gs, lams, outs)
     p = make_params(**kw)
     lib = _capi.lib()

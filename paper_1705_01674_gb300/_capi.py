@@ -48,6 +48,10 @@ class SgwlsParams(ctypes.Structure):
         ("chunk_lines", ctypes.c_int),
         ("factor_cache", ctypes.c_int),
         ("guide_channels", ctypes.c_int),
+        ("schedule", ctypes.c_int),
+        ("ring_slots", ctypes.c_int),
+        ("group_warps", ctypes.c_int),
+        ("lookahead", ctypes.c_int),
     ]
 
 
@@ -95,6 +99,8 @@ def _declare(lib):
     lib.sgwls_filter_pass_noalloc.restype = ci
     lib.sgwls_launch_count.argtypes = []
     lib.sgwls_launch_count.restype = ctypes.c_ulonglong
+    lib.sgwls_device_flag.argtypes = [ci]
+    lib.sgwls_device_flag.restype = ci
     if hasattr(lib, "sgwls_batched_workspace_bytes"):
         lib.sgwls_batched_workspace_bytes.argtypes = [ci, ctypes.POINTER(SgwlsImage), P]
         lib.sgwls_batched_workspace_bytes.restype = sz
@@ -134,7 +140,8 @@ def check(status: int, where: str):
 
 def make_params(r=1, iters=1, step=1, axis_order=0, weight="exp", sigma_s=None, sigma_r=0.1,
                 alpha_s=1.2, alpha_r=1.2, eps=1e-4, storage="f32", inter_storage=None,
-                refine=0, chunk_lines=0, factor_cache=0, guide_channels=1) -> SgwlsParams:
+                refine=0, chunk_lines=0, factor_cache=0, guide_channels=1, schedule=0,
+                ring_slots=0, group_warps=0, lookahead=0) -> SgwlsParams:
     p = SgwlsParams()
     lib().sgwls_params_default(ctypes.byref(p))
     p.weight = {"exp": W_EXP, "frac": W_FRAC}[weight]
@@ -151,6 +158,10 @@ def make_params(r=1, iters=1, step=1, axis_order=0, weight="exp", sigma_s=None, 
     p.chunk_lines = int(chunk_lines)
     p.factor_cache = int(factor_cache)
     p.guide_channels = int(guide_channels)
+    p.schedule = int(schedule)
+    p.ring_slots = int(ring_slots)
+    p.group_warps = int(group_warps)
+    p.lookahead = int(lookahead)
     dt = {"f32": F32, "bf16": BF16}
     p.storage = dt[storage]
     p.inter_storage = dt[inter_storage or storage]

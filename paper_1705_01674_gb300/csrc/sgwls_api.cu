@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sgwls.h"
@@ -29,9 +30,53 @@ cudaError_t set_smem_raw(const void* kernel, size_t bytes) {
   return e;
 }
 
+cudaError_t resident_blocks(const void* kernel, int G, size_t smem, int* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, int> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(kernel, G, smem, dev);
+  auto it = done.find(key);
+  if (it != done.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  int per_sm = 0, nsm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * G, smem)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  *out = done[key] = per_sm * nsm;
+  return cudaSuccess;
+}
+
 namespace {
 
 thread_local char g_cuda_err[256] = "";
+
+// Device word that a kernel sets when one of its bounded waits gave up
+// (the queue-scheduled pass); read and cleared by sgwls_device_flag.  The
+// name is a host-side stand-in: its device address is looked up once per
+// device, with that device current.
+__device__ unsigned g_device_flag;
+constexpr int kMaxDevices = 64;
+std::mutex g_flag_mu;
+unsigned* g_flag_ptr[kMaxDevices] = {};
+
+cudaError_t device_flag_ptr(unsigned** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_flag_mu);
+  if (!g_flag_ptr[dev]) {
+    void* p = nullptr;
+    if ((e = cudaGetSymbolAddress(&p, g_device_flag)) != cudaSuccess) return e;
+    g_flag_ptr[dev] = static_cast<unsigned*>(p);
+  }
+  *out = g_flag_ptr[dev];
+  return cudaSuccess;
+}
 
 // Launch counter: every kernel the library launches adds one.
 unsigned long long g_launches = 0;
@@ -70,7 +115,7 @@ int n_centres(int D, int r, int step, int* nreg) {
 // keep: the pass keeps its chunk factors (k_backsub follows k_summary; no
 // k_recover tile), so only the summary's tile and 2-ports bound the block.
 Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, bool keep = false, int step = 1,
-               int gc = 1) {
+               int gc = 1, int gmax = kGMax) {
   const int bands = step == 1 ? (D + (32 - 2 * r) - 1) / (32 - 2 * r) : (n_centres(D, r, step, nullptr) + 31) / 32;
   auto second = [&](int hh, int G) {
     return keep ? smem_backsub(r, CC, hh, G, step) : smem_recover(r, CC, hh, G, bwd);
@@ -89,7 +134,7 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
     // enough chunks for ~kTargetWarps warps in flight: h <= L * bands / target
     h = std::max(1, (int)(((long long)L * bands) / kTargetWarps));
     // blocks of G = 8 chunk-warps, two blocks per SM: shrink h to fit
-    while (h > 1 && block(h, kGMax) > kSmemBlockTarget) --h;
+    while (h > 1 && block(h, gmax) > kSmemBlockTarget) --h;
   }
   if (chunk_lines > 0) h = std::min(chunk_lines, L);
   while (h > 1 && block(h, 1) > kSmemBlockMax) --h;
@@ -100,7 +145,7 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   // keep: as many chunk-warps per block as fit two blocks per SM
   const size_t gcap = keep ? kSmemBlockTarget : kSmemBlockMax;
   int G = 1;
-  while (G < kGMax && G < pl.P && block(h, 2 * G) <= gcap) G *= 2;
+  while (G < gmax && G < pl.P && block(h, 2 * G) <= gcap) G *= 2;
   pl.G = G;
   pl.NG = (pl.P + G - 1) / G;
   pl.smem_sum = smem_summary(r, CC, h, G, step, gc);
@@ -130,6 +175,9 @@ size_t fac_bytes(int L, int r, int CC, int sstride) {
   return (size_t)L * (2 * r + 1) * (2 * r + CC) * sstride * sizeof(float);
 }
 size_t psi_bytes(int P, int r, int sstride) { return (size_t)P * r * r * sstride * sizeof(float); }
+// Factor-store ring of the queue-scheduled pass: as many band slots as fit
+// this budget (well inside GB300's 126 MB L2, next to the pass's images).
+constexpr size_t kRingBytes = size_t(64) << 20;
 // Guidance planes of a call (guide_channels 0 and 1: one plane).
 int guide_planes(const sgwls_params* p) { return p->guide_channels > 1 ? p->guide_channels : 1; }
 // Plan of one forward pass; *keep: its chunk factors are kept between the
@@ -141,20 +189,38 @@ Plan fwd_plan(const sgwls_params* p, int L, int D, int CC, int sstride, bool* ke
   const bool need = p->step > 1 || p->refine || gc > 1;
   bool k = need || p->factor_cache == 1 ||
            (p->factor_cache == 0 && fac_bytes(L, p->r, CC, sstride) <= kFactorCacheBytes);
-  Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k, p->step, k ? gc : 1);
+  const int gmax = p->group_warps > 0 ? p->group_warps : kGMax;
+  Plan pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, k, p->step, k ? gc : 1, gmax);
   // keeping factors needs at least two chunks
-  if (k && need && pl.P < 2 && L >= 2) pl = make_plan(L, D, p->r, CC, (L + 1) / 2, false, true, p->step, gc);
+  if (k && need && pl.P < 2 && L >= 2)
+    pl = make_plan(L, D, p->r, CC, (L + 1) / 2, false, true, p->step, gc, gmax);
   if (k && pl.P < 2) {
     k = false;
-    pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, false);
+    pl = make_plan(L, D, p->r, CC, p->chunk_lines, false, false, 1, 1, gmax);
   }
   *keep = k;
+  // on request (schedule = 2) a plain forward pass with kept factors runs as
+  // one queue-scheduled kernel whose factor store is a ring of band slots
+  // (measured on GB300 at 1920 x 1080 RGB, r = 1..5: at best 3 % faster than
+  // the two kernels, mostly slower, so not the default)
+  if (k && p->step == 1 && !p->refine && gc == 1 && p->schedule == 2) {
+    pl.queue = 1;
+    const int nb = sstride / 32;
+    const size_t band = fac_bytes(L, p->r, CC, 32) + psi_bytes(pl.P, p->r, 32);
+    const int slots = p->ring_slots > 0
+                          ? p->ring_slots
+                          : (int)std::max<size_t>(kRingBytes / band, (size_t)kLookahead + 2);
+    pl.nslot = slots >= nb ? 0 : slots;
+  }
   return pl;
 }
 
+// Control words of a pass, per band of 32 subsystems of the longer
+// direction: k_summary's block tickets, then (queue-scheduled pass) the
+// done flags and reader counts, then the queue and exit counters.
+int counter_bands(int H, int W, int r) { return (std::max(H, W) - 2 * r + 31) / 32; }
 size_t counter_bytes(int H, int W, int r) {
-  const int bands = (std::max(H, W) - 2 * r + 31) / 32;
-  return align256((size_t)bands * sizeof(int));
+  return align256(((size_t)3 * counter_bands(H, W, r) + 2) * sizeof(int));
 }
 
 // Largest per-pass scratch over both directions and all channel groups.
@@ -174,8 +240,8 @@ Layout make_layout(int H, int W, int C, const sgwls_params* p) {
       xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
       mdata = std::max(mdata, (size_t)pl.NG * std::max(pl.G - 1, 1) * n_mfields(r, CC) * nsys * sizeof(float));
       if (keep) {
-        fac = std::max(fac, fac_bytes(L, r, CC, nsys));
-        psi = std::max(psi, psi_bytes(pl.P, r, nsys));
+        fac = std::max(fac, pl.nslot ? fac_bytes(L, r, CC, 32 * pl.nslot) : fac_bytes(L, r, CC, nsys));
+        psi = std::max(psi, pl.nslot ? psi_bytes(pl.P, r, 32 * pl.nslot) : psi_bytes(pl.P, r, nsys));
         if (p->refine) {
           ent = std::max(ent, (size_t)L * (2 * r + 1) * CC * nsys * sizeof(float));
         }
@@ -223,6 +289,12 @@ sgwls_status check_params(int H, int W, int C, const sgwls_params* p) {
   if (p->chunk_lines < 0) return SGWLS_E_INVALID;
   if (p->factor_cache < 0 || p->factor_cache > 2) return SGWLS_E_INVALID;
   if (p->guide_channels < 0 || p->guide_channels > SGWLS_GUIDE_MAX) return SGWLS_E_INVALID;
+  if (p->schedule < 0 || p->schedule > 2) return SGWLS_E_INVALID;
+  if (p->group_warps != 0 && p->group_warps != 1 && p->group_warps != 2 && p->group_warps != 4 &&
+      p->group_warps != 8)
+    return SGWLS_E_INVALID;
+  if (p->ring_slots < 0 || (p->ring_slots > 0 && p->ring_slots < kLookahead + 2)) return SGWLS_E_INVALID;
+  if (p->lookahead < 0 || p->lookahead > 4096) return SGWLS_E_INVALID;
   if ((p->storage != SGWLS_F32 && p->storage != SGWLS_BF16) ||
       (p->inter_storage != SGWLS_F32 && p->inter_storage != SGWLS_BF16))
     return SGWLS_E_DTYPE;
@@ -388,6 +460,15 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
   a.xsep = reinterpret_cast<float*>(wsb + lo.xsep_off);
   a.mdata = reinterpret_cast<float*>(wsb + lo.mdata_off);
   a.band_cnt = reinterpret_cast<int*>(wsb + lo.cnt_off);
+  {
+    const int nbc = counter_bands(H, W, p->r);
+    a.done = a.band_cnt + nbc;
+    a.rdcnt = a.done + nbc;
+    a.qctl = a.rdcnt + nbc;
+    a.lookahead = p->lookahead;   // 0: chosen at launch
+    cudaError_t e = device_flag_ptr(&a.err);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
   fill_weights(a, p, lambda);
   for (int c0 = 0; c0 < C; c0 += kGroupMax) {
     const int CC = std::min(kGroupMax, C - c0);
@@ -406,9 +487,11 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.rhs = a.refine ? reinterpret_cast<float*>(wsb + lo.rhs_off) : nullptr;
     a.xent = a.refine ? reinterpret_cast<float*>(wsb + lo.xent_off) : nullptr;
     a.xmode = 0;
+    a.nslot = pl.nslot;
     cudaError_t e = launch_pass_any(p->r, CC, a, pl, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    __atomic_add_fetch(&g_launches, (unsigned long long)(a.refine ? 5 : (pl.P > 1 ? 2 : 1)), __ATOMIC_RELAXED);
+    __atomic_add_fetch(&g_launches, (unsigned long long)(a.refine ? 5 : (pl.queue || pl.P < 2) ? 1 : 2),
+                       __ATOMIC_RELAXED);
   }
   return SGWLS_OK;
 }
@@ -531,8 +614,8 @@ bool batch_keep(int B, const sgwls_image* imgs, const sgwls_params* p) {
 
 // Lines per chunk shared by every image of a batch (blocks of kGMax chunks,
 // two blocks per SM).
-int batch_h(int r, int CC, bool keep) {
-  int h = keep ? keep_lines(r) : 64;
+int batch_h(int r, int CC, bool keep, int chunk_lines) {
+  int h = chunk_lines > 0 ? chunk_lines : keep ? keep_lines(r) : 64;
   auto block = [&](int hh) {
     return keep ? std::max(smem_summary(r, CC, hh, kGMax), smem_backsub(r, CC, hh, kGMax))
                 : smem_recover(r, CC, hh, kGMax);
@@ -559,7 +642,7 @@ struct BatchImgLayout {
 // Workspace of image i starts at `base`; returns its layout.
 BatchImgLayout batch_img_layout(size_t base, int H, int W, int C, const sgwls_params* p, bool keep) {
   const int r = p->r;
-  const int h0 = batch_h(r, C, keep);
+  const int h0 = batch_h(r, C, keep, p->chunk_lines);
   size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
@@ -593,14 +676,11 @@ sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) 
   if (s0 != SGWLS_OK) return s0;
   // sliding step, refinement, vector guidance: single images
   if (p->step != 1 || p->refine || p->guide_channels > 1) return SGWLS_E_UNSUPPORTED;
-  const int C = imgs[0].C;
-  if (C < 1 || C > kGroupMax) return C < 1 ? SGWLS_E_SHAPE : SGWLS_E_UNSUPPORTED;
   for (int i = 0; i < B; ++i) {
     const sgwls_image& im = imgs[i];
     sgwls_status s = check_params(im.H, im.W, im.C, p);
     if (s != SGWLS_OK) return s;
-    if (im.C != C) return SGWLS_E_UNSUPPORTED;
-    if (!im.f || !im.g || !im.u || im.f == im.u) return SGWLS_E_INVALID;
+    if (!im.f || !im.g || !im.u || im.f == im.u || im.g == im.u) return SGWLS_E_INVALID;
     if (!(im.lambda >= 0.f) || !isfinite(im.lambda)) return SGWLS_E_INVALID;
     if (im.saved) return SGWLS_E_UNSUPPORTED;
   }
@@ -622,8 +702,57 @@ size_t batch_workspace(int B, const sgwls_image* imgs, const sgwls_params* p) {
   return off;
 }
 
+// Images of any channel count: every image is split into channel groups of
+// at most kGroupMax channels (views of its input and output at a channel
+// offset; same guidance and lambda), and the groups are gathered by size
+// into uniform batches, sets[CC - 1] holding the groups of CC channels.
+void channel_group_sets(int B, const sgwls_image* imgs, const sgwls_params* p,
+                        std::vector<sgwls_image> (&sets)[kGroupMax]) {
+  const size_t el = dt_size(p->storage);
+  for (int i = 0; i < B; ++i) {
+    const sgwls_image& im = imgs[i];
+    const size_t plane = (size_t)im.H * im.W * el;
+    for (int c0 = 0; c0 < im.C; c0 += kGroupMax) {
+      sgwls_image v = im;
+      v.C = std::min(kGroupMax, im.C - c0);
+      v.f = static_cast<const char*>(im.f) + (size_t)c0 * plane;
+      v.u = static_cast<char*>(im.u) + (size_t)c0 * plane;
+      sets[v.C - 1].push_back(v);
+    }
+  }
+}
+
+// Workspace of a batch of any channel counts: the uniform batches one after
+// another, each 256-byte aligned.
+size_t batch_workspace_any(int B, const sgwls_image* imgs, const sgwls_params* p) {
+  std::vector<sgwls_image> sets[kGroupMax];
+  channel_group_sets(B, imgs, p, sets);
+  size_t off = 0;
+  for (auto& v : sets)
+    if (!v.empty()) off = align256(off + batch_workspace((int)v.size(), v.data(), p));
+  return off;
+}
+
 }  // namespace
 
+sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st);
+
+// Batched filter of images of any channel counts: one uniform batch per
+// channel-group size present (see channel_group_sets).
+sgwls_status run_batched_any(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st) {
+  std::vector<sgwls_image> sets[kGroupMax];
+  channel_group_sets(B, imgs, p, sets);
+  size_t off = 0;
+  for (auto& v : sets) {
+    if (v.empty()) continue;
+    const sgwls_status s = run_batched((int)v.size(), v.data(), p, static_cast<char*>(ws) + off, st);
+    if (s != SGWLS_OK) return s;
+    off = align256(off + batch_workspace((int)v.size(), v.data(), p));
+  }
+  return SGWLS_OK;
+}
+
+// A uniform batch: every image has the same channel count C <= kGroupMax.
 sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st) {
   const int C = imgs[0].C;
   const int r = p->r;
@@ -637,7 +766,7 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
     return SGWLS_OK;
   }
   const bool keep = batch_keep(B, imgs, p);
-  const int h0 = batch_h(r, C, keep);
+  const int h0 = batch_h(r, C, keep, p->chunk_lines);
   const int OB = 32 - 2 * r;
   const int npass = 2 * p->iters;
   std::vector<BatchImgLayout> lay(B);
@@ -772,7 +901,8 @@ BwdLayout make_bwd_layout(int H, int W, int C, const sgwls_params* p) {
     const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
     for (int c0 = 0; c0 < C; c0 += gch) {
       const int CC = 2 * std::min(gch, C - c0);
-      const Plan pl = make_plan(L, D, r, CC, p->chunk_lines, true);
+      const Plan pl = make_plan(L, D, r, CC, p->chunk_lines, true, false, 1, 1,
+                                p->group_warps > 0 ? p->group_warps : kGMax);
       summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
       xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
       mdata = std::max(mdata, (size_t)pl.NG * std::max(pl.G - 1, 1) * n_mfields(r, CC) * nsys * sizeof(float));
@@ -863,7 +993,8 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
     const int gch = bwd_group(p->r);
     for (int c0 = 0; c0 < C; c0 += gch) {
       const int nch = std::min(gch, C - c0);
-      const Plan pl = make_plan(a.L, a.D, p->r, 2 * nch, p->chunk_lines, true);
+      const Plan pl = make_plan(a.L, a.D, p->r, 2 * nch, p->chunk_lines, true, false, 1, 1,
+                                p->group_warps > 0 ? p->group_warps : kGMax);
       a.h = pl.h;
       a.P = pl.P;
       a.ngroups = pl.NG;
@@ -904,6 +1035,10 @@ void sgwls_params_default(sgwls_params* p) {
   p->chunk_lines = 0;
   p->factor_cache = 0;
   p->guide_channels = 1;
+  p->schedule = 0;
+  p->ring_slots = 0;
+  p->group_warps = 0;
+  p->lookahead = 0;
 }
 
 const char* sgwls_status_string(sgwls_status s) {
@@ -974,6 +1109,16 @@ sgwls_status sgwls_interpolate(const void* f, const void* hmap, const void* g, v
 
 unsigned long long sgwls_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+sgwls_status sgwls_device_flag(int clear) {
+  unsigned* ptr = nullptr;
+  cudaError_t e = device_flag_ptr(&ptr);
+  if (e != cudaSuccess) return cuda_fail(e);
+  unsigned v = 0;
+  if ((e = cudaMemcpy(&v, ptr, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+  if (clear && v != 0u && (e = cudaMemset(ptr, 0, sizeof(unsigned))) != cudaSuccess) return cuda_fail(e);
+  return v ? SGWLS_E_DEVICE_FLAG : SGWLS_OK;
+}
+
 }  // extern "C"
 
 extern "C" {
@@ -1007,16 +1152,16 @@ extern "C" {
 
 size_t sgwls_batched_workspace_bytes(int B, const sgwls_image* imgs, const sgwls_params* p) {
   if (check_batch(B, imgs, p) != SGWLS_OK) return 0;
-  return batch_workspace(B, imgs, p);
+  return batch_workspace_any(B, imgs, p);
 }
 
 sgwls_status sgwls_filter_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, size_t ws_bytes,
                                   void* stream) {
   sgwls_status s = check_batch(B, imgs, p);
   if (s != SGWLS_OK) return s;
-  const size_t need = batch_workspace(B, imgs, p);
+  const size_t need = batch_workspace_any(B, imgs, p);
   if (need > 0 && (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255))) return SGWLS_E_WORKSPACE;
-  return run_batched(B, imgs, p, ws, static_cast<cudaStream_t>(stream));
+  return run_batched_any(B, imgs, p, ws, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -67,6 +67,19 @@ struct PassArgs {
   // (the only rows where it is not zero).
   float* fac;
   float* psi;
+  // Queue-scheduled pass (k_pass_q): the factor store is a ring of nslot
+  // band slots (0: one slot per band, the two-kernel pass); per band
+  // `done` (its summary items and reduced system finished) and `rdcnt`
+  // (back-substitution items that finished reading it); qctl[0] the work
+  // queue, qctl[1] the count of blocks that left; `lookahead` bands between
+  // a band's summary items and the back-substitution items that need it.
+  // `err` (device word, shared by all calls) is set when a wait gives up.
+  int nslot;
+  int lookahead;
+  int* done;
+  int* rdcnt;
+  int* qctl;
+  unsigned* err;
   // Refinement of each subsystem solve (refine = 1): first solve with
   // xmode 1 (every entry's solution to xent, no averaging); k_resid forms
   // rho = f - A u in FP32 (A's identity kept apart) into rhs; second solve with rhs as the
@@ -142,6 +155,42 @@ __device__ __forceinline__ float range_factor_sq(const PassArgs& a, float d2) {
 // two or more kernels earlier.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Nanoseconds of the global timer (for the time limit of a wait).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Waits (one thread) until *p >= v.  Gives up, sets bit `code` of *err and
+// returns false after at least 2^20 polls and 2 s of global time (both, so
+// that time the context spends switched out does not count alone), or as
+// soon as another block has set *err; the caller then skips its work and the
+// host reads the flag (sgwls_device_flag).  Every wait of this library is
+// on work that an earlier-scheduled, already running block holds, so the
+// limit is not reached in a correct run.
+__device__ __forceinline__ bool wait_geq(const int* p, int v, unsigned* err, unsigned code) {
+  if (ld_acquire(p) >= v) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    __nanosleep(it < 16 ? 32 : 256);
+    if (ld_acquire(p) >= v) return true;
+    if ((it & 63) == 0) {
+      if (*reinterpret_cast<const volatile unsigned*>(err) != 0u) return false;
+      if (it >= (1u << 20) && global_ns() - t0 > 2000000000ull) {
+        atomicOr(err, code);
+        return false;
+      }
+    }
+  }
+}
 
 __device__ __forceinline__ float fast_rcp(float x) {
   float y;

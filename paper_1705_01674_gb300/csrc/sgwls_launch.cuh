@@ -13,7 +13,14 @@ struct Plan {
   int G;          // chunks (warps) per block
   int NG;         // chunk groups = ceil(P / G)
   size_t smem_sum, smem_rec;
+  int queue = 0;  // the pass runs as the queue-scheduled k_pass_q
+  int nslot = 0;  // its factor-store ring slots (0: one per band)
 };
+
+// Least number of bands between a band's summary items and the
+// back-substitution items of the queue-scheduled pass; a ring needs at least
+// look-ahead + 2 slots.
+constexpr int kLookahead = 2;
 
 // Shared memory of the two tiled kernels for a plan (bytes); gc guidance
 // planes.
@@ -68,6 +75,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // later launches (for example inside a CUDA-graph capture) make no call.
 cudaError_t set_smem_raw(const void* kernel, size_t bytes);
 
+// Blocks of `kernel` (32 x G threads, `smem` dynamic bytes) resident on the
+// whole current device, cached per (kernel, G, smem, device).
+cudaError_t resident_blocks(const void* kernel, int G, size_t smem, int* out);
+
 // (The default limit of 48 KB covers static and dynamic shared memory
 // together: the batched kernels hold their argument block in static shared
 // memory, so the attribute is raised from 32 KB of dynamic memory on.)
@@ -81,7 +92,7 @@ template <int R, int CC, bool BWD = false>
 cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st);
 
 // Refined pass (refine = 1): first solve keeping every entry's solution,
-// the FP64 residual, the solve of the residual (same factors recomputed
+// the FP32 residual, the solve of the residual (same factors recomputed
 // from the same tile) adding the first solution, then the averaging.
 template <int R, int CC>
 cudaError_t launch_refined_pass(const PassArgs& a, const Plan& pl, cudaStream_t st) {
@@ -116,6 +127,29 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
     const size_t chain = (size_t)pl.NG * (3 * R * R + 2 * R * CC) * 32 * sizeof(float);
     b.chain_smem = (pl.NG > 1 && chain <= kReducedSmemMax) ? 1 : 0;
     const size_t smem = b.chain_smem ? std::max(pl.smem_sum, chain) : pl.smem_sum;
+    if constexpr (!BWD) {
+      if (pl.queue) {
+        // one persistent kernel: summary and back-substitution items
+        if (!b.fac || a.step != 1 || a.gc > 1 || b.rhs || b.xmode != 0 || !b.qctl) return cudaErrorInvalidValue;
+        const size_t qsmem = std::max(smem, smem_backsub(R, CC, a.h, pl.G, 1));
+        if ((e = set_smem(k_pass_q<R, CC>, qsmem)) != cudaSuccess) return e;
+        int res = 0;
+        if ((e = resident_blocks(reinterpret_cast<const void*>(k_pass_q<R, CC>), pl.G, qsmem, &res)) != cudaSuccess)
+          return e;
+        if (res < 1) return cudaErrorInvalidConfiguration;
+        // look-ahead: by default about one generation of resident blocks
+        // (a band's summary items finish before the items that need it are
+        // taken); a ring of S slots allows at most S - 2
+        int la = a.lookahead > 0 ? a.lookahead : std::max(kLookahead, res / (2 * pl.NG) + 2);
+        if (pl.nslot > 0) la = std::min(la, pl.nslot - 2);
+        b.lookahead = la;
+        const long long items = (long long)pl.NG * (((a.nsys + 31) >> 5) + (a.D + OB - 1) / OB);
+        const int grid = (int)std::min<long long>(items, res);
+        e = launch_pdl(k_pass_q<R, CC>, dim3(grid), dim3(32, pl.G), qsmem, st, b);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+      }
+    }
     void (*ks)(PassArgs) = k_summary<R, CC, 0>;
     if constexpr (!BWD) {
       if (b.rhs)

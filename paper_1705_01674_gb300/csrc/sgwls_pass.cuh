@@ -44,6 +44,10 @@
 //               backward sweep (also the adjoint pass of the backward).
 //   k_resid     the refinement's residual f - A u for every vector entry,
 //               in FP32 with A's identity kept apart from its Laplacian.
+//   k_pass_q    a forward pass with kept factors at step 1 as ONE
+//               persistent kernel: its blocks take k_summary and k_backsub
+//               work items from a queue, band by band, so a band's factors
+//               (a ring of band slots) are read back while still in L2.
 //
 // Compile-time modes: k_summary keeps its factors or not, takes its
 // right-hand sides from the tile or from the refinement's residual, and
@@ -57,6 +61,7 @@
 #pragma once
 
 #include "sgwls_common.cuh"
+#include "sgwls_sched.h"
 
 namespace sgwls {
 
@@ -826,10 +831,16 @@ struct StridedG {
 // fac[band][e][field][32] with e = line * (2r+1) + j over the L lines and
 // field < 2r + CC; psi[band][c][k][i][32].  Inside a band every offset is a
 // compile-time multiple of 32 floats from the line's base.
+// With a.nslot > 0 the store is a ring of a.nslot band slots (the
+// queue-scheduled pass reuses a slot once every reader of its band is done).
+__device__ __forceinline__ size_t fac_slot(const PassArgs& a, int sys) {
+  const int band = sys >> 5;
+  return (size_t)(a.nslot > 0 ? band % a.nslot : band);
+}
 template <int R, int CC>
 __device__ __forceinline__ float* fac_lane(const PassArgs& a, int sys) {
   const size_t band = (size_t)a.L * (2 * R + 1) * (2 * R + CC) * 32;
-  return a.fac + (size_t)(sys >> 5) * band + (sys & 31);
+  return a.fac + fac_slot(a, sys) * band + (sys & 31);
 }
 // Per-entry buffers of the refinement (rhs, xent): [band][e][CC][32].
 template <int R, int CC>
@@ -840,7 +851,7 @@ __device__ __forceinline__ float* ent_lane(const PassArgs& a, float* buf, int sy
 template <int R>
 __device__ __forceinline__ float* psi_lane(const PassArgs& a, int sys) {
   const size_t band = (size_t)a.P * R * R * 32;
-  return a.psi + (size_t)(sys >> 5) * band + (sys & 31);
+  return a.psi + fac_slot(a, sys) * band + (sys & 31);
 }
 // With a.fac set it also keeps, per interior entry, the factor row, z0 and
 // Phi for k_backsub, and psi for the last r interior entries.
@@ -1422,8 +1433,10 @@ __device__ __forceinline__ void band_chain(const PassArgs& a, int bx, float* sme
 // refinement's second solve); 3: kept, a vector guidance of a.gc planes.
 // One instantiation per mode keeps the unused sweeps out of each kernel's
 // code.
+// Returns true (in every thread) when this block completed its band: it
+// solved the band's reduced system, or the band has a single chunk group.
 template <int R, int CC, int SM>
-__device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, float* smem) {
+__device__ __forceinline__ bool body_summary(const PassArgs& a, int bx, int by, float* smem) {
   using F = Fields<R, CC>;
   using MF = MFields<R, CC>;
   const int lane = threadIdx.x;
@@ -1461,7 +1474,7 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   }
   __syncthreads();
   merge_tree<R, CC>(a, csum, lane, sys, grp, c0, nch, G, active);
-  if (a.ngroups < 2) return;   // one group: no reduced system
+  if (a.ngroups < 2) return true;   // one group: no reduced system
   // The last block of this band of 32 subsystems to finish (an atomic ticket
   // taken after a memory fence; nothing waits) solves the band's reduced
   // system on the group separators, overlapping the other bands' work.
@@ -1470,10 +1483,11 @@ __device__ __forceinline__ void body_summary(const PassArgs& a, int bx, int by, 
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) s_last = atomicAdd(&a.band_cnt[bx], 1) == a.ngroups - 1;
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();
   band_chain<R, CC>(a, bx, smem);
   if (threadIdx.x == 0 && threadIdx.y == 0) a.band_cnt[bx] = 0;   // ready for the next pass
+  return true;
 }
 
 template <int R, int CC, int SM>
@@ -2166,6 +2180,101 @@ template <int R, int CC, int MODE>
 __global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArgs a) {
   extern __shared__ float smem[];
   body_backsub<R, CC, MODE>(a, blockIdx.x, blockIdx.y, smem);
+}
+
+// ---------------------------------------------------------------------------
+// k_pass_q: one forward pass (sliding step 1, kept chunk factors) as a
+// single persistent kernel.  Its blocks take work items from an atomic
+// queue in the order of QueueSched (sgwls_sched.h): summary items (the body
+// of k_summary for one chunk group of one band, the band's last one solving
+// its reduced system) and back-substitution items (the body of k_backsub)
+// a few bands behind them.  Compared with the two-kernel pass the factors of
+// a band are read back soon after they are written, so with the factor
+// store a ring of a.nslot band slots they stay in L2 instead of streaming
+// through HBM, and the summary and back-substitution work of different
+// bands share the SMs (no wave tail between two grids).  A back-substitution
+// item waits for its bands' done flags; a summary item whose ring slot still
+// holds an older band waits until that band's readers finished.  Both waits
+// are bounded (wait_geq); a block whose wait gives up skips its item.
+// Grid: at most the resident blocks; block (32, G).
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool flag_set(const unsigned* err) {
+  return *reinterpret_cast<const volatile unsigned*>(err) != 0u;
+}
+
+template <int R, int CC>
+__global__ void __launch_bounds__(256) k_pass_q(const __grid_constant__ PassArgs a) {
+  extern __shared__ float smem[];
+  __shared__ int s_item, s_ok;
+  QueueSched q;
+  q.nb = (a.nsys + 31) >> 5;
+  q.OB = 32 - 2 * R;
+  q.nbx = (a.D + q.OB - 1) / q.OB;
+  q.NG = a.ngroups;
+  q.LA = a.lookahead;
+  q.r = R;
+  const int total = q.total();
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+  griddep_wait();     // the queue words were reset by the previous pass's last block
+  griddep_launch();
+  for (;;) {
+    if (lead) s_item = atomicAdd(&a.qctl[0], 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;   // uniform
+    int band, bx, grp;
+    if (q.decode(item, &band, &bx, &grp)) {
+      if (lead) {
+        bool ok = !flag_set(a.err);
+        if (ok && a.nslot > 0 && band >= a.nslot) {
+          const int old = band - a.nslot;   // the band whose factors occupy this slot
+          ok = wait_geq(&a.rdcnt[old], q.NG * q.readers(old), a.err, 1u);
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (s_ok) {
+        const bool done = body_summary<R, CC, 1>(a, band, grp, smem);
+        __threadfence();
+        __syncthreads();
+        if (done && lead) st_release(&a.done[band], 1);
+      }
+    } else {
+      const int blo = q.band_lo(bx), bhi = q.band_hi(bx);
+      if (lead)
+        s_ok = !flag_set(a.err) && wait_geq(&a.done[blo], 1, a.err, 2u) && wait_geq(&a.done[bhi], 1, a.err, 2u);
+      __syncthreads();
+      if (s_ok) body_backsub<R, CC, 0>(a, bx, grp, smem);
+      __syncthreads();   // every thread's factor loads have returned
+      if (lead) {
+        __threadfence();
+        atomicAdd(&a.rdcnt[blo], 1);
+        if (bhi != blo) atomicAdd(&a.rdcnt[bhi], 1);
+      }
+    }
+    __syncthreads();
+  }
+  // The last block to leave resets the control words for the next pass
+  // (which reads them only after its griddep_wait).
+  __syncthreads();
+  if (lead) {
+    __threadfence();
+    s_item = atomicAdd(&a.qctl[1], 1) == (int)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_item) {
+    const int nt = blockDim.x * blockDim.y;
+    for (int b = threadIdx.y * 32 + threadIdx.x; b < q.nb; b += nt) {
+      a.done[b] = 0;
+      a.rdcnt[b] = 0;
+    }
+    if (lead) {
+      a.qctl[0] = 0;
+      a.qctl[1] = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

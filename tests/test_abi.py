@@ -205,8 +205,13 @@ def test_batched_validation_host_only(capi):
     assert lib.sgwls_batched_workspace_bytes(2, good, ctypes.byref(p)) > 0
     assert lib.sgwls_filter_batched(0, good, ctypes.byref(p), ctypes.c_void_p(0x100000), 1 << 30,
                                     ctypes.c_void_p(0)) == E_INVALID
-    assert call([{}, {"C": 2}]) == E_UNSUP                 # every image the same channel count
-    assert call([{"C": 5}]) == E_UNSUP                     # one channel group per batched call
+    # any channel counts: the workspace holds one uniform batch per channel-group size
+    mixed = table([{}, {"C": 3}, {"C": 5}])
+    n_mixed = lib.sgwls_batched_workspace_bytes(3, mixed, ctypes.byref(p))
+    n_one = lib.sgwls_batched_workspace_bytes(1, table([{}]), ctypes.byref(p))
+    assert n_mixed > n_one > 0 and n_mixed % 256 == 0
+    assert call([{"C": 65}]) == E_SHAPE
+    assert call([{"u": 0x2000}]) == E_INVALID              # output aliases the guidance
     assert call([{"C": 0}]) == E_SHAPE
     assert call([{}, {"H": 4}]) == E_SHAPE                 # smaller than 2r+1
     assert call([{"f": 0}]) == E_INVALID

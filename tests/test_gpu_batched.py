@@ -143,3 +143,34 @@ def test_batched_full_uneven_workload(api):
         x = imgs[b].astype(np.float64)
         ref = sgwls(x, x[0], lams[b], prm)
         assert float(np.abs(outs[b].cpu().numpy().astype(np.float64) - ref).max()) <= TOL, x.shape
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_batched_mixed_channel_counts(api, r):
+    """Images of 1, 3, 5 and 6 channels (channel groups of 1, 3, 4 + 1 and
+    4 + 2) of uneven sizes in one call: every image against the oracle, and
+    the launch count: one uniform batch per channel-group size present
+    (sizes 1, 2, 3, 4), each two launches per pass."""
+    import torch
+    rng = np.random.default_rng(70 + r)
+    imgs, guides, lams = [], [], []
+    for b, C in enumerate([1, 3, 5, 6, 3, 1]):
+        H, W = (int(x) for x in rng.integers(2 * r + 5, 80, size=2))
+        rgb = synth.rgb_scene(H, W, seed=700 + b, n_rect=8, n_disk=2)
+        x = np.concatenate([rgb, rgb[::-1], rgb])[:C].copy()
+        imgs.append(x)
+        guides.append(synth.luminance(rgb))
+        lams.append(float(rng.uniform(0.5, 3.0)))
+    fs = [torch.from_numpy(x).cuda() for x in imgs]
+    gs = [torch.from_numpy(x).cuda() for x in guides]
+    kw = dict(r=r, iters=2, sigma_r=0.1)
+    n0 = api.launch_count()
+    outs = api.sgwls_filter_batched(fs, gs, lams, **kw)
+    torch.cuda.synchronize()
+    n1 = api.launch_count()
+    assert n1 - n0 <= 4 * 2 * 2 * 2   # 4 group sizes x 4 passes x at most 2 kernels
+    prm = Params(r=r, iters=2, sigma_s=float(r), sigma_r=0.1)
+    for x, g, lam, u in zip(imgs, guides, lams, outs):
+        ref = sgwls(x.astype(np.float64), g.astype(np.float64), lam, prm)
+        err = float(np.abs(u.cpu().numpy().astype(np.float64) - ref).max())
+        assert err <= TOL, (x.shape, err)
