@@ -706,42 +706,57 @@ def _timed(fn, steps, warmup, flush, stream):
 def run_fwd_bwd(sg, dev, stream, flush, steps, warmup):
     """Forward + backward of 16 RGB 512 x 512 images (r = 1, T = 3, loss
     sum((U - target)^2); gradients with respect to f, the guidance and
-    lambda through the C ABI, checkpoints kept by the forward).  Roofline
-    over the whole step: 2T forward passes at 28 B/px (RGB FP32 estimate in
-    and out, luminance guidance) and 2T backward passes at 48 B/px
-    (checkpoint, guidance, u-bar in, f-bar out, g-bar read and written)."""
+    lambda): the batched forward with per-image checkpoints, the loss
+    gradient 2 (U - target), the batched backward (every pass one launch per
+    kernel over all images).  The same step as a loop of single-image calls
+    is reported beside it.  Roofline over the whole step: 2T forward passes
+    at 28 B/px (RGB FP32 estimate in and out, luminance guidance) and 2T
+    backward passes at 48 B/px (checkpoint, guidance, u-bar in, f-bar out,
+    g-bar read and written)."""
     import torch
 
     import synth
     F, Tg = synth.diff_batch(n=DIFF["n"], H=DIFF["H"], W=DIFF["W"], seed=DIFF["seed"])
-    fs = torch.from_numpy(F).to(dev)
-    ts = torch.from_numpy(Tg).to(dev)
-    gs = torch.stack([torch.from_numpy(synth.luminance(x)) for x in F]).to(dev)
+    n = DIFF["n"]
+    fs = [torch.from_numpy(F[b]).to(dev) for b in range(n)]
+    ts = [torch.from_numpy(Tg[b]).to(dev) for b in range(n)]
+    gs = [torch.from_numpy(synth.luminance(F[b])).to(dev) for b in range(n)]
+    lams = [DIFF["lam"]] * n
     kw = dict(r=DIFF["r"], iters=DIFF["iters"], sigma_r=DIFF["sigma_r"])
     T = DIFF["iters"]
-    saved = torch.empty((2 * T, 3, DIFF["H"], DIFF["W"]), device=dev)
-    u = torch.empty_like(fs[0])
+    saveds = [torch.empty((2 * T, 3, DIFF["H"], DIFF["W"]), device=dev) for _ in range(n)]
+    us = [torch.empty_like(x) for x in fs]
+    gus = [torch.empty_like(x) for x in fs]
 
     def fwd_bwd(i):
-        for b in range(fs.shape[0]):
-            sg.sgwls_filter(fs[b], gs[b], DIFF["lam"], out=u, saved=saved, stream=stream, **kw)
-            gu = 2.0 * (u - ts[b])
-            sg.sgwls_filter_backward(gu, gs[b], saved, DIFF["lam"], stream=stream, **kw)
+        sg.sgwls_filter_batched(fs, gs, lams, outs=us, saveds=saveds, stream=stream, **kw)
+        for b in range(n):
+            torch.mul(torch.sub(us[b], ts[b]), 2.0, out=gus[b])
+        sg.sgwls_filter_backward_batched(gus, gs, saveds, lams, stream=stream, **kw)
+
+    def fwd_bwd_single(i):
+        for b in range(n):
+            sg.sgwls_filter(fs[b], gs[b], DIFF["lam"], out=us[b], saved=saveds[b], stream=stream, **kw)
+            torch.mul(torch.sub(us[b], ts[b]), 2.0, out=gus[b])
+            sg.sgwls_filter_backward(gus[b], gs[b], saveds[b], DIFF["lam"], stream=stream, **kw)
 
     def fwd_only(i):
-        for b in range(fs.shape[0]):
-            sg.sgwls_filter(fs[b], gs[b], DIFF["lam"], out=u, stream=stream, **kw)
+        sg.sgwls_filter_batched(fs, gs, lams, outs=us, stream=stream, **kw)
 
-    npx = DIFF["n"] * DIFF["H"] * DIFF["W"]
+    npx = n * DIFF["H"] * DIFF["W"]
     mp = npx / 1e6 * T
     ms_fb = _timed(fwd_bwd, steps, warmup, flush, stream) / steps
+    ms_fb1 = _timed(fwd_bwd_single, steps, warmup, flush, stream) / steps
     ms_f = _timed(fwd_only, steps, warmup, flush, stream) / steps
     peak, _, kind = _peaks()
     step_bytes = npx * 2 * T * (28 + 48)
     achieved = step_bytes / (ms_fb / 1e3) / 1e9
     return {"workload": DIFF["name"] + ": 16 x RGB 512x512, luminance guidance, r=1, T=3, loss sum((U - target)^2), "
-                                       "gradients w.r.t. f, g and lambda",
-            "value": mp / (ms_fb / 1e3), "unit": UNIT, "ms_per_step": ms_fb, "fwd_value": mp / (ms_f / 1e3),
+                                       "gradients w.r.t. f, g and lambda; batched forward (checkpoints) + batched "
+                                       "backward",
+            "value": mp / (ms_fb / 1e3), "unit": UNIT, "ms_per_step": ms_fb,
+            "single_calls_value": mp / (ms_fb1 / 1e3), "speedup_vs_single_calls": ms_fb1 / ms_fb,
+            "fwd_value": mp / (ms_f / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "whole forward + backward step (16 images)",
                          "peak_source": f"{kind} hbm_gbs", "algorithmic_bytes_per_step": step_bytes}}
@@ -890,6 +905,18 @@ def run_secondary(sg, dev, stream, flush, steps=5, warmup=2):
     ms_c = _timed(rgbg, steps, warmup, flush, stream) / steps
     out["rgb_guidance"] = {"workload": "1024x768 RGB r=1 T=3 guided by the RGB image itself (3 guidance planes)",
                            "value": mp3 / (ms_c / 1e3), "unit": UNIT, "ms_per_step": ms_c}
+
+    # the line-relaxation variant (opt-in; not the paper's subsystem): one
+    # banded system per image line per pass, off-line neighbours at their
+    # current estimates
+    kwl = dict(r=1, iters=3, sigma_r=0.1)
+
+    def lrelax(i):
+        sg.sgwls_line_relax(f3, g3, (0.5, 2.0)[i % 2], out=u3, stream=stream, **kwl)
+
+    ms_l = _timed(lrelax, steps, warmup, flush, stream) / steps
+    out["line_relax"] = {"workload": "1024x768 RGB r=1 T=3, line-relaxation variant (one thread per line)",
+                         "value": mp3 / (ms_l / 1e3), "unit": UNIT, "ms_per_step": ms_l}
     del f3, g3, u3
     return out
 

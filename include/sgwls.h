@@ -204,7 +204,9 @@ typedef struct {
   void* u;         /* C x H x W output (p->storage), not aliasing f  */
   int H, W, C;     /* any channel count 1 <= C <= SGWLS_C_MAX per image */
   float lambda;    /* per-image lambda >= 0                           */
-  void* saved;     /* must be NULL (no checkpoints in batched calls)  */
+  void* saved;     /* NULL, or 2*iters*C*H*W elements (p->inter_storage)
+                      receiving the input estimate of every pass, as the
+                      `saved` argument of sgwls_filter               */
 } sgwls_image;
 
 /* Guided sparse interpolation (Sec. 2.3, Eq. 21): the SG-WLS filter applied
@@ -278,6 +280,60 @@ size_t sgwls_backward_workspace_bytes(int H, int W, int C, const sgwls_params* p
 sgwls_status sgwls_filter_backward(const void* grad_u, const void* g, const void* saved, int H, int W, int C,
                                    float lambda, const sgwls_params* p, void* grad_f, void* grad_g,
                                    float* grad_lambda, void* ws, size_t ws_bytes, void* stream);
+
+/* Line relaxation of the 2D WLS model: an opt-in variant, NOT the paper's
+ * SG-WLS subsystem (Sec. 2.1 solves the whole (2r+1)-line zig-zag strip).
+ * It reads "each pass solves one 1D system per line with the off-line
+ * neighbours at their current estimates" as a block-Jacobi iteration on the
+ * dense 2D WLS system of Eqs. 1-4 (A = I + lambda L over the (2r+1) x (2r+1)
+ * square neighbourhood, Eq. 2 weights): every pass solves, for each row (row
+ * direction) or column (column direction),
+ *   (1 + lambda sum_{q in N(p)} w_pq) u_p - lambda sum_{q on the line} w_pq u_q
+ *       = F_p + lambda sum_{q off the line} w_pq U_q,
+ * F the input, U the estimate the pass starts from (U = F before the first
+ * pass); 2 * iters passes in the order of axis_order.  Repeated, it
+ * converges to the 2D WLS solution A^-1 F.
+ *   f, u  device FP32 C x H x W (u may alias neither f nor g); g: device
+ *         FP32 H x W guidance
+ *   p     as sgwls_filter; FP32 storage, r <= 4, step 1, no refinement, one
+ *         guidance plane (else SGWLS_E_UNSUPPORTED)
+ *   ws    workspace of sgwls_line_relax_workspace_bytes bytes, 256-byte
+ *         aligned.  Asynchronous on `stream`. */
+size_t sgwls_line_relax_workspace_bytes(int H, int W, int C, const sgwls_params* p);
+sgwls_status sgwls_line_relax(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
+                              const sgwls_params* p, void* ws, size_t ws_bytes, void* stream);
+
+/* One image of a batched backward (all pointers device pointers, FP32). */
+typedef struct {
+  const float* grad_u;   /* C x H x W, dLoss/du                                  */
+  const float* g;        /* H x W guidance of the forward call                   */
+  const float* saved;    /* 2*iters*C*H*W checkpoints of the forward call          */
+  float* grad_f;         /* C x H x W output, dLoss/df (may not alias grad_u)       */
+  float* grad_g;         /* H x W output, dLoss/dg, or NULL                        */
+  float* grad_lambda;    /* one float, dLoss/dlambda, or NULL                      */
+  int H, W, C;           /* any channel count 1 <= C <= SGWLS_C_MAX                 */
+  float lambda;          /* the image's lambda of the forward call                  */
+} sgwls_grad_image;
+
+/* Workspace bytes sgwls_filter_backward_batched needs (0 if the arguments
+ * are invalid).  Host-only; `imgs` is a host array. */
+size_t sgwls_backward_batched_workspace_bytes(int B, const sgwls_grad_image* imgs, const sgwls_params* p);
+
+/* Reverse-mode derivative of a batched forward (sgwls_filter_batched with
+ * checkpoints) for B images of uneven sizes and channel counts: per image
+ * what sgwls_filter_backward computes (the paper has no backward pass; the
+ * chain rule through Eqs. 2, 4, 5 and Sec. 2.3), with every pass of every
+ * image run together: one launch that divides each image's dLoss/d(pass
+ * output) by its subsystem counts, then one launch per kernel over the
+ * channel groups (u and v of up to three channels at r = 1, two otherwise,
+ * solved against one factorisation) of all images, per group size.
+ * Parameters as sgwls_filter_backward (FP32 storage; frac weights need
+ * alpha_r >= 1); ws: sgwls_backward_batched_workspace_bytes bytes, 256-byte
+ * aligned.  Gradients w.r.t. g and lambda are accumulated with
+ * floating-point atomics: their last bits depend on the order of
+ * accumulation. */
+sgwls_status sgwls_filter_backward_batched(int B, const sgwls_grad_image* imgs, const sgwls_params* p, void* ws,
+                                           size_t ws_bytes, void* stream);
 
 /* One pass like sgwls_filter_pass, for callers that cannot allocate device
  * memory when they filter (a host with a fixed device-memory budget, or a

@@ -278,10 +278,12 @@ def sgwls(f: torch.Tensor, g: torch.Tensor, lam, **kw) -> torch.Tensor:
     return sgwls_filter(f, g, float(lam), **kw)
 
 
-def _image_table(fs, gs, lams, outs):
+def _image_table(fs, gs, lams, outs, saveds=None, iters=1, inter_bf16=False):
     n = len(fs)
     if not (len(gs) == n and len(lams) == n and len(outs) == n):
         raise ValueError("fs, gs, lams (and outs) must have the same length")
+    if saveds is not None and len(saveds) != n:
+        raise ValueError("saveds must have one entry per image")
     tab = (_capi.SgwlsImage * n)()
     for i, (f, g, lam, u) in enumerate(zip(fs, gs, lams, outs)):
         _check_tensor(f, f"fs[{i}]")
@@ -295,6 +297,13 @@ def _image_table(fs, gs, lams, outs):
         tab[i].H, tab[i].W, tab[i].C = H, W, C
         tab[i].lam = float(lam)
         tab[i].saved = None
+        if saveds is not None and saveds[i] is not None:
+            sv = saveds[i]
+            _check_tensor(sv, f"saveds[{i}]")
+            sdt = torch.bfloat16 if inter_bf16 else torch.float32
+            if sv.dtype != sdt or sv.numel() < 2 * iters * C * H * W:
+                raise ValueError(f"saveds[{i}] must hold 2*iters*C*H*W = {2 * iters * C * H * W} elements of {sdt}")
+            tab[i].saved = sv.data_ptr()
     return tab
 
 
@@ -304,18 +313,21 @@ def batched_workspace_bytes(fs, gs, lams, **kw) -> int:
     return int(_capi.lib().sgwls_batched_workspace_bytes(len(fs), tab, ctypes.byref(p)))
 
 
-def sgwls_filter_batched(fs, gs, lams, *, outs=None, workspace: torch.Tensor | None = None,
+def sgwls_filter_batched(fs, gs, lams, *, outs=None, saveds=None, workspace: torch.Tensor | None = None,
                          stream: torch.cuda.Stream | None = None, autotune=None, **kw):
-    """SG-WLS of many images of uneven sizes through ``sgwls_filter_batched``
-    (one launch per kernel per pass over all images).  fs / gs / lams:
-    sequences of (C,H,W) inputs, (H,W) guidance tensors and lambdas."""
+    """SG-WLS of many images of uneven sizes and channel counts through
+    ``sgwls_filter_batched`` (per pass one launch per kernel per
+    channel-group size).  fs / gs / lams: sequences of (C,H,W) inputs, (H,W)
+    guidance tensors and lambdas; ``saveds`` (optional): per image a tensor
+    of 2*iters*C*H*W elements receiving the per-pass checkpoints that
+    ``sgwls_filter_backward_batched`` reads."""
     if outs is None:
         outs = [torch.empty_like(f) for f in fs]
     kw.setdefault("storage", "bf16" if fs[0].dtype == torch.bfloat16 else "f32")
     kw = _tuned("batched", autotune, lambda: autotune_mod.batched_key(fs, kw),
                 lambda: autotune_mod.tune_batched(fs, gs, lams, **kw), kw)
-    tab = _image_table(fs, gs, lams, outs)
     p = make_params(**kw)
+    tab = _image_table(fs, gs, lams, outs, saveds, p.iters, p.inter_storage == _capi.BF16)
     lib = _capi.lib()
     nws = lib.sgwls_batched_workspace_bytes(len(fs), tab, ctypes.byref(p))
     if workspace is None or workspace.numel() < nws:
@@ -325,6 +337,81 @@ def sgwls_filter_batched(fs, gs, lams, *, outs=None, workspace: torch.Tensor | N
                                       ctypes.c_size_t(workspace.numel()), ctypes.c_void_p(st.cuda_stream))
     _capi.check(status, "sgwls_filter_batched")
     return outs
+
+
+def sgwls_line_relax(f: torch.Tensor, g: torch.Tensor, lam: float, *, out: torch.Tensor | None = None,
+                     workspace: torch.Tensor | None = None, stream: torch.cuda.Stream | None = None,
+                     **kw) -> torch.Tensor:
+    """Line relaxation of the 2D WLS model through ``sgwls_line_relax`` (an
+    opt-in variant, not the paper's SG-WLS: one banded system per image line
+    per pass, off-line neighbours at their current estimates).  f: (C,H,W)
+    or (H,W) float32; g: (H,W) float32.  Keyword parameters: see
+    ``make_params`` (r <= 4)."""
+    _check_tensor(f, "f")
+    _check_tensor(g, "g")
+    C, H, W = _chw(f)
+    if tuple(g.shape) != (H, W) or f.dtype != torch.float32 or g.dtype != torch.float32:
+        raise ValueError("f must be float32 and g a float32 (H, W) guidance")
+    p = make_params(**kw)
+    lib = _capi.lib()
+    if out is None:
+        out = torch.empty_like(f)
+    else:
+        _check_like(out, f, "out")
+    nws = lib.sgwls_line_relax_workspace_bytes(H, W, C, ctypes.byref(p))
+    if workspace is None or workspace.numel() < nws:
+        workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=f.device)
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    status = lib.sgwls_line_relax(ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), H, W, C, ctypes.c_float(float(lam)),
+                                  ctypes.byref(p), ctypes.c_void_p(workspace.data_ptr()),
+                                  ctypes.c_size_t(workspace.numel()), ctypes.c_void_p(st.cuda_stream))
+    _capi.check(status, "sgwls_line_relax")
+    return out
+
+
+def sgwls_filter_backward_batched(grad_us, gs, saveds, lams, *, stream: torch.cuda.Stream | None = None,
+                                  workspace: torch.Tensor | None = None, **kw):
+    """dLoss/df, dLoss/dg, dLoss/dlambda of many images through
+    ``sgwls_filter_backward_batched``: grad_us (C,H,W) FP32 per image, gs
+    (H,W) FP32, saveds the per-image checkpoints written by
+    ``sgwls_filter_batched(..., saveds=...)``, lams the forward lambdas.
+    Returns three lists (grad_f, grad_g, grad_lambda as 0-d tensors)."""
+    n = len(grad_us)
+    if not (len(gs) == n and len(saveds) == n and len(lams) == n):
+        raise ValueError("grad_us, gs, saveds and lams must have the same length")
+    p = make_params(**kw)
+    tab = (_capi.SgwlsGradImage * n)()
+    gfs, ggs, gls = [], [], []
+    for i, (gu, g, sv, lam) in enumerate(zip(grad_us, gs, saveds, lams)):
+        for x, name in ((gu, "grad_us"), (g, "gs"), (sv, "saveds")):
+            _check_tensor(x, f"{name}[{i}]")
+            if x.dtype != torch.float32:
+                raise TypeError(f"{name}[{i}] must be float32 for the backward")
+        C, H, W = _chw(gu)
+        if tuple(g.shape) != (H, W):
+            raise ValueError(f"gs[{i}] must be (H, W)")
+        if sv.numel() < 2 * p.iters * C * H * W:
+            raise ValueError(f"saveds[{i}] must hold 2*iters*C*H*W elements")
+        gf = torch.empty_like(gu)
+        gg = torch.empty((H, W), dtype=torch.float32, device=gu.device)
+        gl = torch.empty((), dtype=torch.float32, device=gu.device)
+        gfs.append(gf)
+        ggs.append(gg)
+        gls.append(gl)
+        tab[i].grad_u, tab[i].g, tab[i].saved = gu.data_ptr(), g.data_ptr(), sv.data_ptr()
+        tab[i].grad_f, tab[i].grad_g, tab[i].grad_lambda = gf.data_ptr(), gg.data_ptr(), gl.data_ptr()
+        tab[i].H, tab[i].W, tab[i].C = H, W, C
+        tab[i].lam = float(lam)
+    lib = _capi.lib()
+    nws = lib.sgwls_backward_batched_workspace_bytes(n, tab, ctypes.byref(p))
+    if workspace is None or workspace.numel() < nws:
+        workspace = torch.empty(max(nws, 1), dtype=torch.uint8, device=grad_us[0].device)
+    st = stream if stream is not None else torch.cuda.current_stream(grad_us[0].device)
+    status = lib.sgwls_filter_backward_batched(n, tab, ctypes.byref(p), ctypes.c_void_p(workspace.data_ptr()),
+                                               ctypes.c_size_t(workspace.numel()), ctypes.c_void_p(st.cuda_stream))
+    _capi.check(status, "sgwls_filter_backward_batched")
+    return gfs, ggs, gls
 
 
 from .shard import sgwls_filter_sharded  # noqa: E402  (one image over several ranks)

@@ -70,6 +70,23 @@ class SgwlsImage(ctypes.Structure):
     ]
 
 
+class SgwlsGradImage(ctypes.Structure):
+    """Mirror of ``sgwls_grad_image`` (one entry of a batched backward)."""
+
+    _fields_ = [
+        ("grad_u", ctypes.c_void_p),
+        ("g", ctypes.c_void_p),
+        ("saved", ctypes.c_void_p),
+        ("grad_f", ctypes.c_void_p),
+        ("grad_g", ctypes.c_void_p),
+        ("grad_lambda", ctypes.c_void_p),
+        ("H", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("C", ctypes.c_int),
+        ("lam", ctypes.c_float),
+    ]
+
+
 class SgwlsError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -106,6 +123,14 @@ def _declare(lib):
         lib.sgwls_batched_workspace_bytes.restype = sz
         lib.sgwls_filter_batched.argtypes = [ci, ctypes.POINTER(SgwlsImage), P, vp, sz, vp]
         lib.sgwls_filter_batched.restype = ci
+    lib.sgwls_line_relax_workspace_bytes.argtypes = [ci, ci, ci, P]
+    lib.sgwls_line_relax_workspace_bytes.restype = sz
+    lib.sgwls_line_relax.argtypes = [vp, vp, vp, ci, ci, ci, cf, P, vp, sz, vp]
+    lib.sgwls_line_relax.restype = ci
+    lib.sgwls_backward_batched_workspace_bytes.argtypes = [ci, ctypes.POINTER(SgwlsGradImage), P]
+    lib.sgwls_backward_batched_workspace_bytes.restype = sz
+    lib.sgwls_filter_backward_batched.argtypes = [ci, ctypes.POINTER(SgwlsGradImage), P, vp, sz, vp]
+    lib.sgwls_filter_backward_batched.restype = ci
     if hasattr(lib, "sgwls_backward_workspace_bytes"):
         lib.sgwls_backward_workspace_bytes.argtypes = [ci, ci, ci, P]
         lib.sgwls_backward_workspace_bytes.restype = sz

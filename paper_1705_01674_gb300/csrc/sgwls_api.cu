@@ -13,6 +13,7 @@
 
 #include "../../include/sgwls.h"
 #include "sgwls_launch.cuh"
+#include "sgwls_line.cuh"
 
 namespace sgwls {
 
@@ -428,6 +429,23 @@ cudaError_t launch_batch_any(int r, int CC, const BatchArgs& ba, const BatchLaun
   }
 }
 #undef SGWLS_CASE_CC
+#define SGWLS_CASE_CC(R)                                                         \
+  case R:                                                                        \
+    switch (CC) {                                                                \
+      case 2: return launch_batch_bwd_inst<R, 2>(ba, bl, st);                    \
+      case 4: return launch_batch_bwd_inst<R, 4>(ba, bl, st);                    \
+      default: return cudaErrorInvalidValue;                                     \
+    }
+// CC: u and v planes of CC / 2 channels (6 at r = 1 only)
+cudaError_t launch_batch_bwd_any(int r, int CC, const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st) {
+  if (CC == kBwdWideRhs) return r == 1 ? launch_batch_bwd_inst<1, kBwdWideRhs>(ba, bl, st) : cudaErrorInvalidValue;
+  switch (r) {
+    SGWLS_CASE_CC(1) SGWLS_CASE_CC(2) SGWLS_CASE_CC(3) SGWLS_CASE_CC(4)
+    SGWLS_CASE_CC(5) SGWLS_CASE_CC(6) SGWLS_CASE_CC(7) SGWLS_CASE_CC(8)
+    default: return cudaErrorInvalidValue;
+  }
+}
+#undef SGWLS_CASE_CC
 
 
 // One pass along `dir` (Sec. 2.3, the four steps): out = pass(in).
@@ -682,7 +700,6 @@ sgwls_status check_batch(int B, const sgwls_image* imgs, const sgwls_params* p) 
     if (s != SGWLS_OK) return s;
     if (!im.f || !im.g || !im.u || im.f == im.u || im.g == im.u) return SGWLS_E_INVALID;
     if (!(im.lambda >= 0.f) || !isfinite(im.lambda)) return SGWLS_E_INVALID;
-    if (im.saved) return SGWLS_E_UNSUPPORTED;
   }
   return SGWLS_OK;
 }
@@ -706,18 +723,23 @@ size_t batch_workspace(int B, const sgwls_image* imgs, const sgwls_params* p) {
 // at most kGroupMax channels (views of its input and output at a channel
 // offset; same guidance and lambda), and the groups are gathered by size
 // into uniform batches, sets[CC - 1] holding the groups of CC channels.
+// strides[CC - 1][k]: elements between the per-pass checkpoints of group k
+// (its image's C H W: a group's checkpoint of pass t is its channels of the
+// image's checkpoint t).
 void channel_group_sets(int B, const sgwls_image* imgs, const sgwls_params* p,
-                        std::vector<sgwls_image> (&sets)[kGroupMax]) {
-  const size_t el = dt_size(p->storage);
+                        std::vector<sgwls_image> (&sets)[kGroupMax], std::vector<long long> (&strides)[kGroupMax]) {
+  const size_t el = dt_size(p->storage), eli = dt_size(p->inter_storage);
   for (int i = 0; i < B; ++i) {
     const sgwls_image& im = imgs[i];
-    const size_t plane = (size_t)im.H * im.W * el;
+    const size_t plane = (size_t)im.H * im.W;
     for (int c0 = 0; c0 < im.C; c0 += kGroupMax) {
       sgwls_image v = im;
       v.C = std::min(kGroupMax, im.C - c0);
-      v.f = static_cast<const char*>(im.f) + (size_t)c0 * plane;
-      v.u = static_cast<char*>(im.u) + (size_t)c0 * plane;
+      v.f = static_cast<const char*>(im.f) + (size_t)c0 * plane * el;
+      v.u = static_cast<char*>(im.u) + (size_t)c0 * plane * el;
+      v.saved = im.saved ? static_cast<char*>(im.saved) + (size_t)c0 * plane * eli : nullptr;
       sets[v.C - 1].push_back(v);
+      strides[v.C - 1].push_back((long long)im.C * (long long)plane);
     }
   }
 }
@@ -726,7 +748,8 @@ void channel_group_sets(int B, const sgwls_image* imgs, const sgwls_params* p,
 // another, each 256-byte aligned.
 size_t batch_workspace_any(int B, const sgwls_image* imgs, const sgwls_params* p) {
   std::vector<sgwls_image> sets[kGroupMax];
-  channel_group_sets(B, imgs, p, sets);
+  std::vector<long long> strides[kGroupMax];
+  channel_group_sets(B, imgs, p, sets, strides);
   size_t off = 0;
   for (auto& v : sets)
     if (!v.empty()) off = align256(off + batch_workspace((int)v.size(), v.data(), p));
@@ -735,17 +758,21 @@ size_t batch_workspace_any(int B, const sgwls_image* imgs, const sgwls_params* p
 
 }  // namespace
 
-sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st);
+sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st,
+                         const long long* saved_stride);
 
 // Batched filter of images of any channel counts: one uniform batch per
 // channel-group size present (see channel_group_sets).
 sgwls_status run_batched_any(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st) {
   std::vector<sgwls_image> sets[kGroupMax];
-  channel_group_sets(B, imgs, p, sets);
+  std::vector<long long> strides[kGroupMax];
+  channel_group_sets(B, imgs, p, sets, strides);
   size_t off = 0;
-  for (auto& v : sets) {
+  for (int k = 0; k < kGroupMax; ++k) {
+    std::vector<sgwls_image>& v = sets[k];
     if (v.empty()) continue;
-    const sgwls_status s = run_batched((int)v.size(), v.data(), p, static_cast<char*>(ws) + off, st);
+    const sgwls_status s =
+        run_batched((int)v.size(), v.data(), p, static_cast<char*>(ws) + off, st, strides[k].data());
     if (s != SGWLS_OK) return s;
     off = align256(off + batch_workspace((int)v.size(), v.data(), p));
   }
@@ -753,7 +780,9 @@ sgwls_status run_batched_any(int B, const sgwls_image* imgs, const sgwls_params*
 }
 
 // A uniform batch: every image has the same channel count C <= kGroupMax.
-sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st) {
+// saved_stride[i] (null: C H W): elements between image i's checkpoints.
+sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, cudaStream_t st,
+                         const long long* saved_stride) {
   const int C = imgs[0].C;
   const int r = p->r;
   const int sdt = p->storage, idt = p->inter_storage;
@@ -784,6 +813,12 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
     cudaError_t e = cudaMemsetAsync(wsb, 0, ncnt, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
+  // checkpoints: pass 0's input is a copy of f
+  for (int i = 0; i < B; ++i) {
+    if (!imgs[i].saved) continue;
+    const sgwls_status s = copy_image(imgs[i].f, sdt, imgs[i].saved, idt, (long long)imgs[i].H * imgs[i].W * C, st);
+    if (s != SGWLS_OK) return s;
+  }
   static thread_local BatchArgs batch_args;   // host-side argument block (the kernels get a copy)
   BatchArgs* ba = &batch_args;
   for (int t = 0; t < npass; ++t) {
@@ -811,10 +846,15 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
         const size_t count = (size_t)im.H * im.W * C;
         const size_t ib = count * dt_size(idt);
         void* img = wsb + lo.img;
+        // with checkpoints, pass t reads checkpoint t and writes checkpoint t + 1
+        char* const sv = static_cast<char*>(im.saved);
+        const size_t sb = (size_t)(saved_stride ? saved_stride[i0 + k] : (long long)count) * dt_size(idt);
         const void* src;
         void* dst;
         if (t == 0) {
           src = im.f;
+        } else if (sv) {
+          src = sv + (size_t)t * sb;
         } else if (idt == sdt) {
           src = ((npass - t) & 1) ? img : im.u;
         } else {
@@ -822,6 +862,8 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
         }
         if (t == npass - 1) {
           dst = im.u;
+        } else if (sv) {
+          dst = sv + (size_t)(t + 1) * sb;
         } else if (idt == sdt) {
           dst = ((npass - 1 - t) & 1) ? img : im.u;
         } else {
@@ -1011,6 +1053,353 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
   return SGWLS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched backward: the adjoint of a batched forward, every pass one launch
+// per kernel over all images (grouped by channel-group size).
+
+namespace {
+
+constexpr int kScaleMax = 64;   // images per batched scale launch
+
+// Every image's vbar / count of one pass direction (k_bwd_scale over a batch:
+// a flat index over all images' elements, the image by binary search).
+struct ScaleTab {
+  int n, r, dir;
+  const float* vin[kScaleMax];
+  float* vout[kScaleMax];
+  int H[kScaleMax], W[kScaleMax];
+  long long start[kScaleMax + 1];   // first element of each image
+};
+
+__global__ void k_bwd_scale_b(const __grid_constant__ ScaleTab t) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.start[t.n]) return;
+  int lo = 0, hi = t.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.start[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  const long long k = i - t.start[lo];
+  const int H = t.H[lo], W = t.W[lo];
+  const long long pix = k % ((long long)H * W);
+  const int y = (int)(pix / W), x = (int)(pix - (long long)y * W);
+  const int o = t.dir == 0 ? x : y;
+  const int D = t.dir == 0 ? W : H;
+  const int lo_c = max(t.r, o - t.r), hi_c = min(D - 1 - t.r, o + t.r);
+  t.vout[lo][k] = t.vin[lo][k] / (float)(hi_c - lo_c + 1);
+}
+
+// Lines per chunk of a batched adjoint pass (blocks of kGMax chunks).
+int batch_h_bwd(int r, int CC, int chunk_lines) {
+  int h = chunk_lines > 0 ? chunk_lines : 64;
+  while (h > 1 && smem_recover(r, CC, h, kGMax, true) > kSmemBlockTarget) --h;
+  return h;
+}
+
+// One channel group of one image of a batched backward.
+struct BwdJob {
+  int img, c0, nch;
+};
+
+struct BwdBatchLayout {
+  std::vector<size_t> w0, w1, gbuf;                 // per image
+  std::vector<size_t> summ, xsep, mdata, cnt;       // per job
+  std::vector<BwdJob> jobs[kGroupMax];              // by nch - 1 (nch <= 3)
+  std::vector<size_t> jobpos[kGroupMax];            // index into summ / xsep / ...
+  size_t ncnt = 0, total = 0;
+};
+
+BwdBatchLayout bwd_batch_layout(int B, const sgwls_grad_image* imgs, const sgwls_params* p) {
+  BwdBatchLayout lo;
+  const int r = p->r;
+  const int gch = bwd_group(r);
+  std::vector<BwdJob> all;
+  for (int i = 0; i < B; ++i)
+    for (int c0 = 0; c0 < imgs[i].C; c0 += gch) all.push_back({i, c0, std::min(gch, imgs[i].C - c0)});
+  // counters of every job first (one region, cleared once per call)
+  size_t off = 0;
+  for (const BwdJob& j : all) {
+    lo.cnt.push_back(off);
+    off += counter_bytes(imgs[j.img].H, imgs[j.img].W, r);
+  }
+  lo.ncnt = off;
+  off = align256(off);
+  for (int i = 0; i < B; ++i) {
+    const size_t img = align256((size_t)imgs[i].C * imgs[i].H * imgs[i].W * sizeof(float));
+    lo.w0.push_back(off);
+    lo.w1.push_back(off + img);
+    lo.gbuf.push_back(off + 2 * img);
+    off += 2 * img + align256(((size_t)imgs[i].H * imgs[i].W + 64) * sizeof(float));
+  }
+  for (size_t k = 0; k < all.size(); ++k) {
+    const BwdJob& j = all[k];
+    const int CC = 2 * j.nch;
+    const int h0 = batch_h_bwd(r, CC, p->chunk_lines);
+    size_t summ = 0, xsep = 0, mdata = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+      const int L = dir == 0 ? imgs[j.img].H : imgs[j.img].W;
+      const int D = dir == 0 ? imgs[j.img].W : imgs[j.img].H;
+      const int nsys = ((D - 2 * r) + 31) / 32 * 32;
+      const Plan pl = batch_plan(L, r, CC, h0);
+      summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
+      xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
+      mdata = std::max(mdata, (size_t)pl.NG * (kGMax - 1) * n_mfields(r, CC) * nsys * sizeof(float));
+    }
+    lo.summ.push_back(off);
+    lo.xsep.push_back(off + align256(summ));
+    lo.mdata.push_back(off + align256(summ) + align256(xsep));
+    off += align256(summ) + align256(xsep) + align256(mdata);
+    lo.jobs[j.nch - 1].push_back(j);
+    lo.jobpos[j.nch - 1].push_back(k);
+  }
+  lo.total = off;
+  return lo;
+}
+
+sgwls_status check_batch_bwd(int B, const sgwls_grad_image* imgs, const sgwls_params* p) {
+  if (B < 1 || !imgs || !p) return SGWLS_E_INVALID;
+  sgwls_status s0 = check_params(imgs[0].H, imgs[0].W, imgs[0].C, p);
+  if (s0 != SGWLS_OK) return s0;
+  if (p->storage != SGWLS_F32 || p->inter_storage != SGWLS_F32) return SGWLS_E_UNSUPPORTED;
+  if (p->weight == SGWLS_W_FRAC && p->alpha_r < 1.f) return SGWLS_E_UNSUPPORTED;
+  if (p->step != 1 || p->refine || p->guide_channels > 1) return SGWLS_E_UNSUPPORTED;
+  for (int i = 0; i < B; ++i) {
+    const sgwls_grad_image& im = imgs[i];
+    sgwls_status s = check_params(im.H, im.W, im.C, p);
+    if (s != SGWLS_OK) return s;
+    if (!im.grad_u || !im.g || !im.grad_f || (p->iters > 0 && !im.saved)) return SGWLS_E_INVALID;
+    if (im.grad_f == im.grad_u) return SGWLS_E_INVALID;
+    if (!(im.lambda >= 0.f) || !isfinite(im.lambda)) return SGWLS_E_INVALID;
+  }
+  return SGWLS_OK;
+}
+
+}  // namespace
+
+sgwls_status run_backward_batched(int B, const sgwls_grad_image* imgs, const sgwls_params* p, void* ws,
+                                  cudaStream_t st) {
+  const BwdBatchLayout lo = bwd_batch_layout(B, imgs, p);
+  char* wsb = static_cast<char*>(ws);
+  const int r = p->r;
+  const int npass = 2 * p->iters;
+  cudaError_t e;
+  std::vector<float*> gg(B), gl(B);
+  std::vector<const float*> vbar(B);
+  for (int i = 0; i < B; ++i) {
+    const size_t plane = (size_t)imgs[i].H * imgs[i].W;
+    float* gb = reinterpret_cast<float*>(wsb + lo.gbuf[i]);
+    gg[i] = imgs[i].grad_g ? imgs[i].grad_g : gb;
+    gl[i] = imgs[i].grad_lambda ? imgs[i].grad_lambda : gb + plane;
+    if ((e = cudaMemsetAsync(gg[i], 0, plane * sizeof(float), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(gl[i], 0, sizeof(float), st)) != cudaSuccess) return cuda_fail(e);
+    vbar[i] = imgs[i].grad_u;
+    if (npass == 0) {
+      e = cudaMemcpyAsync(imgs[i].grad_f, imgs[i].grad_u, plane * imgs[i].C * sizeof(float),
+                          cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  }
+  if (npass == 0) return SGWLS_OK;
+  if ((e = cudaMemsetAsync(wsb, 0, lo.ncnt, st)) != cudaSuccess) return cuda_fail(e);
+  static thread_local ScaleTab scale_tab;
+  static thread_local BatchArgs batch_args;
+  const int OB = 32 - 2 * r;
+  for (int t = npass - 1; t >= 0; --t) {
+    const int dir = ((t & 1) == 0) ? p->axis_order : 1 - p->axis_order;
+    // vbar / count of every image, one launch per 64 images
+    for (int i0 = 0; i0 < B; i0 += kScaleMax) {
+      ScaleTab& tb = scale_tab;
+      memset(&tb, 0, sizeof(tb));
+      tb.n = std::min(kScaleMax, B - i0);
+      tb.r = r;
+      tb.dir = dir;
+      tb.start[0] = 0;
+      for (int k = 0; k < tb.n; ++k) {
+        const sgwls_grad_image& im = imgs[i0 + k];
+        tb.vin[k] = vbar[i0 + k];
+        tb.vout[k] = reinterpret_cast<float*>(wsb + lo.w0[i0 + k]);
+        tb.H[k] = im.H;
+        tb.W[k] = im.W;
+        tb.start[k + 1] = tb.start[k] + (long long)im.C * im.H * im.W;
+      }
+      k_bwd_scale_b<<<(unsigned)((tb.start[tb.n] + 255) / 256), 256, 0, st>>>(tb);
+      __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    }
+    // the adjoint pass of every channel group, one uniform batch per group size
+    for (int gsz = 1; gsz <= kGroupMax; ++gsz) {
+      const std::vector<BwdJob>& jobs = lo.jobs[gsz - 1];
+      const std::vector<size_t>& pos = lo.jobpos[gsz - 1];
+      const int CC = 2 * gsz;
+      const int h0 = batch_h_bwd(r, CC, p->chunk_lines);
+      for (size_t j0 = 0; j0 < jobs.size(); j0 += kBatchMax) {
+        const int nb = (int)std::min<size_t>(kBatchMax, jobs.size() - j0);
+        BatchArgs* ba = &batch_args;
+        memset(ba, 0, sizeof(BatchArgs));
+        PassArgs& a = ba->base;
+        a.dir = dir;
+        a.in_dt = a.out_dt = a.g_dt = DT_F32;
+        a.n_in1 = gsz;
+        a.step = 1;
+        fill_weights(a, p, 1.0f);   // sp0 (lambda applied per image)
+        ba->nimg = nb;
+        BatchLaunch bl = {};
+        bl.G = kGMax;
+        size_t red_max = 0;
+        int b[3] = {0, 0, 0};
+        for (int k = 0; k < nb; ++k) {
+          const BwdJob& jb = jobs[j0 + k];
+          const size_t q = pos[j0 + k];
+          const sgwls_grad_image& im = imgs[jb.img];
+          const size_t plane = (size_t)im.H * im.W;
+          const size_t count = plane * im.C;
+          ImgDesc& d = ba->img[k];
+          d.in = im.saved + (size_t)t * count + (size_t)jb.c0 * plane;
+          d.in2 = reinterpret_cast<const float*>(wsb + lo.w0[jb.img]) + (size_t)jb.c0 * plane;
+          d.out = (t == 0 ? im.grad_f : reinterpret_cast<float*>(wsb + lo.w1[jb.img])) + (size_t)jb.c0 * plane;
+          d.g = im.g;
+          d.grad_g = gg[jb.img];
+          d.grad_lam = gl[jb.img];
+          d.summ = reinterpret_cast<float*>(wsb + lo.summ[q]);
+          d.xsep = reinterpret_cast<float*>(wsb + lo.xsep[q]);
+          d.mdata = reinterpret_cast<float*>(wsb + lo.mdata[q]);
+          d.band_cnt = reinterpret_cast<int*>(wsb + lo.cnt[q]);
+          d.plane = (long long)plane;
+          d.H = im.H;
+          d.W = im.W;
+          d.L = dir == 0 ? im.H : im.W;
+          d.D = dir == 0 ? im.W : im.H;
+          d.nsys = d.D - 2 * r;
+          d.sstride = (d.nsys + 31) / 32 * 32;
+          const Plan pl = batch_plan(d.L, r, CC, h0);
+          d.h = pl.h;
+          d.P = pl.P;
+          d.ngroups = pl.NG;
+          d.lam = im.lambda;
+          d.nbx[0] = (d.nsys + 31) / 32;
+          d.nbx[1] = (d.nsys + 31) / 32;
+          d.nbx[2] = (d.D + OB - 1) / OB;
+          d.b0[0] = b[0];
+          d.b0[1] = b[1];
+          d.b0[2] = b[2];
+          b[0] += d.nbx[0] * pl.NG;
+          b[1] += d.nbx[1];
+          b[2] += d.nbx[2] * pl.NG;
+          bl.any_multi |= pl.P > 1;
+          bl.any_red |= pl.NG > 1;
+          red_max = std::max(red_max, (size_t)pl.NG * n_fields(r, CC) * 32 * sizeof(float));
+          bl.smem[0] = smem_summary(r, CC, h0, kGMax);
+          bl.smem[2] = smem_recover(r, CC, h0, kGMax, true);
+        }
+        bl.nblk[0] = b[0];
+        bl.nblk[1] = b[1];
+        bl.nblk[2] = b[2];
+        bl.red_smem = red_max <= kReducedSmemMax;
+        bl.smem[1] = bl.red_smem ? red_max : 0;
+        if ((e = launch_batch_bwd_any(r, CC, *ba, bl, st)) != cudaSuccess) return cuda_fail(e);
+        __atomic_add_fetch(&g_launches, (unsigned long long)(1 + (bl.any_multi ? 1 : 0)), __ATOMIC_RELAXED);
+      }
+    }
+    for (int i = 0; i < B; ++i) vbar[i] = t == 0 ? imgs[i].grad_f : reinterpret_cast<float*>(wsb + lo.w1[i]);
+  }
+  return SGWLS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Line relaxation (opt-in variant): T x (first direction, second direction)
+// block-Jacobi passes of the dense 2D WLS system, one banded solve per line.
+
+#define SGWLS_LINE_CC(R)                                                         \
+  case R:                                                                        \
+    switch (CC) {                                                                \
+      case 1: return launch_line_inst<R, 1>(a, st);                              \
+      case 2: return launch_line_inst<R, 2>(a, st);                              \
+      case 3: return launch_line_inst<R, 3>(a, st);                              \
+      case 4: return launch_line_inst<R, 4>(a, st);                              \
+      default: return cudaErrorInvalidValue;                                     \
+    }
+cudaError_t launch_line_any(int r, int CC, const LineArgs& a, cudaStream_t st) {
+  switch (r) {
+    SGWLS_LINE_CC(1) SGWLS_LINE_CC(2) SGWLS_LINE_CC(3) SGWLS_LINE_CC(4)
+    default: return cudaErrorInvalidValue;
+  }
+}
+#undef SGWLS_LINE_CC
+
+namespace {
+
+struct LineLayout {
+  size_t img, scratch, total;
+};
+
+LineLayout line_layout(int H, int W, int C, const sgwls_params* p) {
+  LineLayout lo;
+  lo.img = 0;
+  const size_t img = p->iters > 0 ? align256((size_t)C * H * W * sizeof(float)) : 0;
+  lo.scratch = img;
+  const int CCmax = std::min(kGroupMax, C);
+  lo.total = img + align256((size_t)H * W * (p->r + CCmax) * sizeof(float));
+  return lo;
+}
+
+sgwls_status check_line(int H, int W, int C, const sgwls_params* p) {
+  sgwls_status s = check_params(H, W, C, p);
+  if (s != SGWLS_OK) return s;
+  if (p->storage != SGWLS_F32 || p->inter_storage != SGWLS_F32) return SGWLS_E_UNSUPPORTED;
+  if (p->r > kLineRMax || p->step != 1 || p->refine || p->guide_channels > 1) return SGWLS_E_UNSUPPORTED;
+  return SGWLS_OK;
+}
+
+}  // namespace
+
+sgwls_status run_line_relax(const float* f, const float* g, float* u, int H, int W, int C, float lambda,
+                            const sgwls_params* p, void* ws, cudaStream_t st) {
+  const LineLayout lo = line_layout(H, W, C, p);
+  char* wsb = static_cast<char*>(ws);
+  const long long plane = (long long)H * W;
+  cudaError_t e;
+  const int npass = 2 * p->iters;
+  if (npass == 0) {
+    e = cudaMemcpyAsync(u, f, (size_t)plane * C * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? SGWLS_OK : cuda_fail(e);
+  }
+  LineArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = g;
+  a.plane = plane;
+  a.H = H;
+  a.W = W;
+  a.weight = p->weight;
+  a.range_k = p->weight == SGWLS_W_EXP ? (float)(-1.4426950408889634 / (2.0 * (double)p->sigma_r * p->sigma_r))
+                                       : p->alpha_r;
+  a.eps = p->eps;
+  const int r = p->r, S = 2 * r + 1;
+  for (int dy = -r; dy <= r; ++dy)
+    for (int dx = -r; dx <= r; ++dx) {
+      const double d2 = (double)dx * dx + (double)dy * dy;
+      const double sp = p->weight == SGWLS_W_EXP ? exp(-d2 / (2.0 * (double)p->sigma_s * p->sigma_s))
+                                                 : 1.0 / (pow(sqrt(d2), (double)p->alpha_s) + (double)p->eps);
+      a.wsp[(dy + r) * S + dx + r] = (float)(lambda * sp);
+    }
+  a.scratch = reinterpret_cast<float*>(wsb + lo.scratch);
+  float* img = reinterpret_cast<float*>(wsb + lo.img);
+  const float* cur = f;
+  for (int t = 0; t < npass; ++t) {
+    a.dir = ((t & 1) == 0) ? p->axis_order : 1 - p->axis_order;
+    float* dst = (t == npass - 1) ? u : (((npass - 1 - t) & 1) ? img : u);
+    for (int c0 = 0; c0 < C; c0 += kGroupMax) {
+      const int CC = std::min(kGroupMax, C - c0);
+      a.f = f + (size_t)c0 * plane;
+      a.uin = cur + (size_t)c0 * plane;
+      a.uout = dst + (size_t)c0 * plane;
+      if ((e = launch_line_any(r, CC, a, st)) != cudaSuccess) return cuda_fail(e);
+      __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED);
+    }
+    cur = dst;
+  }
+  return SGWLS_OK;
+}
+
 }  // namespace sgwls
 
 using namespace sgwls;
@@ -1153,6 +1542,37 @@ extern "C" {
 size_t sgwls_batched_workspace_bytes(int B, const sgwls_image* imgs, const sgwls_params* p) {
   if (check_batch(B, imgs, p) != SGWLS_OK) return 0;
   return batch_workspace_any(B, imgs, p);
+}
+
+size_t sgwls_line_relax_workspace_bytes(int H, int W, int C, const sgwls_params* p) {
+  if (check_line(H, W, C, p) != SGWLS_OK) return 0;
+  return line_layout(H, W, C, p).total;
+}
+
+sgwls_status sgwls_line_relax(const void* f, const void* g, void* u, int H, int W, int C, float lambda,
+                              const sgwls_params* p, void* ws, size_t ws_bytes, void* stream) {
+  sgwls_status s = check_line(H, W, C, p);
+  if (s != SGWLS_OK) return s;
+  if (!f || !g || !u || f == u || g == u) return SGWLS_E_INVALID;
+  if (!(lambda >= 0.f) || !isfinite(lambda)) return SGWLS_E_INVALID;
+  const size_t need = line_layout(H, W, C, p).total;
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
+  return run_line_relax(static_cast<const float*>(f), static_cast<const float*>(g), static_cast<float*>(u), H, W,
+                        C, lambda, p, ws, static_cast<cudaStream_t>(stream));
+}
+
+size_t sgwls_backward_batched_workspace_bytes(int B, const sgwls_grad_image* imgs, const sgwls_params* p) {
+  if (check_batch_bwd(B, imgs, p) != SGWLS_OK) return 0;
+  return bwd_batch_layout(B, imgs, p).total;
+}
+
+sgwls_status sgwls_filter_backward_batched(int B, const sgwls_grad_image* imgs, const sgwls_params* p, void* ws,
+                                           size_t ws_bytes, void* stream) {
+  sgwls_status s = check_batch_bwd(B, imgs, p);
+  if (s != SGWLS_OK) return s;
+  const size_t need = bwd_batch_layout(B, imgs, p).total;
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return SGWLS_E_WORKSPACE;
+  return run_backward_batched(B, imgs, p, ws, static_cast<cudaStream_t>(stream));
 }
 
 sgwls_status sgwls_filter_batched(int B, const sgwls_image* imgs, const sgwls_params* p, void* ws, size_t ws_bytes,

@@ -16,8 +16,11 @@ constexpr int kBatchMax = 64;   // images per batched launch
 
 struct ImgDesc {
   const void* in;
+  const void* in2;   // backward: the v-bar planes (null: in)
   const void* g;
   void* out;
+  float* grad_g;     // backward: this image's dLoss/dG and dLoss/dlambda
+  float* grad_lam;
   float* summ;
   float* xsep;
   float* mdata;
@@ -61,8 +64,10 @@ __device__ __forceinline__ void build_args(const BatchArgs& ba, int i, PassArgs&
   for (int k = tid; k < nsp; k += nthreads) sa.sp[k] = d.lam * ba.base.sp0[k];
   if (tid == 0) {
     sa.in = d.in;
-    sa.in2 = d.in;
+    sa.in2 = d.in2 ? d.in2 : d.in;
     sa.g = d.g;
+    sa.grad_g = d.grad_g;
+    sa.grad_lam = d.grad_lam;
     sa.out = d.out;
     sa.summ = d.summ;
     sa.xsep = d.xsep;
@@ -97,7 +102,9 @@ __global__ void __launch_bounds__(256) k_summary_b(const __grid_constant__ Batch
   body_summary<R, CC, SM>(sa, local - by * ba.img[i].nbx[0], by, smem);
 }
 
-template <int R, int CC>
+// BWD: the adjoint pass of every image (u from the checkpoint planes `in`,
+// v from the v-bar planes `in2`, gradients to the image's own buffers).
+template <int R, int CC, bool BWD = false>
 __global__ void __launch_bounds__(256) k_recover_b(const __grid_constant__ BatchArgs ba) {
   extern __shared__ float smem[];
   __shared__ PassArgs sa;
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(256) k_recover_b(const __grid_constant__ Batch
   const int local = blockIdx.x - ba.img[i].b0[2];
   const int by = local / ba.img[i].nbx[2];
   build_args(ba, i, sa);
-  body_recover<R, CC, false>(sa, local - by * ba.img[i].nbx[2], by, smem);
+  body_recover<R, CC, BWD>(sa, local - by * ba.img[i].nbx[2], by, smem);
 }
 
 template <int R, int CC>

@@ -214,6 +214,27 @@ cudaError_t launch_batch_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStre
   return cudaGetLastError();
 }
 
+// Batched adjoint pass: one launch per kernel over all images of `ba` (the
+// summaries recompute their factors; CC = u and v planes of CC / 2
+// channels).
+template <int R, int CC>
+cudaError_t launch_batch_bwd_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st) {
+  cudaError_t e;
+  BatchArgs b = ba;
+  b.base.early_stage = bl.any_multi ? 1 : 0;
+  b.base.chain_smem = bl.red_smem ? 1 : 0;
+  if (bl.any_multi) {
+    const size_t smem = bl.red_smem ? std::max(bl.smem[0], bl.smem[1]) : bl.smem[0];
+    if ((e = set_smem(k_summary_b<R, CC, 0>, smem)) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_summary_b<R, CC, 0>, dim3(bl.nblk[0]), dim3(32, bl.G), smem, st, b)) != cudaSuccess)
+      return e;
+  }
+  if ((e = set_smem(k_recover_b<R, CC, true>, bl.smem[2])) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_recover_b<R, CC, true>, dim3(bl.nblk[2]), dim3(32, bl.G), bl.smem[2], st, b)) != cudaSuccess)
+    return e;
+  return cudaGetLastError();
+}
+
 // The launchers are instantiated one (radius, channel group) per object
 // file (sgwls_inst.cu, compiled once per pair by build.py, so the builds of
 // the kernels run in parallel); the dispatchers switch on the runtime r and
@@ -223,6 +244,12 @@ template <int R, int CC>
 cudaError_t launch_pass_inst(const PassArgs& a, const Plan& pl, bool bwd, cudaStream_t st);
 template <int R, int CC>
 cudaError_t launch_batch_inst(const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st);
+template <int R, int CC>
+cudaError_t launch_batch_bwd_inst(const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st);
+cudaError_t launch_batch_bwd_any(int r, int CC, const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st);
+struct LineArgs;
+template <int R, int CC>
+cudaError_t launch_line_inst(const LineArgs& a, cudaStream_t st);
 cudaError_t launch_pass_any(int r, int CC, const PassArgs& a, const Plan& pl, cudaStream_t st);
 cudaError_t launch_batch_any(int r, int CC, const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st);
 

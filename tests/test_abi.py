@@ -218,7 +218,6 @@ def test_batched_validation_host_only(capi):
     assert call([{"u": 0x1000}]) == E_INVALID              # output aliases the input
     assert call([{"lam": -1.0}]) == E_INVALID
     assert call([{"lam": float("nan")}]) == E_INVALID
-    assert call([{"saved": 0x9000}]) == E_UNSUP            # no checkpoints in batched calls
     assert call([{}], p=capi.make_params(r=9)) == E_INVALID
     assert call([{}], p=capi.make_params(r=2, step=2)) == E_UNSUP
     bad = capi.make_params(r=2)
@@ -294,3 +293,43 @@ def test_noalloc_validation_matches_workspace_pass(capi):
                                        64, 80, 3, ctypes.c_float(1.0),
                                        ctypes.byref(capi.make_params(r=1, factor_cache=1)), 0, ctypes.c_void_p(0))
     assert st == E_UNSUP
+
+
+def test_batched_backward_validation_host_only(capi):
+    """sgwls_filter_backward_batched and its workspace query reject bad
+    tables on the host (no pointer is dereferenced)."""
+    lib = capi.lib()
+    E_INVALID, E_WS, E_UNSUP = -1, -4, -7
+
+    def table(specs):
+        tab = (capi.SgwlsGradImage * len(specs))()
+        for i, sp in enumerate(specs):
+            base = 0x100000 * (i + 1)
+            d = dict(grad_u=base, g=base + 0x1000, saved=base + 0x2000, grad_f=base + 0x3000, grad_g=0,
+                     grad_lambda=0, H=40, W=50, C=3, lam=1.0)
+            d.update(sp)
+            for k, v in d.items():
+                setattr(tab[i], "lam" if k == "lam" else k, v)
+        return tab
+
+    def call(specs, p=None, ws=0x10000000, nws=1 << 30):
+        p = p if p is not None else capi.make_params(r=1, iters=2)
+        tab = table(specs)
+        return lib.sgwls_filter_backward_batched(len(specs), tab, ctypes.byref(p), ctypes.c_void_p(ws), nws,
+                                                 ctypes.c_void_p(0))
+
+    p = capi.make_params(r=1, iters=2)
+    good = table([{}, {"C": 1, "H": 70}, {"C": 5}])
+    n = lib.sgwls_backward_batched_workspace_bytes(3, good, ctypes.byref(p))
+    assert n > 0 and n % 256 == 0
+    assert lib.sgwls_filter_backward_batched(0, good, ctypes.byref(p), ctypes.c_void_p(0x10000000), 1 << 30,
+                                             ctypes.c_void_p(0)) == E_INVALID
+    assert call([{"grad_f": 0x100000}]) == E_INVALID        # grad_f aliases grad_u
+    assert call([{"saved": 0}]) == E_INVALID                # iters > 0 needs the checkpoints
+    assert call([{"grad_u": 0}]) == E_INVALID
+    assert call([{"lam": -1.0}]) == E_INVALID
+    assert call([{}], p=capi.make_params(r=1, iters=2, storage="bf16")) == E_UNSUP
+    assert call([{}], p=capi.make_params(r=2, step=2)) == E_UNSUP
+    assert call([{}], p=capi.make_params(weight="frac", alpha_r=0.8)) == E_UNSUP
+    assert call([{}], nws=1024) == E_WS
+    assert call([{}], ws=0x10000010) == E_WS
