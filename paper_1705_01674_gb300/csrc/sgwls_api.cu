@@ -103,6 +103,17 @@ constexpr int kGMax = 8;
 // fewer than kTargetWarps chunk-warps.
 inline int keep_lines(int r) { return r == 1 ? 6 : r == 2 ? 12 : r == 3 ? 8 : 16; }
 
+// Chunk length of a sliding-step (tau > 1) pass, by radius and step: the
+// fastest of 3..12 lines on GB300 for a 1-megapixel RGB image, T = 3, with
+// tensor-copy staging (8 lines where the sweep found no better length, and
+// beyond r = 5 or tau = 5).
+inline int step_lines(int r, int step) {
+  if (r == 3) return step == 2 ? 6 : step == 3 ? 12 : 8;
+  if (r == 4) return step == 2 ? 6 : 8;
+  if (r == 5) return (step == 3 || step == 4) ? 6 : step == 5 ? 12 : 8;
+  return 8;
+}
+
 // Subsystems of a pass across D offsets with sliding step `step`: the
 // regular centres r, r + step, ... <= D-1-r, and the last centre D-1-r
 // appended when the stride misses it (every line stays covered).  *nreg:
@@ -124,10 +135,8 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G, step, gc)); };
   int h;
   if (keep && step > 1) {
-    // sliding step: fewer subsystems, so fewer warps; shorter chunks would
-    // only add merge work (8 lines measured best or near best on GB300 for
-    // r = 2..5, tau = 2..2r+1 on a 1-megapixel RGB image)
-    h = 8;
+    // sliding step: fewer subsystems, so fewer warps (see step_lines)
+    h = step_lines(r, step);
   } else if (keep) {
     h = keep_lines(r);
     while (h > 1 && (long long)L * bands / h < kTargetWarps) --h;
@@ -448,6 +457,60 @@ cudaError_t launch_batch_bwd_any(int r, int CC, const BatchArgs& ba, const Batch
 #undef SGWLS_CASE_CC
 
 
+// Tensor-copy (TMA) descriptors of the column direction's tile staging.
+// The driver's encoder is looked up once through the runtime (no link
+// against the driver library).
+using TmaEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmaEncodeFn tma_encoder() {
+  static std::once_flag once;
+  static TmaEncodeFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmaEncodeFn>(p);
+  });
+  return fn;
+}
+
+// Fills a.tm_in / a.tm_g for a column-direction pass and returns true when
+// the tensor-copy staging applies: FP32 estimate and guidance, one guidance
+// plane, one input source, rows and plane bases 16-byte aligned (W a
+// multiple of 4), the box (tile pitch x G h + 2 lines) at most 256 per
+// dimension.  Every box then starts on a 16-byte boundary (x = 32 band step,
+// or the back-substitution block's first column rounded down to 4).
+bool setup_tma(PassArgs& a, const Plan& pl, int r, int CC) {
+  if (a.dir != 0 || a.gc != 1 || a.in_dt != DT_F32 || a.g_dt != DT_F32 || a.in2 != a.in) return false;
+  if ((a.W & 3) || (reinterpret_cast<uintptr_t>(a.in) & 15) || (reinterpret_cast<uintptr_t>(a.g) & 15)) return false;
+  // the tile of a band: 32 + 2r columns at step 1, 31 step + 2r + 1 beyond
+  const int pitch = tile_pitch_n(tile_ncol(r, a.step), 0);
+  const int ntl = pl.G * pl.h + 2;
+  if (ntl > 256 || pitch > 256) return false;
+  TmaEncodeFn enc = tma_encoder();
+  if (!enc) return false;
+  const cuuint64_t W = (cuuint64_t)a.W, H = (cuuint64_t)a.H;
+  const cuuint64_t dims3[3] = {W, H, (cuuint64_t)CC};
+  const cuuint64_t str3[2] = {W * 4, W * H * 4};
+  const cuuint32_t box3[3] = {(cuuint32_t)pitch, (cuuint32_t)ntl, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  if (enc(&a.tm_in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(a.in), dims3, str3, box3, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  const cuuint64_t dims2[2] = {W, H};
+  const cuuint64_t str2[1] = {W * 4};
+  const cuuint32_t box2[2] = {(cuuint32_t)pitch, (cuuint32_t)ntl};
+  if (enc(&a.tm_g, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(a.g), dims2, str2, box2, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  return true;
+}
+
 // One pass along `dir` (Sec. 2.3, the four steps): out = pass(in).
 sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const void* g, int H, int W, int C,
                       float lambda, const sgwls_params* p, int dir, void* ws, cudaStream_t st, bool zero_counters) {
@@ -506,6 +569,7 @@ sgwls_status run_pass(const void* in, int in_dt, void* out, int out_dt, const vo
     a.xent = a.refine ? reinterpret_cast<float*>(wsb + lo.xent_off) : nullptr;
     a.xmode = 0;
     a.nslot = pl.nslot;
+    a.tma = (!pl.queue && setup_tma(a, pl, p->r, CC)) ? 1 : 0;
     cudaError_t e = launch_pass_any(p->r, CC, a, pl, st);
     if (e != cudaSuccess) return cuda_fail(e);
     __atomic_add_fetch(&g_launches, (unsigned long long)(a.refine ? 5 : (pl.queue || pl.P < 2) ? 1 : 2),

@@ -93,7 +93,7 @@ __device__ __forceinline__ void build_args(const BatchArgs& ba, int i, PassArgs&
 
 template <int R, int CC, int SM>
 __global__ void __launch_bounds__(256) k_summary_b(const __grid_constant__ BatchArgs ba) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(128) float smem[];
   __shared__ PassArgs sa;
   const int i = find_image(ba, 0, blockIdx.x);
   const int local = blockIdx.x - ba.img[i].b0[0];
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_summary_b(const __grid_constant__ Batch
 // v from the v-bar planes `in2`, gradients to the image's own buffers).
 template <int R, int CC, bool BWD = false>
 __global__ void __launch_bounds__(256) k_recover_b(const __grid_constant__ BatchArgs ba) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(128) float smem[];
   __shared__ PassArgs sa;
   const int i = find_image(ba, 2, blockIdx.x);
   const int local = blockIdx.x - ba.img[i].b0[2];
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_recover_b(const __grid_constant__ Batch
 
 template <int R, int CC>
 __global__ void __launch_bounds__(256) k_backsub_b(const __grid_constant__ BatchArgs ba) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(128) float smem[];
   __shared__ PassArgs sa;
   const int i = find_image(ba, 2, blockIdx.x);
   const int local = blockIdx.x - ba.img[i].b0[2];

@@ -11,6 +11,7 @@
 //   k + r - j   (line odd: reversed), with j = p % n and n = 2r + 1.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the tensor-copy descriptors of the tile staging)
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -80,6 +81,13 @@ struct PassArgs {
   int* rdcnt;
   int* qctl;
   unsigned* err;
+  // Tensor-copy (TMA) staging of the column direction's tiles (FP32, step
+  // 1, one guidance plane, 16-byte-aligned rows): tm_in maps the CC
+  // estimate planes as a 3D tensor (W, H, CC), tm_g the guidance as 2D
+  // (W, H); both boxes are pitch x (G h + 2) floats.  0: the other staging.
+  int tma;
+  CUtensorMap tm_in;
+  CUtensorMap tm_g;
   // Refinement of each subsystem solve (refine = 1): first solve with
   // xmode 1 (every entry's solution to xent, no averaging); k_resid forms
   // rho = f - A u in FP32 (A's identity kept apart) into rhs; second solve with rhs as the
@@ -188,6 +196,65 @@ __device__ __forceinline__ bool wait_geq(const int* p, int v, unsigned* err, uns
         atomicOr(err, code);
         return false;
       }
+    }
+  }
+}
+
+// ---- tensor copies (TMA) completed on a shared-memory mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  // make the initialised barrier visible to the tensor-copy (async) proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 2D / 3D box of a tensor map into shared memory (coordinates in elements,
+// innermost first), completing `bar` with the box's bytes.
+__device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(smem_u32(bar))
+      : "memory");
+}
+// Waits (every thread) for phase `parity` of `bar`: at least 2^20 polls and
+// 2 s, then the error flag is set and the wait continues for as long again
+// (the copies in flight target this block's shared memory) before it gives
+// up; returns false if it timed out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = global_ns();
+  bool flagged = false;
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return !flagged;
+    if ((it & 63) == 0 && it >= (1u << 20) && global_ns() - t0 > 2000000000ull) {
+      if (flagged) return false;
+      if (err) atomicOr(err, 4u);
+      flagged = true;
+      it = 0;
+      t0 = global_ns();
     }
   }
 }

@@ -26,7 +26,7 @@ constexpr int kLookahead = 2;
 // planes.
 inline size_t tile_floats(int r, int CC, int h, int G, int step = 1, int gc = 1) {
   const int ncol = tile_ncol(r, step);
-  return (size_t)(CC + gc) * (G * h + 2) * std::max(tile_pitch_n(ncol, 0), tile_pitch_n(ncol, 1));
+  return (size_t)(CC + gc) * tile_pstride(G * h + 2, std::max(tile_pitch_n(ncol, 0), tile_pitch_n(ncol, 1)));
 }
 inline size_t smem_summary(int r, int CC, int h, int G, int step = 1, int gc = 1) {
   return 4 * (tile_floats(r, CC, h, G, step, gc) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
@@ -131,6 +131,7 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
       if (pl.queue) {
         // one persistent kernel: summary and back-substitution items
         if (!b.fac || a.step != 1 || a.gc > 1 || b.rhs || b.xmode != 0 || !b.qctl) return cudaErrorInvalidValue;
+        b.tma = 0;   // its blocks stage many tiles; the tensor-copy path is single-use
         const size_t qsmem = std::max(smem, smem_backsub(R, CC, a.h, pl.G, 1));
         if ((e = set_smem(k_pass_q<R, CC>, qsmem)) != cudaSuccess) return e;
         int res = 0;

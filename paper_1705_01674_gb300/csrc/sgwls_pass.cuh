@@ -89,18 +89,24 @@ struct MFields {
 
 // ---------------------------------------------------------------------------
 // Shared-memory strip tile: planes 0..CC-1 = estimate channels, then the
-// guidance plane(s); tile[(plane * ntl + tl) * pitch + col] holds (line tl0 + tl,
-// across-offset off0 + col), zero outside the image.  pitch is odd so the
-// transposed staging of the row direction is free of bank conflicts.
+// guidance plane(s); tile[plane * pstride + tl * pitch + col] holds (line
+// tl0 + tl, across-offset off0 + col), zero outside the image.  pitch is odd
+// so the transposed staging of the row direction is free of bank conflicts;
+// pstride (>= ntl * pitch) is a multiple of 32 floats, so every plane starts
+// on a 128-byte boundary (the destination alignment of a tensor copy).
 struct Tile {
   float* p;
   int tl0, ntl, off0, pitch;
-  int cs;     // physical column of across-offset off0 (vector-aligned staging)
-  int ncol;   // staged columns (runtime-width staging of the sliding-step path)
+  int pstride;   // floats between planes
+  int cs;        // physical column of across-offset off0 (vector-aligned staging)
+  int ncol;      // staged columns (runtime-width staging of the sliding-step path)
   __device__ __forceinline__ const float* row(int plane, int line) const {
-    return p + (plane * ntl + (line - tl0)) * pitch + cs;
+    return p + plane * pstride + (line - tl0) * pitch + cs;
   }
 };
+
+// Floats between tile planes for ntl lines of `pitch` floats.
+__host__ __device__ constexpr int tile_pstride(int ntl, int pitch) { return (ntl * pitch + 31) / 32 * 32; }
 
 // Tile columns of a band of 32 subsystems: their strips of 2r+1 offsets,
 // centres step apart (the appended last centre lies inside that span).
@@ -156,7 +162,7 @@ __device__ __noinline__ void stage_tile_mixed(const PassArgs& a, const Tile& t, 
       v = pl < CC ? ld_px(plane_base<CC>(a, pl, a.in_dt == DT_F32 ? 4 : 2), pix, a.in_dt)
                   : ld_px(plane_base<CC>(a, pl, a.g_dt == DT_F32 ? 4 : 2), pix, a.g_dt);
     }
-    t.p[(pl * t.ntl + tl) * t.pitch + col] = v;
+    t.p[pl * t.pstride + tl * t.pitch + col] = v;
   }
 }
 
@@ -179,7 +185,7 @@ __device__ __noinline__ void stage_tile_t(const PassArgs& a, const Tile& t, int 
 #pragma unroll 1
   for (int pl = p0; pl < p1; ++pl) {
     const char* base = plane_base<CC>(a, pl, F32 ? 4 : 2);
-    float* dplane = t.p + pl * t.ntl * t.pitch;
+    float* dplane = t.p + pl * t.pstride;
     if (a.dir == 0) {
       // rows = lines; 2 columns per lane cover ncol <= 64
       for (int tl0 = warp; tl0 < t.ntl; tl0 += U * nw) {
@@ -251,7 +257,7 @@ __device__ __noinline__ void stage_tile_async(const PassArgs& a, const Tile& t, 
 #pragma unroll 1
   for (int pl = p0; pl < p1; ++pl) {
     const float* base = reinterpret_cast<const float*>(plane_base<CC>(a, pl, 4));
-    float* dplane = t.p + pl * t.ntl * t.pitch;
+    float* dplane = t.p + pl * t.pstride;
     if (a.dir == 0) {
       // flat over (line, offset); NCOL is a compile-time constant
       const int nel = t.ntl * NCOL;
@@ -435,7 +441,7 @@ __device__ __forceinline__ void stage_tile_vec(const PassArgs& a, const Tile& t,
   for (int pl = p0; pl < p1; ++pl) {
     const int dt = pl < CC ? a.in_dt : a.g_dt;
     const void* base = plane_base<CC>(a, pl, dt == DT_F32 ? 4 : 2);
-    float* dplane = t.p + pl * t.ntl * t.pitch;
+    float* dplane = t.p + pl * t.pstride;
     if (dt == DT_F32)
       stage_plane_vec<true, NCOL>(a, t, base, dplane);
     else
@@ -479,7 +485,7 @@ __device__ __noinline__ void stage_tile_rt(const PassArgs& a, const Tile& t, int
   for (int pl = p0; pl < p1; ++pl) {
     const int dt = pl < CC ? a.in_dt : a.g_dt;
     const void* base = plane_base<CC>(a, pl, dt == DT_F32 ? 4 : 2);
-    float* dplane = t.p + pl * t.ntl * t.pitch;
+    float* dplane = t.p + pl * t.pstride;
     if (a.dir == 0) {
       for (int tl = threadIdx.y; tl < t.ntl; tl += blockDim.y) {
         const int line = t.tl0 + tl;
@@ -737,7 +743,7 @@ __device__ __forceinline__ void prologue_weights(const PassArgs& a, const Tile& 
     float wf[R];
 #pragma unroll LineUnroll<R>::value
     for (int j = 0; j < n; ++j) {
-      forward_weights<R, ODD, GCM>(a, gr, gnr, j, true, wf, t.ntl * t.pitch);
+      forward_weights<R, ODD, GCM>(a, gr, gnr, j, true, wf, t.pstride);
       push_weights<R>(wh, wf);
     }
   };
@@ -864,7 +870,7 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
   constexpr bool LW = LineUnroll<R>::value > 1;   // a line's weights computed together
   using F = Fields<R, CC>;
   const Chunk q = make_chunk<R>(a, c);
-  const int pstride = t.ntl * t.pitch;
+  const int pstride = t.pstride;
   float* const fac = KEEP ? fac_lane<R, CC>(a, sys) : nullptr;
   // RHSB: the right-hand side of every entry comes from a.rhs (the
   // refinement's residual) instead of the estimate planes of the tile
@@ -1023,16 +1029,43 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
   }
 }
 
+// Tensor-copy staging of a fixed-width column-direction tile (a.tma): thread
+// (0, 0) issues one box per plane [p0, p1) into the tile -- the estimate
+// planes through the 3D map tm_in, the guidance through tm_g -- starting at
+// the 16-byte boundary x = off0 - cs and line tl0 (negative or past the image:
+// zeros).  The boxes complete `bar`, whose expected bytes the caller set.
+template <int CC>
+__device__ __forceinline__ void tma_stage(const PassArgs& a, const Tile& t, int p0, int p1, unsigned long long* bar) {
+  if (threadIdx.x != 0 || threadIdx.y != 0) return;
+  const int x = t.off0 - t.cs, y = t.tl0;
+  for (int pl = p0; pl < p1; ++pl) {
+    float* dst = t.p + pl * t.pstride;
+    if (pl < CC)
+      tma_load_3d(dst, &a.tm_in, x, y, pl, bar);
+    else
+      tma_load_2d(dst, &a.tm_g, x, y, bar);
+  }
+}
+
+// Bytes of the CC + 1 boxes of a tensor-copy tile.
+__device__ __forceinline__ unsigned tma_tile_bytes(const Tile& t, int planes) {
+  return (unsigned)(planes * t.ntl * t.pitch * sizeof(float));
+}
+
 // Tile geometry of a block of G chunks starting at chunk c0.
 // ncol columns from off0; fixed: the 32 + 2r columns of step 1 (staged with
 // 4-element transfers when aligned), otherwise the runtime-width staging.
 __device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int off0, int ncol, bool fixed, float* p,
                                            Tile& t) {
   t.tl0 = c0 * a.h - 1;
-  t.ntl = min((c0 + G) * a.h, a.L) + 1 - t.tl0;
+  // with tensor-copy staging every block's tile has the box's G h + 2 lines
+  // (lines past the image are filled with zeros by the copy)
+  const bool tma = a.tma && a.dir == 0;
+  t.ntl = tma ? G * a.h + 2 : min((c0 + G) * a.h, a.L) + 1 - t.tl0;
   t.off0 = off0;
-  t.cs = (fixed && a.dir == 0 && vec_staging(a)) ? (off0 & 3) : 0;
+  t.cs = (a.dir == 0 && (tma || (fixed && vec_staging(a)))) ? (off0 & 3) : 0;
   t.pitch = tile_pitch_n(ncol, a.dir);
+  t.pstride = tile_pstride(t.ntl, t.pitch);
   t.ncol = ncol;
   t.p = p;
 }
@@ -1455,15 +1488,27 @@ __device__ __forceinline__ bool body_summary(const PassArgs& a, int bx, int by, 
   group_tile(a, c0, G, off0, unit ? 32 + 2 * R : tile_ncol(R, a.step), unit, smem, t);
   // SM 3: a guidance of a.gc planes (tile planes CC .. CC + gc - 1)
   const int np = CC + (SM == 3 ? a.gc : 1);
-  float* csum = smem + np * t.ntl * t.pitch;   // [G][F::N][32]
+  float* csum = smem + np * t.pstride;   // [G][F::N][32]
   // The guidance is an input of the whole filter (no kernel of the filter
   // writes it): its planes are staged before the wait, overlapping the
   // preceding kernel's tail; the estimate planes after it.
-  if (unit) stage_tile<CC, 32 + 2 * R>(a, t, CC, np); else stage_tile_rt<CC>(a, t, CC, np);
-  griddep_wait();
-  griddep_launch();
-  if (unit) stage_tile<CC, 32 + 2 * R>(a, t, 0, CC); else stage_tile_rt<CC>(a, t, 0, CC);
-  cp_async_wait_all();
+  if (a.tma) {   // (a sliding step's wider tile too: its box starts at 32 bx step, 16-byte aligned)
+    __shared__ unsigned long long s_bar;
+    if (threadIdx.x == 0 && threadIdx.y == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) mbar_expect_tx(&s_bar, tma_tile_bytes(t, np));
+    tma_stage<CC>(a, t, CC, np, &s_bar);
+    griddep_wait();
+    griddep_launch();
+    tma_stage<CC>(a, t, 0, CC, &s_bar);
+    mbar_wait_bounded(&s_bar, 0, a.err);
+  } else {
+    if (unit) stage_tile<CC, 32 + 2 * R>(a, t, CC, np); else stage_tile_rt<CC>(a, t, CC, np);
+    griddep_wait();
+    griddep_launch();
+    if (unit) stage_tile<CC, 32 + 2 * R>(a, t, 0, CC); else stage_tile_rt<CC>(a, t, 0, CC);
+    cp_async_wait_all();
+  }
   __syncthreads();
 
   const bool active = sys < a.nsys;
@@ -1492,7 +1537,7 @@ __device__ __forceinline__ bool body_summary(const PassArgs& a, int bx, int by, 
 
 template <int R, int CC, int SM>
 __global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(128) float smem[];
   body_summary<R, CC, SM>(a, blockIdx.x, blockIdx.y, smem);
 }
 
@@ -1658,16 +1703,28 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
 
   Tile t;
   group_tile(a, c0, G, bx * OB - 2 * R, 32 + 2 * R, true, smem, t);
-  float* ports = smem + (CC + 1) * t.ntl * t.pitch;   // [G][2][XS][32]
+  float* ports = smem + (CC + 1) * t.pstride;   // [G][2][XS][32]
   float* mbuf = ports + G * 2 * XS * 32;               // [G-1][MF::N][32] merge factors + [2][XS][32]
   float* store = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [G][mcap][NF][32]
   // The input tile comes from the pass before the preceding k_summary, which
   // completed before that k_summary passed its own wait; with a single chunk
   // (no k_summary) the preceding kernel produced the input, so wait first.
-  if (!a.early_stage) griddep_wait();
-  stage_tile<CC, 32 + 2 * R>(a, t);
-  if (a.early_stage) griddep_wait();
-  griddep_launch();
+  if (!BWD && a.tma) {
+    __shared__ unsigned long long s_bar;
+    if (threadIdx.x == 0 && threadIdx.y == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
+    if (!a.early_stage) griddep_wait();
+    if (threadIdx.x == 0 && threadIdx.y == 0) mbar_expect_tx(&s_bar, tma_tile_bytes(t, CC + 1));
+    tma_stage<CC>(a, t, 0, CC + 1, &s_bar);
+    if (a.early_stage) griddep_wait();
+    griddep_launch();
+    mbar_wait_bounded(&s_bar, 0, a.err);
+  } else {
+    if (!a.early_stage) griddep_wait();
+    stage_tile<CC, 32 + 2 * R>(a, t);
+    if (a.early_stage) griddep_wait();
+    griddep_launch();
+  }
   group_ports<R, CC>(a, grp, c0, nch, sys, lane, ports, mbuf);
   // Row direction: the block's output lines are staged as [CC][OB][lines]
   // (odd pitch) and written out along the lines at the end.
@@ -1698,7 +1755,7 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
   float* const st = store + threadIdx.y * mcap * NF * 32 + lane;
 
   // ---- forward sweep over the interior: L row and z = y / D per entry
-  const int pstride = t.ntl * t.pitch;
+  const int pstride = t.pstride;
   {
     float wh[R][R] = {};
     float Lw[R][R] = {};
@@ -1932,7 +1989,7 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
 
 template <int R, int CC, bool BWD>
 __global__ void __launch_bounds__(256) k_recover(const __grid_constant__ PassArgs a) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(128) float smem[];
   body_recover<R, CC, BWD>(a, blockIdx.x, blockIdx.y, smem);
 }
 
@@ -2178,7 +2235,7 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
 
 template <int R, int CC, int MODE>
 __global__ void __launch_bounds__(256) k_backsub(const __grid_constant__ PassArgs a) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(128) float smem[];
   body_backsub<R, CC, MODE>(a, blockIdx.x, blockIdx.y, smem);
 }
 
@@ -2206,7 +2263,7 @@ __device__ __forceinline__ bool flag_set(const unsigned* err) {
 
 template <int R, int CC>
 __global__ void __launch_bounds__(256) k_pass_q(const __grid_constant__ PassArgs a) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(128) float smem[];
   __shared__ int s_item, s_ok;
   QueueSched q;
   q.nb = (a.nsys + 31) >> 5;
