@@ -89,15 +89,16 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *   chunk_lines 0: automatic; otherwise the number of lines per chunk of
  *               the parallel subsystem solve (a tuning knob; the result is
  *               the same up to FP32 rounding for every value)
- *   factor_cache  where the second kernel of a forward pass gets the chunk
- *               factors (LDL^T rows and forward-substituted right-hand
- *               sides) from: 0 automatic (kept in the workspace when one
- *               pass's factors take at most 4 GiB, otherwise recomputed),
- *               1 always kept, 2 always recomputed.  Keeping costs
- *               4 (2r+1)(2r+C') bytes per pixel of workspace (C' = channels
- *               per group, at most 4) and saves the second kernel's
- *               weights and factorisation.  A tuning knob: the results
- *               agree up to FP32 rounding.
+ *   factor_cache  where the second kernel of a forward or adjoint pass
+ *               gets the chunk factors (LDL^T rows and forward-substituted
+ *               right-hand sides) from: 0 automatic (kept in the workspace
+ *               when one pass's factors take at most 4 GiB, otherwise
+ *               recomputed), 1 always kept, 2 always recomputed.  Keeping
+ *               costs 4 (2r+1)(2r+C') bytes per pixel of workspace (C' =
+ *               right-hand sides per group: at most 4 forward; u and v of
+ *               up to 3 channels at r = 1, 2 otherwise, in the backward)
+ *               and saves the second kernel's weights and factorisation.  A
+ *               tuning knob: the results agree up to FP32 rounding.
  *   guide_channels  Cg, the number of guidance planes: 0 or 1 (g is H x W)
  *               or 2 .. SGWLS_GUIDE_MAX (g is Cg x H x W, planar, type
  *               p->storage); |Gi-Gj| in Eq. 2 is then the Euclidean norm of

@@ -47,7 +47,7 @@ CANDIDATES = {
 KIND_KNOBS = {
     "filter": KNOBS,
     "batched": ("chunk_lines", "factor_cache"),
-    "backward": ("chunk_lines", "group_warps"),
+    "backward": ("chunk_lines", "group_warps", "factor_cache"),
 }
 MIN_GAIN = 0.02
 AGREE = 1e-4

@@ -130,7 +130,7 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
                int gc = 1, int gmax = kGMax) {
   const int bands = step == 1 ? (D + (32 - 2 * r) - 1) / (32 - 2 * r) : (n_centres(D, r, step, nullptr) + 31) / 32;
   auto second = [&](int hh, int G) {
-    return keep ? smem_backsub(r, CC, hh, G, step) : smem_recover(r, CC, hh, G, bwd);
+    return keep ? smem_backsub(r, CC, hh, G, step, bwd) : smem_recover(r, CC, hh, G, bwd);
   };
   auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G, step, gc)); };
   int h;
@@ -990,39 +990,69 @@ sgwls_status run_batched(int B, const sgwls_image* imgs, const sgwls_params* p, 
 namespace {
 
 struct BwdLayout {
-  size_t img0, img1, gbuf, summ, xsep, mdata, cnt, total;
+  size_t img0, img1, gbuf, summ, xsep, mdata, fac, psi, cnt, total;
+  bool keep;   // the adjoint passes keep their chunk factors
 };
 
 // Channels per backward group (u and v of each solved against one factor):
 // three at r = 1 (six right-hand sides), two otherwise.
 int bwd_group(int r) { return r == 1 ? kBwdWideRhs / 2 : 2; }
 
+// Whether the adjoint passes of an H x W x C image keep their chunk factors
+// (k_summary then k_backsub's adjoint mode) instead of recomputing them in
+// k_recover: as in the forward, unless factor_cache = 2 or the factors of
+// a pass exceed the factor budget (factor_cache = 1: always).
+bool bwd_keep(int H, int W, int C, const sgwls_params* p) {
+  if (p->factor_cache == 2) return false;
+  if (p->factor_cache == 1) return true;
+  const int CC = 2 * std::min(bwd_group(p->r), C);
+  for (int dir = 0; dir < 2; ++dir) {
+    const int L = dir == 0 ? H : W;
+    const int D = dir == 0 ? W : H;
+    const int nsys = ((D - 2 * p->r) + 31) / 32 * 32;
+    if (fac_bytes(L, p->r, CC, nsys) > kFactorCacheBytes) return false;
+  }
+  return true;
+}
+
+// Plan of one adjoint pass over CC right-hand sides.
+Plan bwd_plan(int L, int D, int CC, const sgwls_params* p, bool keep) {
+  return make_plan(L, D, p->r, CC, p->chunk_lines, true, keep, 1, 1, p->group_warps > 0 ? p->group_warps : kGMax);
+}
+
 BwdLayout make_bwd_layout(int H, int W, int C, const sgwls_params* p) {
   const int r = p->r;
   const int gch = bwd_group(r);
-  size_t summ = 0, xsep = 0, mdata = 0;
+  const bool keep = bwd_keep(H, W, C, p);
+  size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0;
   for (int dir = 0; dir < 2; ++dir) {
     const int L = dir == 0 ? H : W;
     const int D = dir == 0 ? W : H;
     const int nsys = ((D - 2 * r) + 31) / 32 * 32;   // padded subsystem stride
     for (int c0 = 0; c0 < C; c0 += gch) {
       const int CC = 2 * std::min(gch, C - c0);
-      const Plan pl = make_plan(L, D, r, CC, p->chunk_lines, true, false, 1, 1,
-                                p->group_warps > 0 ? p->group_warps : kGMax);
+      const Plan pl = bwd_plan(L, D, CC, p, keep);
       summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
       xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
       mdata = std::max(mdata, (size_t)pl.NG * std::max(pl.G - 1, 1) * n_mfields(r, CC) * nsys * sizeof(float));
+      if (keep && pl.P > 1) {
+        fac = std::max(fac, fac_bytes(L, r, CC, nsys));
+        psi = std::max(psi, psi_bytes(pl.P, r, nsys));
+      }
     }
   }
   const size_t img = align256((size_t)C * H * W * sizeof(float));
   BwdLayout lo;
+  lo.keep = keep;
   lo.img0 = 0;
   lo.img1 = img;
   lo.gbuf = 2 * img;
   lo.summ = lo.gbuf + align256(((size_t)H * W + 64) * sizeof(float));
   lo.xsep = lo.summ + align256(summ);
   lo.mdata = lo.xsep + align256(xsep);
-  lo.cnt = lo.mdata + align256(mdata);
+  lo.fac = lo.mdata + align256(mdata);
+  lo.psi = lo.fac + align256(fac);
+  lo.cnt = lo.psi + align256(psi);
   lo.total = lo.cnt + counter_bytes(H, W, r);
   return lo;
 }
@@ -1099,11 +1129,12 @@ sgwls_status run_backward(const float* grad_u, const float* g, const float* save
     const int gch = bwd_group(p->r);
     for (int c0 = 0; c0 < C; c0 += gch) {
       const int nch = std::min(gch, C - c0);
-      const Plan pl = make_plan(a.L, a.D, p->r, 2 * nch, p->chunk_lines, true, false, 1, 1,
-                                p->group_warps > 0 ? p->group_warps : kGMax);
+      const Plan pl = bwd_plan(a.L, a.D, 2 * nch, p, lo.keep);
       a.h = pl.h;
       a.P = pl.P;
       a.ngroups = pl.NG;
+      a.fac = lo.keep && pl.P > 1 ? reinterpret_cast<float*>(wsb + lo.fac) : nullptr;
+      a.psi = lo.keep && pl.P > 1 ? reinterpret_cast<float*>(wsb + lo.psi) : nullptr;
       a.in = uin + (size_t)c0 * plane;
       a.in2 = w0 + (size_t)c0 * plane;
       a.n_in1 = nch;
@@ -1154,9 +1185,13 @@ __global__ void k_bwd_scale_b(const __grid_constant__ ScaleTab t) {
 }
 
 // Lines per chunk of a batched adjoint pass (blocks of kGMax chunks).
-int batch_h_bwd(int r, int CC, int chunk_lines) {
-  int h = chunk_lines > 0 ? chunk_lines : 64;
-  while (h > 1 && smem_recover(r, CC, h, kGMax, true) > kSmemBlockTarget) --h;
+int batch_h_bwd(int r, int CC, int chunk_lines, bool keep) {
+  int h = chunk_lines > 0 ? chunk_lines : keep ? keep_lines(r) : 64;
+  auto block = [&](int hh) {
+    return keep ? std::max(smem_summary(r, CC, hh, kGMax), smem_backsub(r, CC, hh, kGMax, 1, true))
+                : smem_recover(r, CC, hh, kGMax, true);
+  };
+  while (h > 1 && block(h) > kSmemBlockTarget) --h;
   return h;
 }
 
@@ -1168,15 +1203,26 @@ struct BwdJob {
 struct BwdBatchLayout {
   std::vector<size_t> w0, w1, gbuf;                 // per image
   std::vector<size_t> summ, xsep, mdata, cnt;       // per job
+  std::vector<size_t> fac, psi;                     // per job (keep)
   std::vector<BwdJob> jobs[kGroupMax];              // by nch - 1 (nch <= 3)
   std::vector<size_t> jobpos[kGroupMax];            // index into summ / xsep / ...
   size_t ncnt = 0, total = 0;
+  bool keep = false;   // the adjoint passes keep their chunk factors
 };
+
+// Keep the adjoint's chunk factors for every image of a batched backward,
+// or for none (each job has its own factor store).
+bool bwd_batch_keep(int B, const sgwls_grad_image* imgs, const sgwls_params* p) {
+  for (int i = 0; i < B; ++i)
+    if (!bwd_keep(imgs[i].H, imgs[i].W, imgs[i].C, p)) return false;
+  return true;
+}
 
 BwdBatchLayout bwd_batch_layout(int B, const sgwls_grad_image* imgs, const sgwls_params* p) {
   BwdBatchLayout lo;
   const int r = p->r;
   const int gch = bwd_group(r);
+  lo.keep = bwd_batch_keep(B, imgs, p);
   std::vector<BwdJob> all;
   for (int i = 0; i < B; ++i)
     for (int c0 = 0; c0 < imgs[i].C; c0 += gch) all.push_back({i, c0, std::min(gch, imgs[i].C - c0)});
@@ -1198,8 +1244,8 @@ BwdBatchLayout bwd_batch_layout(int B, const sgwls_grad_image* imgs, const sgwls
   for (size_t k = 0; k < all.size(); ++k) {
     const BwdJob& j = all[k];
     const int CC = 2 * j.nch;
-    const int h0 = batch_h_bwd(r, CC, p->chunk_lines);
-    size_t summ = 0, xsep = 0, mdata = 0;
+    const int h0 = batch_h_bwd(r, CC, p->chunk_lines, lo.keep);
+    size_t summ = 0, xsep = 0, mdata = 0, fac = 0, psi = 0;
     for (int dir = 0; dir < 2; ++dir) {
       const int L = dir == 0 ? imgs[j.img].H : imgs[j.img].W;
       const int D = dir == 0 ? imgs[j.img].W : imgs[j.img].H;
@@ -1208,11 +1254,18 @@ BwdBatchLayout bwd_batch_layout(int B, const sgwls_grad_image* imgs, const sgwls
       summ = std::max(summ, (size_t)pl.NG * n_fields(r, CC) * nsys * sizeof(float));
       xsep = std::max(xsep, (size_t)std::max(pl.NG - 1, 1) * r * CC * nsys * sizeof(float));
       mdata = std::max(mdata, (size_t)pl.NG * (kGMax - 1) * n_mfields(r, CC) * nsys * sizeof(float));
+      if (lo.keep) {
+        fac = std::max(fac, fac_bytes(L, r, CC, nsys));
+        psi = std::max(psi, psi_bytes(pl.P, r, nsys));
+      }
     }
     lo.summ.push_back(off);
     lo.xsep.push_back(off + align256(summ));
     lo.mdata.push_back(off + align256(summ) + align256(xsep));
     off += align256(summ) + align256(xsep) + align256(mdata);
+    lo.fac.push_back(off);
+    lo.psi.push_back(off + align256(fac));
+    off += align256(fac) + align256(psi);
     lo.jobs[j.nch - 1].push_back(j);
     lo.jobpos[j.nch - 1].push_back(k);
   }
@@ -1295,7 +1348,7 @@ sgwls_status run_backward_batched(int B, const sgwls_grad_image* imgs, const sgw
       const std::vector<BwdJob>& jobs = lo.jobs[gsz - 1];
       const std::vector<size_t>& pos = lo.jobpos[gsz - 1];
       const int CC = 2 * gsz;
-      const int h0 = batch_h_bwd(r, CC, p->chunk_lines);
+      const int h0 = batch_h_bwd(r, CC, p->chunk_lines, lo.keep);
       for (size_t j0 = 0; j0 < jobs.size(); j0 += kBatchMax) {
         const int nb = (int)std::min<size_t>(kBatchMax, jobs.size() - j0);
         BatchArgs* ba = &batch_args;
@@ -1309,6 +1362,7 @@ sgwls_status run_backward_batched(int B, const sgwls_grad_image* imgs, const sgw
         ba->nimg = nb;
         BatchLaunch bl = {};
         bl.G = kGMax;
+        bl.keep = lo.keep;
         size_t red_max = 0;
         int b[3] = {0, 0, 0};
         for (int k = 0; k < nb; ++k) {
@@ -1328,6 +1382,8 @@ sgwls_status run_backward_batched(int B, const sgwls_grad_image* imgs, const sgw
           d.xsep = reinterpret_cast<float*>(wsb + lo.xsep[q]);
           d.mdata = reinterpret_cast<float*>(wsb + lo.mdata[q]);
           d.band_cnt = reinterpret_cast<int*>(wsb + lo.cnt[q]);
+          d.fac = lo.keep ? reinterpret_cast<float*>(wsb + lo.fac[q]) : nullptr;
+          d.psi = lo.keep ? reinterpret_cast<float*>(wsb + lo.psi[q]) : nullptr;
           d.plane = (long long)plane;
           d.H = im.H;
           d.W = im.W;
@@ -1353,7 +1409,7 @@ sgwls_status run_backward_batched(int B, const sgwls_grad_image* imgs, const sgw
           bl.any_red |= pl.NG > 1;
           red_max = std::max(red_max, (size_t)pl.NG * n_fields(r, CC) * 32 * sizeof(float));
           bl.smem[0] = smem_summary(r, CC, h0, kGMax);
-          bl.smem[2] = smem_recover(r, CC, h0, kGMax, true);
+          bl.smem[2] = lo.keep ? smem_backsub(r, CC, h0, kGMax, 1, true) : smem_recover(r, CC, h0, kGMax, true);
         }
         bl.nblk[0] = b[0];
         bl.nblk[1] = b[1];

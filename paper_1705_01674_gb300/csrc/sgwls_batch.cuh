@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(256) k_recover_b(const __grid_constant__ Batch
   body_recover<R, CC, BWD>(sa, local - by * ba.img[i].nbx[2], by, smem);
 }
 
-template <int R, int CC>
+// MODE 0: forward back-substitution; 3: the adjoint's (CC = u and v planes)
+template <int R, int CC, int MODE = 0>
 __global__ void __launch_bounds__(256) k_backsub_b(const __grid_constant__ BatchArgs ba) {
   extern __shared__ __align__(128) float smem[];
   __shared__ PassArgs sa;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) k_backsub_b(const __grid_constant__ Batch
   const int local = blockIdx.x - ba.img[i].b0[2];
   const int by = local / ba.img[i].nbx[2];
   build_args(ba, i, sa);
-  body_backsub<R, CC, 0>(sa, local - by * ba.img[i].nbx[2], by, smem);
+  body_backsub<R, CC, MODE>(sa, local - by * ba.img[i].nbx[2], by, smem);
 }
 
 }  // namespace sgwls

@@ -42,12 +42,15 @@ inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
 }
 
 // k_backsub: group ports and merge factors, plus the row-direction output
-// staging; with a sliding step > 1 also each warp's accumulation rows.
-inline size_t smem_backsub(int r, int CC, int h, int G, int step = 1) {
+// staging; with a sliding step > 1 also each warp's accumulation rows; the
+// adjoint (bwd, CC = u and v planes) writes CC / 2 planes and adds the
+// guidance tile and its dLoss/dG accumulators.
+inline size_t smem_backsub(int r, int CC, int h, int G, int step = 1, bool bwd = false) {
   const size_t merge = (size_t)(G - 1) * (3 * r * r + r * CC) * 32 + 2 * (size_t)r * CC * 32;
-  const size_t otile = (size_t)CC * step_own_max(r, step) * ((G * h) | 1);
+  const size_t otile = (size_t)(bwd ? CC / 2 : CC) * step_own_max(r, step) * ((G * h) | 1);
   const size_t accum = step > 1 ? (size_t)G * (CC + 1) * step_acc_width(r, step) : 0;
-  return 4 * ((size_t)G * 2 * r * CC * 32 + merge + otile + accum);
+  const size_t gtile = bwd ? 2 * (size_t)(G * h + 2) * (32 + 2 * r) : 0;
+  return 4 * ((size_t)G * 2 * r * CC * 32 + merge + otile + accum + gtile);
 }
 
 constexpr size_t kReducedSmemMax = 96 * 1024;
@@ -120,7 +123,9 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
   cudaError_t e;
   PassArgs b = a;
   b.early_stage = a.P > 1 ? 1 : 0;   // k_recover follows k_summary
-  if (BWD || a.P < 2) b.fac = b.psi = nullptr;   // factors are kept only by a forward k_summary
+  // factors are kept by k_summary for k_backsub (one chunk: k_recover alone);
+  // the adjoint keeps them for k_backsub's adjoint mode at step 1 only
+  if (a.P < 2 || (BWD && a.step != 1)) b.fac = b.psi = nullptr;
   // a vector guidance is read by the keeping k_summary<..., 3> alone
   if (a.gc > 1 && (!b.fac || b.rhs)) return cudaErrorInvalidValue;
   if (a.P > 1) {
@@ -157,12 +162,22 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
         ks = k_summary<R, CC, 2>;
       else if (b.fac)
         ks = a.gc > 1 ? k_summary<R, CC, 3> : k_summary<R, CC, 1>;
+    } else {
+      if (b.fac) ks = k_summary<R, CC, 1>;
     }
     if ((e = set_smem(ks, smem)) != cudaSuccess) return e;
     e = launch_pdl(ks, dim3((a.nsys + 31) / 32, pl.NG), dim3(32, pl.G), smem, st, b);
     if (e != cudaSuccess) return e;
   }
-  if constexpr (!BWD) {
+  if constexpr (BWD) {
+    if (b.fac) {   // adjoint back-substitution from the kept factors
+      const size_t smem = smem_backsub(R, CC, a.h, pl.G, 1, true);
+      if ((e = set_smem(k_backsub<R, CC, 3>, smem)) != cudaSuccess) return e;
+      e = launch_pdl(k_backsub<R, CC, 3>, dim3((a.D + OB - 1) / OB, pl.NG), dim3(32, pl.G), smem, st, b);
+      if (e != cudaSuccess) return e;
+      return cudaGetLastError();
+    }
+  } else {
     if (b.fac) {   // the factors were kept by k_summary
       const size_t smem = smem_backsub(R, CC, a.h, pl.G, a.step);
       const int nbx = a.step == 1 ? (a.D + OB - 1) / OB : (a.nsys + step_owned_lanes(R, a.step) - 1) /
@@ -215,9 +230,9 @@ cudaError_t launch_batch_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStre
   return cudaGetLastError();
 }
 
-// Batched adjoint pass: one launch per kernel over all images of `ba` (the
-// summaries recompute their factors; CC = u and v planes of CC / 2
-// channels).
+// Batched adjoint pass: one launch per kernel over all images of `ba` (CC =
+// u and v planes of CC / 2 channels).  The summaries keep their factors for
+// the adjoint back-substitution (bl.keep), or k_recover recomputes them.
 template <int R, int CC>
 cudaError_t launch_batch_bwd_rc(const BatchArgs& ba, const BatchLaunch& bl, cudaStream_t st) {
   cudaError_t e;
@@ -226,9 +241,15 @@ cudaError_t launch_batch_bwd_rc(const BatchArgs& ba, const BatchLaunch& bl, cuda
   b.base.chain_smem = bl.red_smem ? 1 : 0;
   if (bl.any_multi) {
     const size_t smem = bl.red_smem ? std::max(bl.smem[0], bl.smem[1]) : bl.smem[0];
-    if ((e = set_smem(k_summary_b<R, CC, 0>, smem)) != cudaSuccess) return e;
-    if ((e = launch_pdl(k_summary_b<R, CC, 0>, dim3(bl.nblk[0]), dim3(32, bl.G), smem, st, b)) != cudaSuccess)
+    auto ks = bl.keep ? k_summary_b<R, CC, 1> : k_summary_b<R, CC, 0>;
+    if ((e = set_smem(ks, smem)) != cudaSuccess) return e;
+    if ((e = launch_pdl(ks, dim3(bl.nblk[0]), dim3(32, bl.G), smem, st, b)) != cudaSuccess) return e;
+  }
+  if (bl.keep && bl.any_multi) {
+    if ((e = set_smem(k_backsub_b<R, CC, 3>, bl.smem[2])) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_backsub_b<R, CC, 3>, dim3(bl.nblk[2]), dim3(32, bl.G), bl.smem[2], st, b)) != cudaSuccess)
       return e;
+    return cudaGetLastError();
   }
   if ((e = set_smem(k_recover_b<R, CC, true>, bl.smem[2])) != cudaSuccess) return e;
   if ((e = launch_pdl(k_recover_b<R, CC, true>, dim3(bl.nblk[2]), dim3(32, bl.G), bl.smem[2], st, b)) != cudaSuccess)

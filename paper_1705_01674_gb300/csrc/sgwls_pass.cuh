@@ -2026,11 +2026,35 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
   const bool valid = sys_raw >= 0 && sys_raw < a.nsys;
   const int sys = min(max(sys_raw, 0), a.nsys - 1);
   const int OWN = unit ? OB : step_own_max(R, a.step);   // otile rows per channel
+  // MODE 3: the adjoint pass from kept factors (planes 0 .. CC/2-1 hold u,
+  // CC/2 .. CC-1 v): its output is the sum of the v values a pixel
+  // received, plus the pair terms of dLoss/dG and dLoss/dlambda
+  constexpr bool BWD = MODE == 3;
+  constexpr int NOUT = BWD ? CC / 2 : CC;   // output planes
+  constexpr int NCOL = 32 + 2 * R;           // BWD: columns of the guidance tile
 
   float* ports = smem;                                  // [G][2][XS][32]
   float* mbuf = ports + G * 2 * XS * 32;                // [G-1][MF::N][32] + [2][XS][32]
-  float* otile = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [CC][OWN][opitch]
+  float* otile = mbuf + (G - 1) * MF::N * 32 + 2 * XS * 32;   // [NOUT][OWN][opitch]
   const int opitch = (G * a.h) | 1;
+  // BWD: the guidance tile of the group's lines (one line of halo above)
+  // and the block's dLoss/dG accumulators, both [ntl][NCOL], columns from
+  // the first lane's strip (across-offset bx OB - 2r)
+  const int gtl0 = c0 * a.h - 1;
+  const int gntl = min((c0 + G) * a.h, a.L) + 1 - gtl0;
+  float* const gtile = otile + NOUT * OWN * opitch;
+  float* const gacc = gtile + gntl * NCOL;
+  float lam_acc = 0.f;
+  if constexpr (BWD) {
+    // the guidance is an input of the whole filter: staged before the wait
+    const int off0 = bx * OB - 2 * R;
+    for (int i = threadIdx.y * 32 + lane; i < gntl * NCOL; i += G * 32) {
+      const int tl = i / NCOL, col = i - tl * NCOL;
+      const int line = gtl0 + tl, off = off0 + col;
+      gtile[i] = (line >= 0 && line < a.L && off >= 0 && off < a.D) ? ld_px(a.g, pix_index(a, line, off), a.g_dt) : 0.f;
+      gacc[i] = 0.f;
+    }
+  }
   // step > 1: per warp, CC accumulation rows and one of reciprocal counts
   const int AW = step_acc_width(R, a.step);
   float* const accw = otile + CC * OWN * opitch + threadIdx.y * (CC + 1) * AW;
@@ -2086,6 +2110,43 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
     const float* const psi = psi_lane<R>(a, sys);
     float Lb[R][R] = {};   // Lb[u-1][t-1] = L[p+u, p+u-t]
     float xw[R][CC] = {};  // x of entries p+1 .. p+R (interior only)
+    // BWD: x of entries p+1 .. p+R of the chunk (its bottom separator too);
+    // a subsystem's pair terms are added by the one block that owns it
+    float xpw[R][CC] = {};
+    (void)xpw;
+    const bool bowner = BWD && valid && lane >= R && lane < 32 - R;
+    // BWD pair term of entries p (line lp, entry jp) and q = p + tq (the
+    // derivative of Eq. 2's weight through Eq. 4): dLoss/dlambda and
+    // dLoss/dG contributions, from the u and v values of both entries
+    auto pair_terms = [&](auto oddp, int lp, int jp, const float (&xp)[CC], int tq, const float (&xq)[CC]) {
+      constexpr bool ODDP = decltype(oddp)::value;
+      const int jq = jp + tq;
+      const int lq = jq < n ? lp : lp + 1;
+      const int colp = lane + ecol<R, ODDP>(jp);
+      const int colq = lane + (jq < n ? ecol<R, ODDP>(jq) : ecol<R, !ODDP>(jq - n));
+      const float gp = gtile[(lp - gtl0) * NCOL + colp];
+      const float gq = gtile[(lq - gtl0) * NCOL + colq];
+      float sdot = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < NOUT; ++ch) sdot += (xp[NOUT + ch] - xq[NOUT + ch]) * (xp[ch] - xq[ch]);
+      const float dg = gp - gq;
+      const float sp = a.sp0[jp * R + tq - 1];
+      float w, dw;
+      if (a.weight == 0) {
+        w = sp * fast_ex2(dg * dg * a.range_k);
+        dw = -w * dg * a.dgk;
+      } else {
+        const float ad = fabsf(dg);
+        const float hh = 1.0f / (powf(ad, a.range_k) + a.eps);
+        w = sp * hh;
+        dw = ad > 0.f ? -sp * hh * hh * a.range_k * powf(ad, a.range_k - 1.0f) * (dg > 0.f ? 1.f : -1.f) : 0.f;
+      }
+      lam_acc -= w * sdot;
+      const float gb = -a.lam * sdot * dw;
+      atomicAdd_block(&gacc[(lp - gtl0) * NCOL + colp], gb);
+      atomicAdd_block(&gacc[(lq - gtl0) * NCOL + colq], -gb);
+    };
+    (void)pair_terms;
     const long long ostride = a.dir == 0 ? 1 : a.W;
     const long long lstride = a.dir == 0 ? a.W : 1;
     float* const outp = reinterpret_cast<float*>(a.out);
@@ -2139,6 +2200,14 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
 #pragma unroll
           for (int tt = 0; tt < R; ++tt) Lb[0][tt] = Lrow[tt];
           push_vec<R, CC>(xw, x);
+        }
+        if constexpr (BWD) {
+          if (bowner) {
+#pragma unroll
+            for (int tq = 1; tq <= R; ++tq)
+              if (!LAST || j + tq < n) pair_terms(odd, line, j, x, tq, xpw[tq - 1]);
+          }
+          push_vec<R, CC>(xpw, x);
         }
         // (registers for r <= 3; the rolled loop of larger r indexes xl
         // dynamically, which places it in local memory)
@@ -2202,11 +2271,15 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
         return;
       }
       const long long pix = (long long)line * lstride + (long long)o * ostride;
+      // (BWD: the sum of the v planes, no division: the caller divided
+      // dLoss/d(pass output) by the counts before the pass)
+      constexpr int CH0 = BWD ? NOUT : 0;
+      const float scale = BWD ? 1.f : inv_cnt;
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) {
+      for (int ch = 0; ch < NOUT; ++ch) {
         float voff[n];
 #pragma unroll
-        for (int e2 = 0; e2 < n; ++e2) voff[e2] = valid ? xl[ecol<R, ODD>(e2)][ch] : 0.f;
+        for (int e2 = 0; e2 < n; ++e2) voff[e2] = valid ? xl[ecol<R, ODD>(e2)][CH0 + ch] : 0.f;
         float sum = voff[R];
 #pragma unroll
         for (int d = 1; d <= R; ++d) {
@@ -2215,21 +2288,55 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
         }
         if (writer) {
           if (a.dir != 0)
-            otile[(ch * OB + (lane - R)) * opitch + (line - oline0)] = sum * inv_cnt;
+            otile[(ch * OB + (lane - R)) * opitch + (line - oline0)] = sum * scale;
           else if (a.out_dt == DT_F32)
-            outp[pix + ch * a.plane] = sum * inv_cnt;
+            outp[pix + ch * a.plane] = sum * scale;
           else
-            st_px(a.out, pix + ch * a.plane, a.out_dt, sum * inv_cnt);
+            st_px(a.out, pix + ch * a.plane, a.out_dt, sum * scale);
         }
       }
     });
+    if constexpr (BWD) {
+      // pairs from the separator above into this chunk's first entries
+      if (q.top && bowner) {
+        const int lp = q.line0 - 1;
+        auto virt = [&](auto oddp) {
+#pragma unroll
+          for (int d = 1; d <= R; ++d) {
+            float xv[CC];
+#pragma unroll
+            for (int ch = 0; ch < CC; ++ch) xv[ch] = xT[R - d][ch];
+#pragma unroll
+            for (int tq = 1; tq <= R; ++tq)
+              if (tq >= d) pair_terms(oddp, lp, n - d, xv, tq, xpw[tq - 1]);
+            push_vec<R, CC>(xpw, xv);
+          }
+        };
+        if (lp & 1) virt(std::true_type{}); else virt(std::false_type{});
+      }
+    }
   }
   if (a.dir != 0 && !(MODE == 2 && a.xmode == 1)) {
     __syncthreads();
     if constexpr (unit)
-      flush_otile<CC, OB>(a, bx, c0, otile, opitch);
+      flush_otile<NOUT, OB>(a, bx, c0, otile, opitch);
     else
       flush_otile_n<CC>(a, c0, otile, opitch, OWN, wlo, whi - wlo);
+  }
+  if constexpr (BWD) {
+    // dLoss/dlambda: warp sum, one atomic per warp; dLoss/dG of the block
+    __syncthreads();
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) lam_acc += __shfl_down_sync(0xffffffffu, lam_acc, d);
+    if (lane == 0 && lam_acc != 0.f) atomicAdd(a.grad_lam, lam_acc);
+    const int off0 = bx * OB - 2 * R;
+    for (int i = threadIdx.y * 32 + lane; i < gntl * NCOL; i += G * 32) {
+      const float v = gacc[i];
+      if (v == 0.f) continue;
+      const int tl = i / NCOL, col = i - tl * NCOL;
+      const int line = gtl0 + tl, off = off0 + col;
+      if (line >= 0 && line < a.L && off >= 0 && off < a.D) atomicAdd(a.grad_g + pix_index(a, line, off), v);
+    }
   }
 }
 

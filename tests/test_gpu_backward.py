@@ -55,14 +55,17 @@ def _rel(a, b):
 @pytest.mark.parametrize("C", [1, 3])
 @pytest.mark.parametrize("axis_order", [0, 1])
 @pytest.mark.parametrize("chunk_lines", [0, 1, 3])
-def test_backward_matches_oracle_adjoint(api, r, C, axis_order, chunk_lines):
+@pytest.mark.parametrize("factor_cache", [0, 2])
+def test_backward_matches_oracle_adjoint(api, r, C, axis_order, chunk_lines, factor_cache):
+    """factor_cache 0: the adjoint passes keep their chunk factors (k_summary,
+    then k_backsub's adjoint mode); 2: k_recover recomputes them."""
     rng = np.random.default_rng(100 * r + 10 * C + axis_order)
     F3 = synth.rgb_scene(37, 45, seed=50 + r, n_rect=10, n_disk=2)
     F = F3[:C].astype(np.float32)
     G = synth.luminance(F3)
     Ubar = rng.normal(size=F.shape).astype(np.float32)
     kw = dict(r=r, iters=2, axis_order=axis_order, sigma_r=0.2)
-    gf, gg, gl = _gpu_grads(api, F, G, 1.5, Ubar, chunk_lines=chunk_lines, **kw)
+    gf, gg, gl = _gpu_grads(api, F, G, 1.5, Ubar, chunk_lines=chunk_lines, factor_cache=factor_cache, **kw)
     rf, rg, rl = sgwls_vjp(F.astype(np.float64), G.astype(np.float64), 1.5, _prm(**kw), Ubar.astype(np.float64))
     assert _rel(gf, rf) <= REL, ("f", _rel(gf, rf))
     assert _rel(gg, rg) <= REL, ("g", _rel(gg, rg))
@@ -198,3 +201,31 @@ def test_batched_backward_matches_oracle_and_single_calls(api, r):
         gf1, gg1, gl1 = api.sgwls_filter_backward(gus[b], gs[b], saveds[b], lams[b], **kw)
         torch.cuda.synchronize()
         assert _rel(gfs[b].cpu().numpy(), gf1.cpu().numpy()) <= 1e-5, b
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+@pytest.mark.parametrize("C", [1, 2, 3])
+def test_backward_kept_factors_many_bands_and_groups(api, r, C):
+    """Kept-factor adjoint over several bands, several chunk groups (3-line
+    chunks: up to 56 chunks, 7 groups of 8) and ragged tails in both
+    directions: against the recomputing adjoint and the oracle's adjoint
+    (1e-3 relative)."""
+    rng = np.random.default_rng(400 + 10 * r + C)
+    F3 = synth.rgb_scene(167, 109, seed=410 + r, n_rect=25, n_disk=5)
+    F = np.concatenate([F3, F3[::-1]])[:C].astype(np.float32)
+    G = synth.luminance(F3)
+    Ubar = rng.normal(size=F.shape).astype(np.float32)
+    kw = dict(r=r, iters=1, sigma_r=0.15, chunk_lines=3)
+    gk = _gpu_grads(api, F, G, 1.3, Ubar, factor_cache=1, **kw)
+    gr = _gpu_grads(api, F, G, 1.3, Ubar, factor_cache=2, **kw)
+    # dLoss/df has no atomics: the two differ by the factors' FP32 rounding;
+    # dLoss/dG and dLoss/dlambda are atomic sums of signed pair terms whose
+    # cancellation amplifies the order-dependent rounding
+    assert _rel(gk[0], gr[0]) <= 1e-5
+    assert _rel(gk[1], gr[1]) <= 1e-4
+    assert abs(gk[2] - gr[2]) <= 1e-4 * abs(gr[2])
+    rf, rg, rl = sgwls_vjp(F.astype(np.float64), G.astype(np.float64), 1.3, _prm(**kw), Ubar.astype(np.float64))
+    assert _rel(gk[0], rf) <= REL
+    assert _rel(gk[1], rg) <= REL
+    assert abs(gk[2] - rl) <= REL * abs(rl)
+    assert api.device_flag() == 0
