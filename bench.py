@@ -927,7 +927,9 @@ def run_case(args):
     """A few calls (args.warmup + args.steps) of one kernel family on a
     moderately sized input, for a profiler's launch list or capture: no
     timing, no JSON line.  The image is 960 x 540 RGB (luminance guidance),
-    the headline's scene at a quarter of its pixels."""
+    the headline's scene at a quarter of its pixels, except for the
+    headline_r<r> cases (the 1920 x 1080 headline image, T = 2, at radius r)
+    and rgb1024x768_r1 (the 1024 x 768 RGB workload, r = 1, T = 3)."""
     import torch
 
     import paper_1705_01674_gb300 as sg
@@ -955,6 +957,19 @@ def run_case(args):
         for _ in range(n):
             u = sg.sgwls_filter(f, g, 1.0, saved=saved, **kwb)
             sg.sgwls_filter_backward((2.0 * (u - 0.5)).contiguous(), g, saved, 1.0, **kwb)
+    elif case.startswith("headline_r"):
+        # the headline workload itself (1920 x 1080 RGB, T = 2) at radius r
+        Ff, Gf = _inputs(WL["seed"])
+        ff, gf = torch.from_numpy(Ff).to(dev), torch.from_numpy(Gf).to(dev)
+        r = int(case[len("headline_r"):])
+        for _ in range(n):
+            sg.sgwls_filter(ff, gf, WL["lam"], r=r, iters=WL["iters"], sigma_r=WL["sigma_r"])
+    elif case == "rgb1024x768_r1":
+        # 1024 x 768 RGB, r = 1, T = 3 (the smaller RGB workload)
+        F2, G2 = _inputs(2, 768, 1024)
+        f2, g2 = torch.from_numpy(F2).to(dev), torch.from_numpy(G2).to(dev)
+        for _ in range(n):
+            sg.sgwls_filter(f2, g2, 0.5, r=1, iters=3, sigma_r=0.1)
     elif case == "batched":
         imgs, lams = synth.batch_uneven_gray(n=16, seed=4, lo=128, hi=768)
         fs = [torch.from_numpy(x).to(dev) for x in imgs]
@@ -965,7 +980,8 @@ def run_case(args):
     return 0
 
 
-CASES = ("queue", "two_kernel", "recompute", "step2", "refine", "backward", "batched")
+CASES = ("queue", "two_kernel", "recompute", "step2", "refine", "backward", "batched", "headline_r1", "headline_r2",
+         "headline_r3", "headline_r5", "rgb1024x768_r1")
 
 
 def main():

@@ -30,7 +30,12 @@
  *            launched; a failed validation returns an SGWLS_E_* code and
  *            touches no memory.  A CUDA launch failure returns SGWLS_E_CUDA
  *            (the CUDA error string is kept by sgwls_last_cuda_error()).
- * Precision  all elimination arithmetic is FP32; no FP64 on the GPU.
+ * Precision  all elimination arithmetic is FP32; no FP64 on the GPU.  Every
+ *            pivot (in the chunk sweeps, the separator merges and the
+ *            reduced chains) is formed as a row's margin plus the magnitudes
+ *            of its remaining couplings, a sum of non-negative terms
+ *            (Grassmann-Taksar-Heyman elimination of the M-matrix I + lambda
+ *            L), so FP32 keeps A_s's identity where lambda w reaches ~1e7.
  *            `storage` selects FP32 or BF16 for the input/output/guidance
  *            buffers, `inter_storage` for the estimates between passes.
  */
@@ -77,10 +82,10 @@ typedef enum { SGWLS_W_EXP = 0, SGWLS_W_FRAC = 1 } sgwls_weight;
  *               without forming its diagonal (the pair weights recomputed
  *               from the guidance), the solve of rho added to u1, then the
  *               averaging (five kernels per pass instead of two; the
- *               workspace grows by two per-entry buffers).  For
- *               ill-conditioned settings (frac weights, large lambda: lambda
- *               w reaches ~1e7 and the FP32 diagonal 1 + lambda sum w loses
- *               the identity, moving the solution by up to ~5e-3).  Needs
+ *               workspace grows by two per-entry buffers).  An extra
+ *               correction of the FP32 solve; the plain solve's subtraction-
+ *               free pivots already keep the frac weights' large-lambda
+ *               settings (lambda w ~1e7) within 2e-4 of FP64.  Needs
  *               step = 1 and kept factors (not factor_cache = 2); the
  *               batched, backward and no-allocation entry points return
  *               SGWLS_E_UNSUPPORTED for refine = 1

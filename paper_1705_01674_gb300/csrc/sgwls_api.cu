@@ -132,7 +132,14 @@ Plan make_plan(int L, int D, int r, int CC, int chunk_lines, bool bwd = false, b
   auto second = [&](int hh, int G) {
     return keep ? smem_backsub(r, CC, hh, G, step, bwd) : smem_recover(r, CC, hh, G, bwd);
   };
-  auto block = [&](int hh, int G) { return std::max(second(hh, G), smem_summary(r, CC, hh, G, step, gc)); };
+  // k_summary's tile and chunk 2-ports counted side by side (they share
+  // memory in the kernel): the chunk-warp counts below were tuned on GB300
+  // with this measure, which also keeps the large radii (255 registers a
+  // thread) at four chunk-warps a block
+  auto block = [&](int hh, int G) {
+    return std::max(second(hh, G),
+                    4 * (tile_floats(r, CC, hh, G, step, gc) + (size_t)G * (3 * r * r + 2 * r * CC) * 32));
+  };
   int h;
   if (keep && step > 1) {
     // sliding step: fewer subsystems, so fewer warps (see step_lines)

@@ -28,8 +28,11 @@ inline size_t tile_floats(int r, int CC, int h, int G, int step = 1, int gc = 1)
   const int ncol = tile_ncol(r, step);
   return (size_t)(CC + gc) * tile_pstride(G * h + 2, std::max(tile_pitch_n(ncol, 0), tile_pitch_n(ncol, 1)));
 }
+// k_summary: the strip tile and the chunk 2-ports (in the same memory for
+// radius <= 3, see tile_over_2ports).
 inline size_t smem_summary(int r, int CC, int h, int G, int step = 1, int gc = 1) {
-  return 4 * (tile_floats(r, CC, h, G, step, gc) + (size_t)G * (3 * r * r + 2 * r * CC) * 32);
+  const size_t tile = tile_floats(r, CC, h, G, step, gc), ports = (size_t)G * (3 * r * r + 2 * r * CC) * 32;
+  return 4 * (tile_over_2ports(r) ? std::max(tile, ports) : tile + ports);
 }
 inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
   const int n = 2 * r + 1;
@@ -45,9 +48,12 @@ inline size_t smem_recover(int r, int CC, int h, int G, bool bwd = false) {
 // staging; with a sliding step > 1 also each warp's accumulation rows; the
 // adjoint (bwd, CC = u and v planes) writes CC / 2 planes and adds the
 // guidance tile and its dLoss/dG accumulators.
-inline size_t smem_backsub(int r, int CC, int h, int G, int step = 1, bool bwd = false) {
+// dir < 0: the larger of the two directions; the column direction's
+// forward pass at step 1 writes its output lines directly (no output tile).
+inline size_t smem_backsub(int r, int CC, int h, int G, int step = 1, bool bwd = false, int dir = -1) {
   const size_t merge = (size_t)(G - 1) * (3 * r * r + r * CC) * 32 + 2 * (size_t)r * CC * 32;
-  const size_t otile = (size_t)(bwd ? CC / 2 : CC) * step_own_max(r, step) * ((G * h) | 1);
+  const bool no_otile = dir == 0 && step == 1 && !bwd;
+  const size_t otile = no_otile ? 0 : (size_t)(bwd ? CC / 2 : CC) * step_own_max(r, step) * ((G * h) | 1);
   const size_t accum = step > 1 ? (size_t)G * (CC + 1) * step_acc_width(r, step) : 0;
   const size_t gtile = bwd ? 2 * (size_t)(G * h + 2) * (32 + 2 * r) : 0;
   return 4 * ((size_t)G * 2 * r * CC * 32 + merge + otile + accum + gtile);
@@ -179,7 +185,7 @@ cudaError_t launch_pass_rc(const PassArgs& a, const Plan& pl, cudaStream_t st) {
     }
   } else {
     if (b.fac) {   // the factors were kept by k_summary
-      const size_t smem = smem_backsub(R, CC, a.h, pl.G, a.step);
+      const size_t smem = smem_backsub(R, CC, a.h, pl.G, a.step, false, b.xmode != 0 ? -1 : a.dir);
       const int nbx = a.step == 1 ? (a.D + OB - 1) / OB : (a.nsys + step_owned_lanes(R, a.step) - 1) /
                                                               step_owned_lanes(R, a.step);
       auto kern = a.step != 1 ? k_backsub<R, CC, 1> : (b.xmode != 0 ? k_backsub<R, CC, 2> : k_backsub<R, CC, 0>);

@@ -14,12 +14,15 @@
 //   c+1; the rest is the interior I_c = [b, e).  Interiors couple only to
 //   the separators on both sides (bandwidth r < 2r+1 = entries per line).
 //
-// Eliminating a chunk's interior leaves a "2-port" on (S_{c-1}, S_c):
-//   KTT = Y_T' D^-1 Y_T,  KTB = Y_T' D^-1 Y_B,  DS = A(S_c,S_c) - Y_B' D^-1 Y_B,
-//   HT  = Y_T' D^-1 y,    GS  = f(S_c) - Y_B' D^-1 y,
-// with A(I,I) = L D L^T, Y_T = L^-1 A(I,S_{c-1}), Y_B = L^-1 A(I,S_c),
-// y = L^-1 f(I).  Consecutive 2-ports merge by eliminating their shared
-// separator (an associative operation), so the reduction is hierarchical:
+// Eliminating a chunk's interior leaves a "2-port" on (S_{c-1}, S_c): the
+// Schur complement's couplings among the separator entries, the margins
+// (row sums) it passes on to them, and the reduced right-hand sides, with
+// A(I,I) = L D L^T, Y_T = L^-1 A(I,S_{c-1}), Y_B = L^-1 A(I,S_c) and
+// y = L^-1 f(I).  Every pivot is formed as a margin plus coupling
+// magnitudes, a sum of non-negative terms (see gth_row), in the sweeps and
+// in the merges, so FP32 keeps the identity of A_s even where lambda w is
+// ~1e7.  Consecutive 2-ports merge by eliminating their shared separator
+// (an associative operation), so the reduction is hierarchical:
 //
 //   k_summary   block = 32 neighbouring subsystems (lanes) x G chunks (warps).
 //               The block stages its strip tile (estimate planes and guidance)
@@ -65,7 +68,14 @@
 
 namespace sgwls {
 
-// Chunk summary fields (chunk 2-port, and group 2-port in the same format).
+// 2-port fields (chunk 2-port, and group 2-port in the same format), all
+// in margin form: KTT off the diagonal the magnitude of the T_i - T_m
+// coupling Y_T' D^-1 Y_T induces, on it the margin the eliminated entries
+// pass to T_i; KTB the magnitude of the T_i - B_m coupling (Y_T' D^-1 Y_B);
+// DS off the diagonal the magnitude of the B_i - B_m coupling (A's own plus
+// Y_B' D^-1 Y_B), on it B_i's margin (its own 1 plus what it received); HT
+// the right-hand side the eliminated entries add to T_i (-Y_T' D^-1 y); GS
+// B_i's reduced right-hand side (f(S_c) - Y_B' D^-1 y).
 template <int R, int CC>
 struct Fields {
   static constexpr int KTT = 0;
@@ -76,8 +86,10 @@ struct Fields {
   static constexpr int N = 3 * R * R + 2 * R * CC;
 };
 
-// Merge factors kept for the back-fill: Cholesky factor of the eliminated
-// separator block, U = Lm^-1 E_YX, V = Lm^-1 E_YZ, w = Lm^-1 rhs_Y.
+// Merge factors kept for the back-fill (see fold_2ports): LM the eliminated
+// separator's L^T multipliers below the diagonal and reciprocal pivots on
+// it, U and V its couplings to the outer ports and W its right-hand side,
+// each divided by its entry's pivot.
 template <int R, int CC>
 struct MFields {
   static constexpr int LM = 0;
@@ -104,6 +116,9 @@ struct Tile {
     return p + plane * pstride + (line - tl0) * pitch + cs;
   }
 };
+
+// k_summary writes its chunk 2-ports over the strip tile (radius <= 3).
+__host__ __device__ constexpr bool tile_over_2ports(int r) { return r <= 3; }
 
 // Floats between tile planes for ntl lines of `pitch` floats.
 __host__ __device__ constexpr int tile_pstride(int ntl, int pitch) { return (ntl * pitch + 31) / 32 * 32; }
@@ -554,29 +569,30 @@ __device__ __forceinline__ void forward_weights(const PassArgs& a, const float* 
   }
 }
 
-// lambda * w(p, p+t) of every entry of a line (j = 0..2r, t = 1..r), one
-// branch on the weight form per line instead of one per pair.
-template <int R, bool ODD, bool GCM = false>
+// lambda * w(p, p+t) of the entries j = J0 .. J1-1 of a line (t = 1..r), one
+// branch on the weight form per call instead of one per pair.
+template <int R, bool ODD, bool GCM = false, int J0 = 0, int J1 = 2 * R + 1>
 __device__ __forceinline__ void line_weights(const PassArgs& a, const float* gr, const float* gnr, bool end_ok,
                                              float (&wl)[2 * R + 1][R], int gs = 0) {
   constexpr int n = 2 * R + 1;
+  constexpr int GE = J1 + R;   // guidance values g[J0 .. GE-1] are read
   float g[n + R];   // guidance of the line's entries, then of the next line's first r
   if constexpr (GCM) {
     // squared norms of the guidance differences, plane by plane
     float d2[n][R];
 #pragma unroll
-    for (int j = 0; j < n; ++j)
+    for (int j = J0; j < J1; ++j)
 #pragma unroll
       for (int t = 0; t < R; ++t) d2[j][t] = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (k < a.gc) {
 #pragma unroll
-        for (int j = 0; j < n; ++j) g[j] = gr[k * gs + ecol<R, ODD>(j)];
+        for (int j = J0; j < n && j < GE; ++j) g[j] = gr[k * gs + ecol<R, ODD>(j)];
 #pragma unroll
-        for (int m = 0; m < R; ++m) g[n + m] = gnr[k * gs + ecol<R, !ODD>(m)];
+        for (int m = 0; m < R && n + m < GE; ++m) g[n + m] = gnr[k * gs + ecol<R, !ODD>(m)];
 #pragma unroll
-        for (int j = 0; j < n; ++j)
+        for (int j = J0; j < J1; ++j)
 #pragma unroll
           for (int t = 1; t <= R; ++t) {
             const float d = g[j] - g[j + t];
@@ -585,17 +601,17 @@ __device__ __forceinline__ void line_weights(const PassArgs& a, const float* gr,
       }
     }
 #pragma unroll
-    for (int j = 0; j < n; ++j)
+    for (int j = J0; j < J1; ++j)
 #pragma unroll
       for (int t = 1; t <= R; ++t) wl[j][t - 1] = a.sp[j * R + t - 1] * range_factor_sq(a, d2[j][t - 1]);
   } else {
 #pragma unroll
-    for (int j = 0; j < n; ++j) g[j] = gr[ecol<R, ODD>(j)];
+    for (int j = J0; j < n && j < GE; ++j) g[j] = gr[ecol<R, ODD>(j)];
 #pragma unroll
-    for (int k = 0; k < R; ++k) g[n + k] = gnr[ecol<R, !ODD>(k)];
+    for (int k = 0; k < R && n + k < GE; ++k) g[n + k] = gnr[ecol<R, !ODD>(k)];
     if (a.weight == 0) {
 #pragma unroll
-      for (int j = 0; j < n; ++j)
+      for (int j = J0; j < J1; ++j)
 #pragma unroll
         for (int t = 1; t <= R; ++t) {
           const float d = g[j] - g[j + t];
@@ -603,7 +619,7 @@ __device__ __forceinline__ void line_weights(const PassArgs& a, const float* gr,
         }
     } else {
 #pragma unroll
-      for (int j = 0; j < n; ++j)
+      for (int j = J0; j < J1; ++j)
 #pragma unroll
         for (int t = 1; t <= R; ++t)
           wl[j][t - 1] = a.sp[j * R + t - 1] / (powf(fabsf(g[j] - g[j + t]), a.range_k) + a.eps);
@@ -611,7 +627,7 @@ __device__ __forceinline__ void line_weights(const PassArgs& a, const float* gr,
   }
   if (!end_ok) {
 #pragma unroll
-    for (int j = 0; j < n; ++j)
+    for (int j = J0; j < J1; ++j)
 #pragma unroll
       for (int t = 1; t <= R; ++t)
         if (j + t >= n) wl[j][t - 1] = 0.f;
@@ -628,12 +644,34 @@ __device__ __forceinline__ void push_weights(float (&wh)[R][R], const float (&wf
   for (int t = 0; t < R; ++t) wh[0][t] = wf[t];
 }
 
-// One LDL^T row for entry p.  wh[u-1][t-1] = lambda w(p-u, p-u+t); Lw[u-1][v-1]
-// = L[p-u, p-u-v]; Dw[u-1] = 1/D[p-u].  Entries p-t with t > lim are outside
-// the factored interior.  Returns Lrow[t-1] = L[p, p-t] and 1/D[p].
+// One LDL^T row for entry p, with a subtraction-free pivot.
+//
+// A_s = I + lambda L has unit row sums (Eq. 4), so row p of every Schur
+// complement on the way has a non-negative "margin" (its row sum: 1 plus
+// what the eliminated entries passed on) and non-positive off-diagonals;
+// its diagonal is the margin plus the magnitudes of the off-diagonals.
+// Forming the pivot that way, as a sum of non-negative terms, instead of as
+// 1 + lambda sum w - sum (fill), keeps the identity's 1 when lambda w is
+// ~1e7 (the frac weights' settings of Sec. 3), where the subtraction loses
+// it to FP32 rounding.  This is Grassmann, Taksar and Heyman's elimination
+// for M-matrices applied to the band.
+//
+// In:  wh[u-1][t-1] = lambda w(p-u, p-u+t); Lw[u-1][v-1] = L[p-u, p-u-v];
+//      Dw[u-1] = 1/D[p-u]; mw[u-1] = margin of p-u; Uw[u-1][t-1] =
+//      |S[p-u, p-u+t]| (the couplings of p-u to later entries when it was
+//      pivoted; read for t < r); wf[t-1] = lambda w(p, p+t); mbase = 1 plus
+//      the couplings of p to entries outside the factored matrix that are
+//      counted as margin; bit t-1 of `keep` clear: entry p+t lies outside
+//      the factored matrix (its coupling is part of mbase instead).
+//      Entries p-t with t > lim are outside the interior.
+// Out: Lrow[t-1] = L[p, p-t], m = margin of p, Up[t-1] = |S[p, p+t]|;
+//      returns m + sum_t Up[t-1] (the pivot less any couplings the caller
+//      tracks separately).
 template <int R>
-__device__ __forceinline__ float ldl_row(float diag, const float (&wh)[R][R], const float (&Lw)[R][R],
-                                         const float (&Dw)[R], int lim, float (&Lrow)[R]) {
+__device__ __forceinline__ float gth_row(float mbase, const float (&wf)[R], const float (&wh)[R][R],
+                                         const float (&Lw)[R][R], const float (&Dw)[R], const float (&mw)[R],
+                                         const float (&Uw)[R][R], int lim, unsigned keep, float (&Lrow)[R],
+                                         float& m, float (&Up)[R]) {
   float Wt[R];
 #pragma unroll
   for (int t = R; t >= 1; --t) {
@@ -644,10 +682,35 @@ __device__ __forceinline__ float ldl_row(float diag, const float (&wh)[R][R], co
     Wt[t - 1] = in ? acc : 0.f;
     Lrow[t - 1] = in ? acc * Dw[t - 1] : 0.f;
   }
-  float D = diag;
+  m = mbase;
 #pragma unroll
-  for (int t = 0; t < R; ++t) D -= Wt[t] * Lrow[t];
-  return fast_rcp(D);
+  for (int t = 0; t < R; ++t) m -= Lrow[t] * mw[t];
+  float D = m;
+#pragma unroll
+  for (int t = 1; t <= R; ++t) {
+    float u = wf[t - 1];
+    // at distance r no earlier entry couples to both: the coupling is still
+    // A's own, lambda w(p-v, p+t) (wh), so Uw is read for shorter ones only
+#pragma unroll
+    for (int v = 1; v <= R - t; ++v) u -= Lrow[v - 1] * (t + v == R ? wh[v - 1][R - 1] : Uw[v - 1][t + v - 1]);
+    Up[t - 1] = ((keep >> (t - 1)) & 1u) ? u : 0.f;
+    D += Up[t - 1];
+  }
+  return D;
+}
+
+// Shifts the margin and upper-coupling windows by one entry.
+template <int R>
+__device__ __forceinline__ void push_gth(float (&mw)[R], float (&Uw)[R][R], float mp, const float (&Up)[R]) {
+#pragma unroll
+  for (int u = R - 1; u > 0; --u) {
+    mw[u] = mw[u - 1];
+#pragma unroll
+    for (int t = 0; t < R; ++t) Uw[u][t] = Uw[u - 1][t];
+  }
+  mw[0] = mp;
+#pragma unroll
+  for (int t = 0; t < R; ++t) Uw[0][t] = Up[t];
 }
 
 template <int R>
@@ -750,74 +813,6 @@ __device__ __forceinline__ void prologue_weights(const PassArgs& a, const Tile& 
   if (line & 1) pro(std::true_type{}); else pro(std::false_type{});
 }
 
-// ---------------------------------------------------------------------------
-// Small dense helpers (R x R blocks in registers).
-
-// In-place Cholesky M = Lm Lm^T (lower triangle holds Lm, the diagonal holds
-// 1 / Lm_ii).
-template <int R>
-__device__ __forceinline__ void chol_inplace(float (&M)[R][R]) {
-#pragma unroll
-  for (int j = 0; j < R; ++j) {
-    float d = M[j][j];
-#pragma unroll
-    for (int m = 0; m < j; ++m) d -= M[j][m] * M[j][m];
-    const float inv = rsqrtf(d);
-    M[j][j] = inv;
-#pragma unroll
-    for (int i = j + 1; i < R; ++i) {
-      float v = M[i][j];
-#pragma unroll
-      for (int m = 0; m < j; ++m) v -= M[i][m] * M[j][m];
-      M[i][j] = v * inv;
-    }
-  }
-}
-
-// X <- Lm^{-1} X
-template <int R, int K>
-__device__ __forceinline__ void lsolve(const float (&Lm)[R][R], float (&X)[R][K]) {
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-#pragma unroll
-    for (int col = 0; col < K; ++col) {
-      float v = X[i][col];
-#pragma unroll
-      for (int m = 0; m < i; ++m) v -= Lm[i][m] * X[m][col];
-      X[i][col] = v * Lm[i][i];
-    }
-  }
-}
-
-// X <- Lm^{-T} X
-template <int R, int K>
-__device__ __forceinline__ void ltsolve(const float (&Lm)[R][R], float (&X)[R][K]) {
-#pragma unroll
-  for (int i = R - 1; i >= 0; --i) {
-#pragma unroll
-    for (int col = 0; col < K; ++col) {
-      float v = X[i][col];
-#pragma unroll
-      for (int m = i + 1; m < R; ++m) v -= Lm[m][i] * X[m][col];
-      X[i][col] = v * Lm[i][i];
-    }
-  }
-}
-
-// C (+)= sign * A^T B for R x R A and R x K B.
-template <int R, int K>
-__device__ __forceinline__ void add_atb(float (&Cm)[R][K], const float (&A)[R][R], const float (&B)[R][K], float sign) {
-#pragma unroll
-  for (int i = 0; i < R; ++i)
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float v = 0.f;
-#pragma unroll
-      for (int l = 0; l < R; ++l) v += A[l][i] * B[l][k];
-      Cm[i][k] += sign * v;
-    }
-}
-
 // Strided access to the field block of one lane: base[field * stride].
 struct Strided {
   float* base;
@@ -861,9 +856,9 @@ __device__ __forceinline__ float* psi_lane(const PassArgs& a, int sys) {
 }
 // With a.fac set it also keeps, per interior entry, the factor row, z0 and
 // Phi for k_backsub, and psi for the last r interior entries.
-template <int R, int CC, bool KEEP, bool RHSB = false, bool GCM = false>
+template <int R, int CC, bool KEEP, bool RHSB = false, bool GCM = false, typename Out>
 __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, int col, int sys, int c,
-                                              Strided out) {
+                                              Out&& out) {
   const int lane = col;   // tile column of the lane's strip
   constexpr int n = 2 * R + 1;
   constexpr int NFAC = 2 * R + CC;
@@ -886,6 +881,9 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
   float HT[R][CC] = {}, HB[R][CC] = {};
   float DS[R][R] = {};
   float FS[R][CC] = {};
+  float mw[R] = {};        // margins of the last R interior entries
+  float Uw[R][R] = {};     // their couplings to later entries
+  float tauT[R] = {}, tauB[R] = {};   // margin passed to the separators
 
   if (q.top) prologue_weights<R, CC, GCM>(a, t, lane, q.line0 - 1, wh);
 
@@ -896,11 +894,17 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
     const float* gnr = t.row(CC, line + 1) + lane;
     const float* fr = t.row(0, line) + lane;
     const bool end_ok = line + 1 < a.L;
+    // a line's weights: all at once for r <= 2; for r = 3 in two halves
+    // (fewer registers live)
+    constexpr int JH = R == 3 ? R + 1 : n;
     float wl[LW ? n : 1][R];
-    if constexpr (LW) line_weights<R, ODD, GCM>(a, gr, gnr, end_ok, wl, pstride);
+    if constexpr (LW) line_weights<R, ODD, GCM, 0, JH>(a, gr, gnr, end_ok, wl, pstride);
     (void)wl;
 #pragma unroll LineUnroll<R>::value
     for (int j = 0; j < n; ++j) {
+      if constexpr (LW && JH < n) {
+        if (j == JH) line_weights<R, ODD, GCM, JH, n>(a, gr, gnr, end_ok, wl, pstride);
+      }
       float wf[R];
       if constexpr (LW) {
 #pragma unroll
@@ -908,9 +912,6 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
       } else {
         forward_weights<R, ODD, GCM>(a, gr, gnr, j, end_ok, wf, pstride);
       }
-      float diag = 1.f;
-#pragma unroll
-      for (int tt = 0; tt < R; ++tt) diag += wf[tt] + wh[tt][tt];
       float fj[CC];
 #pragma unroll
       for (int ch = 0; ch < CC; ++ch) {
@@ -922,8 +923,10 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
       const bool sep = LAST && q.bot && j >= n - R;
       if (!sep) {
         const int lim = FIRST ? min(j, R) : R;
-        float Lrow[R];
-        const float dinv = ldl_row<R>(diag, wh, Lw, Dw, lim, Lrow);
+        float Lrow[R], mp, Up[R];
+        // the couplings to the bottom separator count among the later
+        // entries', those to the top separator are -YT (added below)
+        float piv = gth_row<R>(1.f, wf, wh, Lw, Dw, mw, Uw, lim, ~0u, Lrow, mp, Up);
         float y[CC];
 #pragma unroll
         for (int ch = 0; ch < CC; ++ch) y[ch] = fj[ch];
@@ -942,10 +945,15 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
             if (tt == j + R - i) YT[i] = FIRST ? -wh[tt - 1][tt - 1] : 0.f;
         fwd_subst<R, R>(Lrow, YTw, YT);
 #pragma unroll
+        for (int i = 0; i < R; ++i) piv -= YT[i];
+        const float dinv = fast_rcp(piv);
+#pragma unroll
         for (int i = 0; i < R; ++i) {
           const float yd = YT[i] * dinv;
 #pragma unroll
-          for (int m = 0; m < R; ++m) KTT[i][m] += yd * YT[m];
+          for (int m = 0; m < R; ++m)
+            if (m > i) KTT[i][m] += yd * YT[m];   // symmetric: the upper part
+          tauT[i] -= yd * mp;
 #pragma unroll
           for (int ch = 0; ch < CC; ++ch) HT[i][ch] += yd * y[ch];
         }
@@ -975,9 +983,10 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
               const float yd = YB[i] * dinv;
 #pragma unroll
               for (int m = 0; m < R; ++m) {
-                KBB[i][m] += yd * YB[m];
+                if (m > i) KBB[i][m] += yd * YB[m];
                 KTB[m][i] += yd * YT[m];
               }
+              tauB[i] -= yd * mp;
 #pragma unroll
               for (int ch = 0; ch < CC; ++ch) HB[i][ch] += yd * y[ch];
             }
@@ -990,18 +999,20 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
           push_vec<R, R>(YBw, YB);
         }
         push_factor<R>(Lw, Dw, Lrow, dinv);
+        push_gth<R>(mw, Uw, mp, Up);
         push_vec<R, CC>(yw, y);
         push_vec<R, R>(YTw, YT);
       } else {
-        // separator entry e + i: its diagonal, its couplings inside S_c, f(S_c)
+        // separator entry e + i: its own margin 1, the magnitudes of its
+        // couplings inside S_c, f(S_c)
         const int isep = j - (n - R);
 #pragma unroll
         for (int i = 0; i < R; ++i) {
           if (i == isep) {
-            DS[i][i] = diag;
+            DS[i][i] = 1.f;
 #pragma unroll
-            for (int m = 0; m < i; ++m) {  // A[e+i, e+m] = -lambda w(e+m, e+i)
-              DS[i][m] = -wh[i - m - 1][i - m - 1];
+            for (int m = 0; m < i; ++m) {  // |A[e+i, e+m]| = lambda w(e+m, e+i)
+              DS[i][m] = wh[i - m - 1][i - m - 1];
               DS[m][i] = DS[i][m];
             }
 #pragma unroll
@@ -1013,17 +1024,18 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
     }
   });
 
+  // the 2-port in margin form (see Fields)
 #pragma unroll
   for (int i = 0; i < R; ++i) {
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      out[F::KTT + i * R + m] = KTT[i][m];
+      out[F::KTT + i * R + m] = m == i ? tauT[i] : KTT[min(i, m)][max(i, m)];
       out[F::KTB + i * R + m] = KTB[i][m];
-      out[F::DS + i * R + m] = DS[i][m] - KBB[i][m];
+      out[F::DS + i * R + m] = m == i ? DS[i][i] + tauB[i] : DS[i][m] + KBB[min(i, m)][max(i, m)];
     }
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) {
-      out[F::HT + i * CC + ch] = HT[i][ch];
+      out[F::HT + i * CC + ch] = -HT[i][ch];
       out[F::GS + i * CC + ch] = FS[i][ch] - HB[i][ch];
     }
   }
@@ -1070,115 +1082,167 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, int c0, int G, int
   t.p = p;
 }
 
-// Folds n consecutive 2-ports (chunk-summary format; in(i) addresses element
-// i's fields) into one by eliminating the n-1 separators between them, left
-// to right.  Element 0 has a top port iff acc_top; element i has a bottom
-// port iff has_bot(i).  Merge i (1 <= i < n) keeps its factors through mf(i)
-// -- Cholesky factor Lm of the separator block, U = Lm^-1 E_YX,
-// V = Lm^-1 E_YZ, w = Lm^-1 rhs_Y -- for the back-fill; out receives the
-// folded 2-port.  Lane = subsystem.
+// Folds n consecutive 2-ports (Fields format; in(i) addresses element i's
+// fields) into one by eliminating the n-1 separators between them, left to
+// right.  Element 0 has a top port iff acc_top; element i has a bottom port
+// iff has_bot(i).  Merge i (1 <= i < n) eliminates separator Y (element
+// i-1's bottom = element i's top) from the rows of Y, X (the fold's top) and
+// Z (element i's bottom) of the reduced system, entry by entry and without
+// subtraction: Y's rows have margin DS_{i-1} + KTT_i on the diagonal slots,
+// couplings |Y_a - Y_b| = the two off-diagonal parts summed, |Y - X| =
+// KTB_{i-1}^T, |Y - Z| = KTB_i and right-hand side GS_{i-1} + HT_i; the
+// pivot of Y_a is its margin plus its remaining couplings, and eliminating
+// it passes c = coupling / pivot times its margin, couplings and right-hand
+// side on to every row it couples to.  Merge i keeps, through mf(i), what
+// the back-fill needs: LM (below the diagonal c of the later Y entries,
+// on it 1 / pivot), U = |Y - X| / pivot, V = |Y - Z| / pivot and
+// W = rhs_Y / pivot, each taken when its entry was pivoted.  out receives
+// the folded 2-port.  Lane = subsystem.
 template <int R, int CC, typename In, typename HasBot, typename Mf, typename Out>
 __device__ __forceinline__ void fold_2ports(int n, bool acc_top, In&& in, HasBot&& has_bot, Mf&& mf, Out&& out) {
   using F = Fields<R, CC>;
   using MF = MFields<R, CC>;
   auto cs = in(0);
-  float ETT[R][R], ETB[R][R], EBB[R][R], qT[R][CC], qB[R][CC];
+  // the fold so far: X (its top), B (its bottom, the next Y)
+  float XX[R][R], XB[R][R], BB[R][R], bX[R][CC], bB[R][CC];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      ETT[i][m] = -cs[F::KTT + i * R + m];
-      ETB[i][m] = -cs[F::KTB + i * R + m];
-      EBB[i][m] = cs[F::DS + i * R + m];
+      XX[i][m] = cs[F::KTT + i * R + m];
+      XB[i][m] = cs[F::KTB + i * R + m];
+      BB[i][m] = cs[F::DS + i * R + m];
     }
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) {
-      qT[i][ch] = -cs[F::HT + i * CC + ch];
-      qB[i][ch] = cs[F::GS + i * CC + ch];
+      bX[i][ch] = cs[F::HT + i * CC + ch];
+      bB[i][ch] = cs[F::GS + i * CC + ch];
     }
   }
-  // Small 2-ports: element i's fields are read one merge ahead (before merge
-  // i-1 writes its factors, which may overwrite element i-1 in place), so
-  // the loads leave the serial path.
-  constexpr bool PREF = F::N <= 40;
-  constexpr int NB = PREF ? F::N : 1;
-  float nb[NB], cb[NB];
-  auto load = [&](int i) {
+  // Element i's KTT, KTB and HT (the fields its merge needs first) are read
+  // one merge ahead, its DS and GS (needed after the separator's pivots) at
+  // the start of its merge; both before merge i writes its factors, which
+  // may overwrite element i in place.  The loads leave the serial path.
+  float pT[R][R], pK[R][R], pH[R][CC];
+  auto load_early = [&](int i) {
     auto src = in(i);
-#pragma unroll
-    for (int f = 0; f < NB; ++f) nb[f] = src[f];
-  };
-  if (PREF && n > 1) load(1);
-  for (int i = 1; i < n; ++i) {
-    const bool b_bot = has_bot(i);
-    auto direct = in(i);
-    if constexpr (PREF) {
-#pragma unroll
-      for (int f = 0; f < NB; ++f) cb[f] = nb[f];
-      if (i + 1 < n) load(i + 1);
-    }
-    auto bs = [&](int f) -> float { if constexpr (PREF) return cb[f < NB ? f : 0]; else return direct[f]; };
-    float M[R][R], U[R][R], V[R][R], w[R][CC];
 #pragma unroll
     for (int y = 0; y < R; ++y) {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        M[y][m] = EBB[y][m] - bs(F::KTT + y * R + m);
-        U[y][m] = ETB[m][y];                       // E_YX = E_XY^T
-        V[y][m] = -bs(F::KTB + y * R + m);         // E_YZ
+        pT[y][m] = src[F::KTT + y * R + m];
+        pK[y][m] = src[F::KTB + y * R + m];
       }
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) w[y][ch] = qB[y][ch] - bs(F::HT + y * CC + ch);
+      for (int ch = 0; ch < CC; ++ch) pH[y][ch] = src[F::HT + y * CC + ch];
     }
-    chol_inplace<R>(M);
-    lsolve<R, R>(M, U);
-    lsolve<R, R>(M, V);
-    lsolve<R, CC>(M, w);
-    if (acc_top) {
-      add_atb<R, R>(ETT, U, U, -1.f);
-      add_atb<R, CC>(qT, U, w, -1.f);
-    }
-#pragma unroll
-    for (int y = 0; y < R; ++y)
-#pragma unroll
-      for (int m = 0; m < R; ++m) ETB[y][m] = 0.f;
-    if (acc_top && b_bot) add_atb<R, R>(ETB, U, V, -1.f);
+  };
+  if (n > 1) load_early(1);
+  for (int i = 1; i < n; ++i) {
+    const bool zb = has_bot(i);
+    auto direct = in(i);
+    float YY[R][R], YX[R][R], YZ[R][R], bY[R][CC], ZZ[R][R], bZ[R][CC], XZ[R][R];
 #pragma unroll
     for (int y = 0; y < R; ++y) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) EBB[y][m] = b_bot ? bs(F::DS + y * R + m) : 0.f;
+      for (int m = 0; m < R; ++m) {
+        YY[y][m] = BB[y][m] + pT[y][m];
+        YX[y][m] = acc_top ? XB[m][y] : 0.f;
+        YZ[y][m] = zb ? pK[y][m] : 0.f;
+        ZZ[y][m] = zb ? direct[F::DS + y * R + m] : 0.f;
+        XZ[y][m] = 0.f;
+      }
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) qB[y][ch] = b_bot ? bs(F::GS + y * CC + ch) : 0.f;
+      for (int ch = 0; ch < CC; ++ch) {
+        bY[y][ch] = bB[y][ch] + pH[y][ch];
+        bZ[y][ch] = zb ? direct[F::GS + y * CC + ch] : 0.f;
+      }
     }
-    if (b_bot) {
-      add_atb<R, R>(EBB, V, V, -1.f);
-      add_atb<R, CC>(qB, V, w, -1.f);
-    }
+    if (i + 1 < n) load_early(i + 1);
     auto md = mf(i);
 #pragma unroll
     for (int y = 0; y < R; ++y) {
+      float d = YY[y][y];
 #pragma unroll
       for (int m = 0; m < R; ++m) {
-        md[MF::LM + y * R + m] = M[y][m];
-        md[MF::U + y * R + m] = U[y][m];
-        md[MF::V + y * R + m] = V[y][m];
+        if (m > y) d += YY[y][m];
+        d += YX[y][m] + YZ[y][m];
+      }
+      const float dinv = fast_rcp(d);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        md[MF::LM + m * R + y] = m == y ? dinv : (m > y ? YY[y][m] * dinv : 0.f);
+        md[MF::U + y * R + m] = YX[y][m] * dinv;
+        md[MF::V + y * R + m] = YZ[y][m] * dinv;
       }
 #pragma unroll
-      for (int ch = 0; ch < CC; ++ch) md[MF::W + y * CC + ch] = w[y][ch];
+      for (int ch = 0; ch < CC; ++ch) md[MF::W + y * CC + ch] = bY[y][ch] * dinv;
+      // pass Y_y's margin, couplings and right-hand side on
+#pragma unroll
+      for (int y2 = y + 1; y2 < R; ++y2) {
+        const float c = YY[y][y2] * dinv;
+        YY[y2][y2] += c * YY[y][y];
+#pragma unroll
+        for (int y3 = y + 1; y3 < R; ++y3)
+          if (y3 != y2) YY[y2][y3] += c * YY[y][y3];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          YX[y2][m] += c * YX[y][m];
+          YZ[y2][m] += c * YZ[y][m];
+        }
+#pragma unroll
+        for (int ch = 0; ch < CC; ++ch) bY[y2][ch] += c * bY[y][ch];
+      }
+      if (acc_top) {
+#pragma unroll
+        for (int x = 0; x < R; ++x) {
+          const float c = YX[y][x] * dinv;
+          XX[x][x] += c * YY[y][y];
+#pragma unroll
+          for (int x2 = 0; x2 < R; ++x2)
+            if (x2 != x) XX[x][x2] += c * YX[y][x2];
+#pragma unroll
+          for (int z = 0; z < R; ++z) XZ[x][z] += c * YZ[y][z];
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch) bX[x][ch] += c * bY[y][ch];
+        }
+      }
+      if (zb) {
+#pragma unroll
+        for (int z = 0; z < R; ++z) {
+          const float c = YZ[y][z] * dinv;
+          ZZ[z][z] += c * YY[y][y];
+#pragma unroll
+          for (int z2 = 0; z2 < R; ++z2)
+            if (z2 != z) ZZ[z][z2] += c * YZ[y][z2];
+#pragma unroll
+          for (int ch = 0; ch < CC; ++ch) bZ[z][ch] += c * bY[y][ch];
+        }
+      }
+    }
+#pragma unroll
+    for (int y = 0; y < R; ++y) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        XB[y][m] = XZ[y][m];
+        BB[y][m] = ZZ[y][m];
+      }
+#pragma unroll
+      for (int ch = 0; ch < CC; ++ch) bB[y][ch] = bZ[y][ch];
     }
   }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      out[F::KTT + i * R + m] = -ETT[i][m];
-      out[F::KTB + i * R + m] = -ETB[i][m];
-      out[F::DS + i * R + m] = EBB[i][m];
+      out[F::KTT + i * R + m] = XX[i][m];
+      out[F::KTB + i * R + m] = XB[i][m];
+      out[F::DS + i * R + m] = BB[i][m];
     }
 #pragma unroll
     for (int ch = 0; ch < CC; ++ch) {
-      out[F::HT + i * CC + ch] = -qT[i][ch];
-      out[F::GS + i * CC + ch] = qB[i][ch];
+      out[F::HT + i * CC + ch] = bX[i][ch];
+      out[F::GS + i * CC + ch] = bB[i][ch];
     }
   }
 }
@@ -1186,31 +1250,47 @@ __device__ __forceinline__ void fold_2ports(int n, bool acc_top, In&& in, HasBot
 // Back-fill of a fold: given the outer separators xX (above element 0, used
 // iff acc_top) and xZ (below element n-1, used iff has_bot(n-1)), recovers
 // the separators between the elements, bottom to top: put(i, x) receives the
-// separator between elements i-1 and i.
+// separator between elements i-1 and i,
+//   x_Y[y] = W[y] + U[y] xX + V[y] xZ + sum_{m > y} LM[m][y] x_Y[m].
 template <int R, int CC, typename HasBot, typename Mf, typename Put>
 __device__ __forceinline__ void backfill_2ports(int n, bool acc_top, const float (&xX)[R][CC], float (&xZ)[R][CC],
                                                 HasBot&& has_bot, Mf&& mf, Put&& put) {
   using MF = MFields<R, CC>;
+  // small factor sets: merge i-1's are read while merge i is solved (put
+  // may write memory the factors live in as far as the compiler knows)
+  constexpr bool PREF = MF::N <= 40;
+  constexpr int NB = PREF ? MF::N : 1;
+  float nb[NB], cb[NB];
+  auto load = [&](int i) {
+    auto src = mf(i);
+#pragma unroll
+    for (int f = 0; f < NB; ++f) nb[f] = src[f];
+  };
+  if (PREF && n > 1) load(n - 1);
   for (int i = n - 1; i >= 1; --i) {
     const bool b_bot = has_bot(i);
-    auto md = mf(i);
-    float Lm[R][R], v[R][CC];
+    auto direct = mf(i);
+    if constexpr (PREF) {
 #pragma unroll
-    for (int y = 0; y < R; ++y) {
+      for (int f = 0; f < NB; ++f) cb[f] = nb[f];
+      if (i > 1) load(i - 1);
+    }
+    auto md = [&](int f) -> float { if constexpr (PREF) return cb[f < NB ? f : 0]; else return direct[f]; };
+    float v[R][CC];
 #pragma unroll
-      for (int m = 0; m < R; ++m) Lm[y][m] = md[MF::LM + y * R + m];
+    for (int y = R - 1; y >= 0; --y) {
 #pragma unroll
       for (int ch = 0; ch < CC; ++ch) {
-        float acc = md[MF::W + y * CC + ch];
+        float acc = md(MF::W + y * CC + ch);
 #pragma unroll
         for (int m = 0; m < R; ++m) {
-          if (acc_top) acc -= md[MF::U + y * R + m] * xX[m][ch];
-          if (b_bot) acc -= md[MF::V + y * R + m] * xZ[m][ch];
+          if (acc_top) acc += md(MF::U + y * R + m) * xX[m][ch];
+          if (b_bot) acc += md(MF::V + y * R + m) * xZ[m][ch];
+          if (m > y) acc += md(MF::LM + m * R + y) * v[m][ch];
         }
         v[y][ch] = acc;
       }
     }
-    ltsolve<R, CC>(Lm, v);
     put(i, v);
 #pragma unroll
     for (int y = 0; y < R; ++y)
@@ -1253,126 +1333,35 @@ __device__ __forceinline__ void merge_tree(const PassArgs& a, float* csum, int l
   }
 }
 
-// Block Cholesky of the separator system of NG consecutive 2-ports of one
-// subsystem (the serial chain).  `fld(g, field)` addresses the 2-ports; the
-// inputs of step g+1 are read before step g is computed.  The factors L_g,
-// Z_g = L_{g-1}^{-1} (-KTB_g) and w_g are written over DS_g, KTB_g and GS_g;
-// the value of the separator between 2-ports g and g+1 goes to xsep as
-// group separator xidx(g) (skipped when !store).
+// The separator system of NG consecutive 2-ports of one subsystem (the
+// serial chain): fold_2ports over all of them (the first has no top port,
+// the last no bottom port), merge g's factors written over 2-port g in
+// place, then the back-fill.  `fld(g, field)` addresses the 2-ports; the
+// value of the separator between 2-ports g and g+1 goes to xsep as group
+// separator xidx(g) (skipped when !store).
 template <int R, int CC, typename Fld, typename Xidx>
 __device__ __forceinline__ void reduced_chain(const PassArgs& a, int sys, int NG, bool store, Fld&& fld,
                                               Xidx&& xidx) {
   using F = Fields<R, CC>;
   const long long ns = a.sstride;
-  // inputs of step g: M0 = DS_g - KTT_{g+1}, r0 = GS_g - HT_{g+1}, B = -KTB_g
-  auto load_step = [&](int g, float (&M)[R][R], float (&rhs)[R][CC], float (&B)[R][R]) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        M[i][m] = fld(g, F::DS + i * R + m) - fld(g + 1, F::KTT + i * R + m);
-        B[i][m] = g >= 1 ? -fld(g, F::KTB + i * R + m) : 0.f;
-      }
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) rhs[i][ch] = fld(g, F::GS + i * CC + ch) - fld(g + 1, F::HT + i * CC + ch);
-    }
+  struct Slot {
+    Fld* f;
+    int g;
+    __device__ __forceinline__ float& operator[](int field) const { return (*f)(g, field); }
   };
-  float Lp[R][R];    // L_{g-1}
-  float wp[R][CC];   // w_{g-1}
-  float Mn[R][R], rn[R][CC], Bn[R][R];
-  load_step(0, Mn, rn, Bn);
-  for (int g = 0; g <= NG - 2; ++g) {
-    float M[R][R], rhs[R][CC], Z[R][R];
+  auto slot = [&](int g) { return Slot{&fld, g}; };
+  auto has_bot = [&](int g) { return g < NG - 1; };
+  float sink[F::N];   // the folded 2-port of the whole subsystem has no ports
+  fold_2ports<R, CC>(NG, false, slot, has_bot, slot, sink);
+  float xX[R][CC] = {}, xZ[R][CC] = {};
+  backfill_2ports<R, CC>(NG, false, xX, xZ, has_bot, slot, [&](int i, const float (&v)[R][CC]) {
+    if (!store) return;
+    const long long xb = (long long)xidx(i - 1) * R * CC;
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
+    for (int y = 0; y < R; ++y)
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        M[i][m] = Mn[i][m];
-        Z[i][m] = Bn[i][m];
-      }
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) rhs[i][ch] = rn[i][ch];
-    }
-    if (g + 1 <= NG - 2) load_step(g + 1, Mn, rn, Bn);
-    if (g >= 1) {
-      lsolve<R, R>(Lp, Z);
-      add_atb<R, R>(M, Z, Z, -1.f);
-      add_atb<R, CC>(rhs, Z, wp, -1.f);
-    }
-    chol_inplace<R>(M);
-    lsolve<R, CC>(M, rhs);
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        if (g >= 1) fld(g, F::KTB + i * R + m) = Z[i][m];
-        fld(g, F::DS + i * R + m) = M[i][m];
-        Lp[i][m] = M[i][m];
-      }
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) {
-        fld(g, F::GS + i * CC + ch) = rhs[i][ch];
-        wp[i][ch] = rhs[i][ch];
-      }
-    }
-  }
-  // back substitution: x_g = L_g^{-T} (w_g - Z_{g+1} x_{g+1})
-  float x[R][CC];
-#pragma unroll
-  for (int i = 0; i < R; ++i)
-#pragma unroll
-    for (int ch = 0; ch < CC; ++ch) x[i][ch] = wp[i][ch];
-  ltsolve<R, CC>(Lp, x);
-  if (store) {
-    const long long xb = (long long)xidx(NG - 2) * R * CC;
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) a.xsep[(xb + i * CC + ch) * ns + sys] = x[i][ch];
-  }
-  float Lc[R][R], v[R][CC], Zc[R][R];
-  auto load_back = [&](int g) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        Lc[i][m] = fld(g, F::DS + i * R + m);
-        Zc[i][m] = fld(g + 1, F::KTB + i * R + m);
-      }
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) v[i][ch] = fld(g, F::GS + i * CC + ch);
-    }
-  };
-  if (NG >= 3) load_back(NG - 3);
-  for (int g = NG - 3; g >= 0; --g) {
-    float Lg[R][R], vg[R][CC], Zg[R][R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-#pragma unroll
-      for (int m = 0; m < R; ++m) {
-        Lg[i][m] = Lc[i][m];
-        Zg[i][m] = Zc[i][m];
-      }
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) vg[i][ch] = v[i][ch];
-    }
-    if (g >= 1) load_back(g - 1);
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-      for (int m = 0; m < R; ++m)
-#pragma unroll
-        for (int ch = 0; ch < CC; ++ch) vg[i][ch] -= Zg[i][m] * x[m][ch];
-    ltsolve<R, CC>(Lg, vg);
-    const long long xb = (long long)xidx(g) * R * CC;
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-#pragma unroll
-      for (int ch = 0; ch < CC; ++ch) {
-        x[i][ch] = vg[i][ch];
-        if (store) a.xsep[(xb + i * CC + ch) * ns + sys] = vg[i][ch];
-      }
-  }
+      for (int ch = 0; ch < CC; ++ch) a.xsep[(xb + y * CC + ch) * ns + sys] = v[y][ch];
+  });
 }
 
 // Segment length of the reduced chain of NG group 2-ports run by nw warps:
@@ -1488,7 +1477,12 @@ __device__ __forceinline__ bool body_summary(const PassArgs& a, int bx, int by, 
   group_tile(a, c0, G, off0, unit ? 32 + 2 * R : tile_ncol(R, a.step), unit, smem, t);
   // SM 3: a guidance of a.gc planes (tile planes CC .. CC + gc - 1)
   const int np = CC + (SM == 3 ? a.gc : 1);
-  float* csum = smem + np * t.pstride;   // [G][F::N][32]
+  // [G][F::N][32]: the chunk 2-ports.  Radius <= 3: written over the tile
+  // once every warp finished its sweep (a block holds the tile or the
+  // 2-ports, not both); larger radii (2-ports of 60+ values, too many to
+  // hold across the barrier) after the tile.
+  constexpr bool OVER = tile_over_2ports(R);
+  float* csum = OVER ? smem : smem + np * t.pstride;
   // The guidance is an input of the whole filter (no kernel of the filter
   // writes it): its planes are staged before the wait, overlapping the
   // preceding kernel's tail; the estimate planes after it.
@@ -1512,10 +1506,19 @@ __device__ __forceinline__ bool body_summary(const PassArgs& a, int bx, int by, 
   __syncthreads();
 
   const bool active = sys < a.nsys;
-  if (active && threadIdx.y < nch) {
-    const Strided out{csum + threadIdx.y * F::N * 32 + lane, 32};
-    const int col = unit ? lane : centre_of(a, sys, R) - R - off0;   // the lane's strip in the tile
-    chunk_summary<R, CC, SM != 0, SM == 2, SM == 3>(a, t, col, sys, c, out);
+  const bool mine = active && threadIdx.y < nch;
+  const int col = unit ? lane : centre_of(a, sys, R) - R - off0;   // the lane's strip in the tile
+  if constexpr (OVER) {
+    float outv[F::N];
+    if (mine) chunk_summary<R, CC, SM != 0, SM == 2, SM == 3>(a, t, col, sys, c, outv);
+    __syncthreads();   // the tile is read no more
+    if (mine) {
+#pragma unroll
+      for (int f = 0; f < F::N; ++f) csum[(threadIdx.y * F::N + f) * 32 + lane] = outv[f];
+    }
+  } else {
+    if (mine)
+      chunk_summary<R, CC, SM != 0, SM == 2, SM == 3>(a, t, col, sys, c, Strided{csum + threadIdx.y * F::N * 32 + lane, 32});
   }
   __syncthreads();
   merge_tree<R, CC>(a, csum, lane, sys, grp, c0, nch, G, active);
@@ -1535,8 +1538,12 @@ __device__ __forceinline__ bool body_summary(const PassArgs& a, int bx, int by, 
   return true;
 }
 
+// Blocks of 256 threads per SM that the registers must allow (the block's
+// shared memory allows them): four at radius 1, three at radius 2, two at
+// radius 3; larger radii keep their r x r windows in up to 255 registers.
 template <int R, int CC, int SM>
-__global__ void __launch_bounds__(256) k_summary(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 3 : R == 3 ? 2 : 1)
+    k_summary(const __grid_constant__ PassArgs a) {
   extern __shared__ __align__(128) float smem[];
   body_summary<R, CC, SM>(a, blockIdx.x, blockIdx.y, smem);
 }
@@ -1760,6 +1767,8 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
     float wh[R][R] = {};
     float Lw[R][R] = {};
     float Dw[R] = {};
+    float mw[R] = {};
+    float Uw[R][R] = {};
     float yw[R][CC] = {};
     if (q.top) prologue_weights<R, CC>(a, t, lane, q.line0 - 1, wh);
     for_lines(q.line0, q.line1, [&](auto odd, const bool FIRST, auto last, int line) {
@@ -1776,11 +1785,29 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
         forward_weights<R, ODD>(a, gr, gnr, j, end_ok, wf);
         const bool sep = LAST && q.bot && j >= n - R;
         if (!sep) {
-          float diag = 1.f;
+          // the factored matrix is the interior alone: the couplings to the
+          // separators (known values, moved to the right-hand side below)
+          // count as margin
+          float mbase = 1.f;
+          unsigned keep = ~0u;
+          if (FIRST && q.top) {
 #pragma unroll
-          for (int tt = 0; tt < R; ++tt) diag += wf[tt] + wh[tt][tt];
-          float Lrow[R];
-          const float dinv = ldl_row<R>(diag, wh, Lw, Dw, FIRST ? min(j, R) : R, Lrow);
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+              for (int tt = 1; tt <= R; ++tt)
+                if (tt == j + R - i) mbase += wh[tt - 1][tt - 1];
+          }
+          if (LAST && q.bot) {
+#pragma unroll
+            for (int tt = 1; tt <= R; ++tt)
+              if (j + tt >= n - R) {
+                mbase += wf[tt - 1];
+                keep &= ~(1u << (tt - 1));
+              }
+          }
+          float Lrow[R], mp, Up[R];
+          const float dinv =
+              fast_rcp(gth_row<R>(mbase, wf, wh, Lw, Dw, mw, Uw, FIRST ? min(j, R) : R, keep, Lrow, mp, Up));
           float y[CC];
 #pragma unroll
           for (int ch = 0; ch < CC; ++ch) y[ch] = fr[ch * pstride + ecol<R, ODD>(j)];
@@ -1815,6 +1842,7 @@ __device__ __forceinline__ void body_recover(const PassArgs& a, int bx, int by, 
 #pragma unroll
           for (int ch = 0; ch < CC; ++ch) slot[(R + ch) * 32] = y[ch] * dinv;
           push_factor<R>(Lw, Dw, Lrow, dinv);
+          push_gth<R>(mw, Uw, mp, Up);
           push_vec<R, CC>(yw, y);
         }
         push_weights<R>(wh, wf);

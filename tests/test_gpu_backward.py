@@ -85,6 +85,21 @@ def test_backward_frac_weights(api):
     assert abs(gl - rl) <= REL * abs(rl)
 
 
+def test_backward_frac_application_setting(api):
+    """The adjoint at the frac weights' HDR setting (lambda = 320, lambda w
+    up to ~3e6): the u and v solves run on the same margin-form pivots as
+    the forward, so the f and lambda gradients keep their 1e-3 bound."""
+    rng = np.random.default_rng(8)
+    F3 = synth.rgb_scene(30, 33, seed=78, n_rect=8, n_disk=2)
+    G = synth.luminance(F3)
+    Ubar = rng.normal(size=F3.shape).astype(np.float32)
+    kw = dict(r=1, iters=1, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+    gf, gg, gl = _gpu_grads(api, F3, G, 320.0, Ubar, **kw)
+    rf, rg, rl = sgwls_vjp(F3.astype(np.float64), G.astype(np.float64), 320.0, _prm(**kw), Ubar.astype(np.float64))
+    assert _rel(gf, rf) <= REL, _rel(gf, rf)
+    assert abs(gl - rl) <= REL * abs(rl), (gl, rl)
+
+
 def test_backward_central_differences_32x32(api):
     """GPU gradients against FP64 central differences of the oracle's forward
     map on a 32x32 crop (loss = sum((U - target)^2))."""

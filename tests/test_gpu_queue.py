@@ -3,8 +3,10 @@ kept factors at sliding step 1): one persistent kernel whose blocks
 take summary and back-substitution work items from a queue, with the
 factor store a ring of band slots.
 
-It runs the same per-item arithmetic as the two-kernel pass (schedule = 1),
-so the two must agree bit for bit; both are compared with the FP64 oracle.
+It runs the same per-item arithmetic as the two-kernel pass (schedule = 1);
+the two kernels are compiled separately, so the compiler may fuse a multiply
+and an add in one and not in the other: they must agree to FP32 rounding
+(1e-6 on [0, 1] values), and both are compared with the FP64 oracle.
 Small rings (ring_slots = 4, the minimum) make every band after the fourth
 wait for the readers of the band whose slot it reuses.  After every case
 the device error flag (set when a bounded wait gives up) must be clear."""
@@ -54,7 +56,9 @@ def test_queue_matches_two_kernels_and_oracle(api, r, shape):
                   dict(schedule=2, chunk_lines=3), dict(schedule=2, lookahead=40)):
         u2 = _run(api, f, g, 1.3, **sched, **kw)
         if "chunk_lines" not in sched:
-            assert torch.equal(u1, u2), sched   # the same arithmetic, another order of work items
+            # the same arithmetic, another order of work items
+            d = float((u1 - u2).abs().max())
+            assert d <= 1e-6, (sched, d)
         err = float(np.abs(u2.cpu().numpy().astype(np.float64) - ref).max())
         assert err <= TOL, (sched, err)
     assert api.device_flag() == 0

@@ -2,10 +2,10 @@
 residual rho = f - u1 - lambda L u1 (A = I + lambda L applied without
 forming its diagonal, the pair weights recomputed from the guidance),
 u = u1 + A~^-1 rho, then the averaging.  At the paper's frac-weight
-application settings (alpha = 1.2, eps = 1e-4, lambda 5 .. 900) the
-unrefined FP32 result sits up to ~5e-3 from the FP64 oracle because the
-FP32 diagonal 1 + lambda sum w (lambda w ~ 1e7) loses the identity; one
-refinement step brings it back within 2e-4."""
+application settings (alpha = 1.2, eps = 1e-4, lambda 5 .. 900), where a
+diagonal formed as 1 + lambda sum w in FP32 would lose the identity, both
+the plain solve (margin-form pivots) and the refined one stay within 2e-4
+of the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -45,8 +45,8 @@ def test_refine_frac_application_settings(api, lam, r):
                 Params(r=r, iters=2, weight="frac", alpha_s=1.2, alpha_r=1.2, eps=1e-4))
     err0 = float(np.abs(_run(api, F, G, lam, **kw) - ref).max())
     err1 = float(np.abs(_run(api, F, G, lam, refine=1, **kw) - ref).max())
+    assert err0 <= TOL, (err0, err1)
     assert err1 <= TOL, (err0, err1)
-    assert err1 < err0
 
 
 @pytest.mark.parametrize("r", [1, 2, 3])
