@@ -108,6 +108,7 @@ inline int keep_lines(int r) { return r == 1 ? 6 : r == 2 ? 12 : r == 3 ? 8 : 16
 // tensor-copy staging (8 lines where the sweep found no better length, and
 // beyond r = 5 or tau = 5).
 inline int step_lines(int r, int step) {
+  if (r == 2 && step == 2) return 6;
   if (r == 3) return step == 2 ? 6 : step == 3 ? 12 : 8;
   if (r == 4) return step == 2 ? 6 : 8;
   if (r == 5) return (step == 3 || step == 4) ? 6 : step == 5 ? 12 : 8;
