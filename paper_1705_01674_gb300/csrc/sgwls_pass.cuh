@@ -2178,9 +2178,33 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
     const long long ostride = a.dir == 0 ? 1 : a.W;
     const long long lstride = a.dir == 0 ? a.W : 1;
     float* const outp = reinterpret_cast<float*>(a.out);
+    // r = 1 (few factor values a line): the next line's factor rows are
+    // loaded into registers while the current line is solved, so the loads
+    // of two lines are in flight at once
+    constexpr bool PIPE = R == 1 && !BWD;
+    float fnext[PIPE ? n : 1][PIPE ? NFAC : 1];
+    auto load_line = [&](int l) {
+      if constexpr (PIPE) {
+        const float* f0 = fac + l * n * NFAC * 32;
+#pragma unroll
+        for (int j = 0; j < n; ++j)
+#pragma unroll
+          for (int f = 0; f < NFAC; ++f) fnext[j][f] = __ldcg(f0 + (j * NFAC + f) * 32);
+      }
+    };
+    if constexpr (PIPE) load_line(q.line1 - 1);
     for_lines_rev(q.line0, q.line1, [&](auto odd, auto last, int line) {
       constexpr bool ODD = decltype(odd)::value;
       constexpr bool LAST = decltype(last)::value;
+      float fcur[PIPE ? n : 1][PIPE ? NFAC : 1];
+      if constexpr (PIPE) {
+#pragma unroll
+        for (int j = 0; j < n; ++j)
+#pragma unroll
+          for (int f = 0; f < NFAC; ++f) fcur[j][f] = fnext[j][f];
+        if (line > q.line0) load_line(line - 1);
+      }
+      (void)fcur;
       float xl[n][CC];
       const float* fl = fac + line * n * NFAC * 32;
 #pragma unroll LineUnroll<R>::value
@@ -2194,7 +2218,9 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
               for (int ch = 0; ch < CC; ++ch) x[ch] = xB[i][ch];
         } else {
           const float* fe = fl + j * NFAC * 32;
-          auto fv = [&](int f) -> float { return __ldcg(fe + f * 32); };
+          auto fv = [&](int f) -> float {
+            if constexpr (PIPE) return fcur[j][f]; else return __ldcg(fe + f * 32);
+          };
           float Lrow[R];
 #pragma unroll
           for (int tt = 0; tt < R; ++tt) Lrow[tt] = fv(tt);
