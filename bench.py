@@ -39,6 +39,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -169,15 +170,24 @@ def alu_peaks(sm_mhz: float):
     return N_SM * FP32_LANES * 2 * hz, N_SM * MUFU_LANES * hz
 
 
+def code_only(text: str) -> str:
+    """C++/CUDA source without its comments, trailing blanks and empty
+    lines (the sources hold no string with a comment marker in it)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def source_hash() -> str:
-    """Hash of the CUDA sources: the DRAM counters in the traffic file are
-    valid only for the kernels they were taken from."""
+    """Hash of the CUDA sources' code (comments left out): the DRAM counters
+    in the traffic file are valid only for the kernels they were taken
+    from."""
     csrc = os.path.join(ROOT, "paper_1705_01674_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(os.listdir(csrc)):
         if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fn.encode() + b"\0" + fh.read())
+            with open(os.path.join(csrc, fn), encoding="utf-8") as fh:
+                h.update(fn.encode() + b"\0" + code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

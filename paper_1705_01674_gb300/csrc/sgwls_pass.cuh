@@ -32,9 +32,10 @@
 //               column; the warps then merge the block's G chunk 2-ports into
 //               one group 2-port as a binary tree, keeping the merge factors
 //               for the back-fill.  The last block of each band to finish
-//               solves the band's reduced system: block Cholesky of the block
-//               tridiagonal system on the group separators (r x r blocks),
-//               split into segments that the warps fold in parallel.
+//               solves the band's reduced system: the chain of the group
+//               2-ports, eliminated separator by separator in margin form
+//               (r x r blocks), split into segments that the warps fold in
+//               parallel.
 //   k_backsub   block = 32 neighbouring centres x G chunks.  The warps
 //               back-fill the separators inside the group down the merge
 //               tree; every thread back-substitutes its interior from the kept

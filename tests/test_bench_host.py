@@ -78,3 +78,10 @@ def test_roofline_lines_pick_the_slower_direction():
     fl, _ = bench.pass_work(1080, 1920, 3, 2, 1)
     assert alu["achieved"] == pytest.approx(fl / 0.2e-3 / 1e12)
     assert alu["frac"] == pytest.approx(fl / 0.2e-3 / bench.alu_peaks(sm_mhz)[0])
+
+
+def test_source_hash_ignores_comments_only():
+    """The traffic file stays valid across comment edits, not code edits."""
+    code = "int a = 1;  // one\n/* block\n comment */\nint b = 2;\n"
+    assert bench.code_only(code) == bench.code_only("int a = 1;\n\n// other words\nint b = 2;")
+    assert bench.code_only(code) != bench.code_only("int a = 1;\nint b = 3;")
