@@ -830,9 +830,10 @@ struct StridedG {
 // Forward sweep of one chunk for the summary: eliminates the interior and
 // writes its 2-port to `out`.
 // Factor store of one subsystem (band of 32 subsystems, lane in the band):
-// fac[band][e][field][32] with e = line * (2r+1) + j over the L lines and
-// field < 2r + CC; psi[band][c][k][i][32].  Inside a band every offset is a
-// compile-time multiple of 32 floats from the line's base.
+// fac[band][e][2r + CC fields x 32 lanes, grouped as in st_fields] with
+// e = line * (2r+1) + j over the L lines; psi[band][c][k][i][32].  Inside a
+// band every offset is a compile-time multiple of 32 floats from the line's
+// base.
 // With a.nslot > 0 the store is a ring of a.nslot band slots (the
 // queue-scheduled pass reuses a slot once every reader of its band is done).
 __device__ __forceinline__ size_t fac_slot(const PassArgs& a, int sys) {
@@ -844,6 +845,40 @@ __device__ __forceinline__ float* fac_lane(const PassArgs& a, int sys) {
   const size_t band = (size_t)a.L * (2 * R + 1) * (2 * R + CC) * 32;
   return a.fac + fac_slot(a, sys) * band + (sys & 31);
 }
+// Factor-store entry of a band: NF fields x 32 lanes, the fields in groups
+// of four, then a pair, then a single one (NF = 4k + 2a + b); in the block
+// of group [f, f + w) lane l's w fields are one w x 4-byte word at
+// entry + f * 32 + w * l.  So a lane stores and loads an entry with a few
+// wide accesses, and a warp's lanes of one band touch contiguous memory.
+template <int NF>
+__device__ __forceinline__ void st_fields(float* eb, int l, const float (&v)[NF]) {
+  int f = 0;
+#pragma unroll
+  for (; f + 4 <= NF; f += 4)
+    *reinterpret_cast<float4*>(eb + f * 32 + 4 * l) = make_float4(v[f], v[f + 1], v[f + 2], v[f + 3]);
+  if constexpr (NF % 4 >= 2) {
+    *reinterpret_cast<float2*>(eb + (NF / 4 * 4) * 32 + 2 * l) = make_float2(v[NF / 4 * 4], v[NF / 4 * 4 + 1]);
+  }
+  if constexpr (NF % 2 == 1) eb[(NF - 1) * 32 + l] = v[NF - 1];
+}
+template <int NF>
+__device__ __forceinline__ void ld_fields(const float* eb, int l, float (&v)[NF]) {
+#pragma unroll
+  for (int f = 0; f + 4 <= NF; f += 4) {
+    const float4 q = __ldcg(reinterpret_cast<const float4*>(eb + f * 32 + 4 * l));
+    v[f] = q.x;
+    v[f + 1] = q.y;
+    v[f + 2] = q.z;
+    v[f + 3] = q.w;
+  }
+  if constexpr (NF % 4 >= 2) {
+    const float2 q = __ldcg(reinterpret_cast<const float2*>(eb + (NF / 4 * 4) * 32 + 2 * l));
+    v[NF / 4 * 4] = q.x;
+    v[NF / 4 * 4 + 1] = q.y;
+  }
+  if constexpr (NF % 2 == 1) v[NF - 1] = __ldcg(eb + (NF - 1) * 32 + l);
+}
+
 // Per-entry buffers of the refinement (rhs, xent): [band][e][CC][32].
 template <int R, int CC>
 __device__ __forceinline__ float* ent_lane(const PassArgs& a, float* buf, int sys) {
@@ -867,7 +902,8 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
   using F = Fields<R, CC>;
   const Chunk q = make_chunk<R>(a, c);
   const int pstride = t.pstride;
-  float* const fac = KEEP ? fac_lane<R, CC>(a, sys) : nullptr;
+  // the band's factor store and the lane in it (st_fields layout)
+  float* const fac = KEEP ? fac_lane<R, CC>(a, sys) - (sys & 31) : nullptr;
   // RHSB: the right-hand side of every entry comes from a.rhs (the
   // refinement's residual) instead of the estimate planes of the tile
   const float* const rhs = RHSB ? ent_lane<R, CC>(a, a.rhs, sys) : nullptr;
@@ -959,13 +995,14 @@ __device__ __forceinline__ void chunk_summary(const PassArgs& a, const Tile& t, 
           for (int ch = 0; ch < CC; ++ch) HT[i][ch] += yd * y[ch];
         }
         if constexpr (KEEP) {
-          float* fe = fac + ((line * n + j) * NFAC) * 32;
+          float fv[NFAC];
 #pragma unroll
-          for (int tt = 0; tt < R; ++tt) fe[tt * 32] = Lrow[tt];
+          for (int tt = 0; tt < R; ++tt) fv[tt] = Lrow[tt];
 #pragma unroll
-          for (int ch = 0; ch < CC; ++ch) fe[(R + ch) * 32] = y[ch] * dinv;
+          for (int ch = 0; ch < CC; ++ch) fv[R + ch] = y[ch] * dinv;
 #pragma unroll
-          for (int i = 0; i < R; ++i) fe[(R + CC + i) * 32] = -YT[i] * dinv;
+          for (int i = 0; i < R; ++i) fv[R + CC + i] = -YT[i] * dinv;
+          st_fields<NFAC>(fac + ((line * n + j) * NFAC) * 32, sys & 31, fv);
         }
         float YB[R];
 #pragma unroll
@@ -2135,7 +2172,9 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
       const int lo = max(R, o - R), hi = min(a.D - 1 - R, o + R);
       inv_cnt = 1.0f / (float)(hi - lo + 1);
     }
-    const float* const fac = fac_lane<R, CC>(a, sys);
+    // the band's factor store and the lane in it (st_fields layout)
+    const float* const fac = fac_lane<R, CC>(a, sys) - (sys & 31);
+    const int flane = sys & 31;
     const float* const psi = psi_lane<R>(a, sys);
     float Lb[R][R] = {};   // Lb[u-1][t-1] = L[p+u, p+u-t]
     float xw[R][CC] = {};  // x of entries p+1 .. p+R (interior only)
@@ -2188,9 +2227,7 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
       if constexpr (PIPE) {
         const float* f0 = fac + l * n * NFAC * 32;
 #pragma unroll
-        for (int j = 0; j < n; ++j)
-#pragma unroll
-          for (int f = 0; f < NFAC; ++f) fnext[j][f] = __ldcg(f0 + (j * NFAC + f) * 32);
+        for (int j = 0; j < n; ++j) ld_fields<NFAC>(f0 + j * NFAC * 32, flane, fnext[j]);
       }
     };
     if constexpr (PIPE) load_line(q.line1 - 1);
@@ -2218,9 +2255,10 @@ __device__ __forceinline__ void body_backsub(const PassArgs& a, int bx, int by, 
 #pragma unroll
               for (int ch = 0; ch < CC; ++ch) x[ch] = xB[i][ch];
         } else {
-          const float* fe = fl + j * NFAC * 32;
+          float fe[PIPE ? 1 : NFAC];
+          if constexpr (!PIPE) ld_fields<NFAC>(fl + j * NFAC * 32, flane, fe);
           auto fv = [&](int f) -> float {
-            if constexpr (PIPE) return fcur[j][f]; else return __ldcg(fe + f * 32);
+            if constexpr (PIPE) return fcur[j][f]; else return fe[f];
           };
           float Lrow[R];
 #pragma unroll
