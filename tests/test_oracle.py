@@ -457,3 +457,34 @@ def test_frac_settings_fp32_sensitivity_is_the_diagonal(r):
         worst_all = max(worst_all, float(np.abs(solve_banded((r, r), ab_all, f) - exact).max()))
     assert worst_off < 1e-7, worst_off
     assert worst_all > 1e-4, worst_all
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+@pytest.mark.parametrize("weight", ["exp", "frac"])
+def test_schur_complements_keep_margin_form(r, weight):
+    """The fact the subtraction-free pivots rest on, checked in FP64 on the
+    oracle's A_s (Eq. 4): eliminating any leading block I of A_s leaves a
+    Schur complement S on the rest whose off-diagonals are <= 0 and whose
+    rows sum to 1 plus the margin the eliminated entries pass on,
+    1 + |A_RI| A_II^-1 1 (so >= 1); hence each diagonal entry of S equals
+    its row's margin plus the magnitudes of its off-diagonals.  A sign error
+    (a Laplacian with +lambda w off the diagonal) breaks all three."""
+    F = synth.rgb_scene(24, 30, seed=21, n_rect=6, n_disk=2)
+    G = synth.luminance(F)
+    prm = Params(r=r, weight=weight, sigma_s=float(r), sigma_r=0.1, alpha_s=1.2, alpha_r=1.2, eps=1e-4)
+    lam = 900.0 if weight == "frac" else 1.0
+    rows, cols = neighbourhood_construction(COLUMN, 12, r, 24, 30)
+    A = _band_to_dense(subsystem_band(rows, cols, G, lam, prm), r)
+    s = A.shape[0]
+    assert np.allclose(A.sum(axis=1), 1.0, rtol=0, atol=1e-9 * np.abs(A).max())
+    for cut in (1, r, 2 * r + 1, s // 3, s // 2):
+        I, Rr = slice(0, cut), slice(cut, s)
+        Aii_inv = np.linalg.inv(A[I, I])
+        S = A[Rr, Rr] - A[Rr, I] @ Aii_inv @ A[I, Rr]
+        off = S - np.diag(np.diag(S))
+        scale = np.abs(A).max()
+        assert off.max() <= 1e-12 * scale
+        margin = 1.0 + np.abs(A[Rr, I]) @ (Aii_inv @ np.ones(cut))
+        assert np.all(margin >= 1.0 - 1e-12)
+        assert np.allclose(S.sum(axis=1), margin, rtol=1e-9, atol=1e-9 * scale)
+        assert np.allclose(np.diag(S), margin + np.abs(off).sum(axis=1), rtol=1e-12, atol=1e-9 * scale)
